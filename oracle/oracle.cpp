@@ -1,0 +1,539 @@
+// FP64 CPU oracle for the anisotropic three-point correlation function (3PCF)
+// of Friesen et al., "Galactos" (SC17, arXiv 1709.00086), Section 3.1.
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously-correct
+// definition that the CUDA path is checked against.  Only the test-suite, the
+// smoke check and the CPU-baseline leg of the benchmark may load it.  It shares
+// no code, header, table or constant with the CUDA library, and it never calls
+// into it.
+//
+// What is computed (Section 3.1, the expansion equation and Algorithm 1):
+//   * edges        e_k = rmin + (rmax-rmin)*k/B, e_0 = rmin, e_B = rmax exactly
+//   * pairs        primary i (< n_primary), secondary j (any point, j != i);
+//                  separation d = x_j - x_i, minimum image per axis when the
+//                  box is periodic ("if d > L/2: d -= L; if d < -L/2: d += L")
+//   * bin          r2 = (dx*dx + dy*dy) + dz*dz in FP64 (no fused multiply-add);
+//                  pair is in bin b iff e_b^2 <= r2 < e_{b+1}^2; r2 == 0 skipped
+//   * frame        LOS = z (modes 0, 1) or the radial direction from the box
+//                  centre to the primary (mode 2), the pair separation being
+//                  rotated so that the LOS becomes +z (Section 3.1, Fig. 2)
+//   * harmonics    Y_lm(theta, phi) = std::sph_legendre(l, m, theta) e^{i m phi}
+//                  (orthonormal, Condon-Shortley phase) -- a library routine,
+//                  not a recurrence of our own
+//   * multipoles   a_lm(i, b) = sum_{j in b} w_j Y_lm(rhat'_ij), m >= 0
+//                  (the discrete form of the integral over the shell, Sec 3.1)
+//   * zeta         zeta^m_{l l'}(b1, b2) = sum_i w_i a_lm(i,b1) conj(a_l'm(i,b2))
+//                  (the product of coefficients about one primary, summed over
+//                  primaries, Sec 3.1)
+//   * counts       number of ordered (i, j) pairs accepted into each bin
+//   * gradient     of L = sum over all stored entries |zeta - zeta_t|^2 with the
+//                  pair set and bins frozen (not in the paper; the adjoint's
+//                  definition)
+//
+// Output layout of zeta: for m = 0..lmax a K_m x K_m complex block, K_m =
+// B*(lmax+1-m), row (l-m)*B + b1, column (l'-m)*B + b2, (re, im) interleaved.
+//
+// Build: g++ -O2 -fopenmp -ffp-contract=off -shared -fPIC (contraction off so
+// that r2 is rounded exactly as written above).
+
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef std::complex<double> cplx;
+
+namespace {
+
+const double kPi = 3.14159265358979323846264338327950288;
+
+struct Geom {
+    double box;
+    int periodic;   // 1 for LOS mode 0 (periodic, z), 0 otherwise
+    int radial;     // 1 for LOS mode 2 (radial from the box centre)
+    int nbins;
+    int lmax;
+    std::vector<double> e2;  // squared edges, nbins+1
+};
+
+int make_geom(Geom& g, int nbins, double rmin, double rmax, int lmax, double box,
+              int los_mode) {
+    if (nbins < 1 || lmax < 0 || !(rmin >= 0.0) || !(rmax > rmin) || !(box > 0.0))
+        return -1;
+    if (los_mode < 0 || los_mode > 2) return -1;
+    g.box = box;
+    g.periodic = (los_mode == 0);
+    g.radial = (los_mode == 2);
+    g.nbins = nbins;
+    g.lmax = lmax;
+    g.e2.resize(nbins + 1);
+    for (int k = 0; k <= nbins; ++k) {
+        double e;
+        if (k == 0) e = rmin;
+        else if (k == nbins) e = rmax;
+        else e = rmin + ((rmax - rmin) * (double)k) / (double)nbins;
+        g.e2[k] = e * e;
+    }
+    return 0;
+}
+
+// Separation, image shift and radial bin of the pair (i -> j).  Returns the
+// bin or -1.  sh[] receives the integer image shift applied per axis.
+int pair_bin(const Geom& g, const double* xi, const double* xj, double d[3], int sh[3]) {
+    for (int a = 0; a < 3; ++a) {
+        double t = xj[a] - xi[a];
+        int s = 0;
+        if (g.periodic) {
+            if (t > 0.5 * g.box) { t -= g.box; s = -1; }
+            else if (t < -0.5 * g.box) { t += g.box; s = 1; }
+        }
+        d[a] = t;
+        sh[a] = s;
+    }
+    double r2 = d[0] * d[0] + d[1] * d[1];
+    r2 = r2 + d[2] * d[2];
+    if (r2 == 0.0) return -1;
+    if (r2 < g.e2[0] || !(r2 < g.e2[g.nbins])) return -1;
+    int b = 0;
+    while (b + 1 < g.nbins && g.e2[b + 1] <= r2) ++b;
+    return b;
+}
+
+// Rotation taking the primary's line of sight to +z (identity for z modes).
+// Radial mode: n = (x_i - c)/|x_i - c|, c the box centre (n = z if x_i = c);
+// Rodrigues rotation about n x z; a half turn about x when n is (nearly) -z.
+void los_rotation(const Geom& g, const double* xi, double R[9]) {
+    for (int k = 0; k < 9; ++k) R[k] = (k % 4 == 0) ? 1.0 : 0.0;
+    if (!g.radial) return;
+    double c = 0.5 * g.box;
+    double n[3] = {xi[0] - c, xi[1] - c, xi[2] - c};
+    double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    if (nn == 0.0) return;
+    for (int a = 0; a < 3; ++a) n[a] /= nn;
+    double ct = n[2];
+    if (ct < -1.0 + 1e-12) {
+        R[4] = -1.0;
+        R[8] = -1.0;
+        return;
+    }
+    // v = n x z = (n_y, -n_x, 0); R = I + [v]x + [v]x^2 / (1 + ct)
+    double v[3] = {n[1], -n[0], 0.0};
+    double K[9] = {0.0, -v[2], v[1], v[2], 0.0, -v[0], -v[1], v[0], 0.0};
+    double K2[9];
+    for (int r = 0; r < 3; ++r)
+        for (int s = 0; s < 3; ++s) {
+            double acc = 0.0;
+            for (int t = 0; t < 3; ++t) acc += K[3 * r + t] * K[3 * t + s];
+            K2[3 * r + s] = acc;
+        }
+    for (int k = 0; k < 9; ++k) R[k] += K[k] + K2[k] / (1.0 + ct);
+}
+
+inline int lm_index(int l, int m) { return l * (l + 1) / 2 + m; }
+inline int n_lm(int lmax) { return (lmax + 1) * (lmax + 2) / 2; }
+
+// Y_lm(rhat) for 0 <= m <= l <= lmax, via the library's spherical Legendre
+// function.  out[lm_index(l,m)].
+void ylm_all(int lmax, const double d[3], cplx* out) {
+    double r = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double ct = d[2] / r;
+    if (ct > 1.0) ct = 1.0;
+    if (ct < -1.0) ct = -1.0;
+    double theta = std::acos(ct);
+    double phi = std::atan2(d[1], d[0]);
+    for (int l = 0; l <= lmax; ++l)
+        for (int m = 0; m <= l; ++m) {
+            double p = std::sph_legendre((unsigned)l, (unsigned)m, theta);
+            out[lm_index(l, m)] = p * cplx(std::cos(m * phi), std::sin(m * phi));
+        }
+}
+
+// Y_{l,m} for any integer m (Y_{l,-m} = (-1)^m conj(Y_lm)); zero if |m| > l.
+cplx ylm_signed(const cplx* Y, int l, int m) {
+    if (l < 0 || m > l || -m > l) return cplx(0.0, 0.0);
+    if (m >= 0) return Y[lm_index(l, m)];
+    cplx v = std::conj(Y[lm_index(l, -m)]);
+    return (((-m) & 1) ? -v : v);
+}
+
+// Gradient of Y_lm(d/|d|) with respect to the separation d, from the ladder
+// relations of the regular solid harmonics R_lm = r^l Y_lm:
+//   dz R_lm          =  sqrt((2l+1)/(2l-1) (l-m)(l+m))   R_{l-1,m}
+//   (dx + i dy) R_lm =  sqrt((2l+1)/(2l-1) (l-m)(l-m-1)) R_{l-1,m+1}
+//   (dx - i dy) R_lm = -sqrt((2l+1)/(2l-1) (l+m)(l+m-1)) R_{l-1,m-1}
+// and grad Y_lm = r^-l grad R_lm - l r^-2 Y_lm d.  Y holds Y_{l'm'}(rhat) for
+// l' <= lmax (computed by ylm_all); gY receives 3 complex per (l, m >= 0).
+void ylm_grad_all(int lmax, const double d[3], const cplx* Y, cplx* gY) {
+    double r = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double rhat[3] = {d[0] / r, d[1] / r, d[2] / r};
+    for (int l = 0; l <= lmax; ++l)
+        for (int m = 0; m <= l; ++m) {
+            cplx gx(0.0, 0.0), gy(0.0, 0.0), gz(0.0, 0.0);
+            if (l >= 1) {
+                double f = (2.0 * l + 1.0) / (2.0 * l - 1.0);
+                double cz = std::sqrt(f * (double)(l - m) * (double)(l + m));
+                double cp = std::sqrt(f * (double)(l - m) * (double)(l - m - 1));
+                double cm = -std::sqrt(f * (double)(l + m) * (double)(l + m - 1));
+                cplx up = cp * ylm_signed(Y, l - 1, m + 1);   // (dx + i dy) R / r^(l-1)
+                cplx dn = cm * ylm_signed(Y, l - 1, m - 1);   // (dx - i dy) R / r^(l-1)
+                gx = 0.5 * (up + dn) / r;
+                gy = (up - dn) / (cplx(0.0, 2.0) * r);
+                gz = cz * ylm_signed(Y, l - 1, m) / r;
+            }
+            cplx y = Y[lm_index(l, m)];
+            double s = (double)l / r;
+            gY[3 * lm_index(l, m) + 0] = gx - s * y * rhat[0];
+            gY[3 * lm_index(l, m) + 1] = gy - s * y * rhat[1];
+            gY[3 * lm_index(l, m) + 2] = gz - s * y * rhat[2];
+        }
+}
+
+inline int64_t zeta_block_offset(int nbins, int lmax, int m) {
+    int64_t off = 0;
+    for (int mm = 0; mm < m; ++mm) {
+        int64_t K = (int64_t)nbins * (lmax + 1 - mm);
+        off += K * K;
+    }
+    return off;  // in complex entries
+}
+
+inline int64_t zeta_size(int nbins, int lmax) { return zeta_block_offset(nbins, lmax, lmax + 1); }
+
+// a_lm(i, b) for one primary, all n points as secondaries.  alm: nbins*nlm
+// complex, zeroed here.  Optional frozen geometry: if pos_bins is given, the
+// pair set, bins and image shifts come from pos_bins and only the separation
+// vectors come from pos.
+void alm_one(const Geom& g, const double* pos, const double* pos_bins, const double* w,
+             int64_t n, int64_t i, cplx* alm, int64_t* counts) {
+    const int nlm = n_lm(g.lmax);
+    std::fill(alm, alm + (int64_t)g.nbins * nlm, cplx(0.0, 0.0));
+    std::vector<cplx> Y(nlm);
+    const double* P = pos_bins ? pos_bins : pos;
+    double R[9];
+    los_rotation(g, pos + 3 * i, R);
+    for (int64_t j = 0; j < n; ++j) {
+        if (j == i) continue;
+        double d[3];
+        int sh[3];
+        int b = pair_bin(g, P + 3 * i, P + 3 * j, d, sh);
+        if (b < 0) continue;
+        if (pos_bins) {
+            for (int a = 0; a < 3; ++a) d[a] = (pos[3 * j + a] - pos[3 * i + a]) + sh[a] * g.box;
+        }
+        double dr[3];
+        for (int a = 0; a < 3; ++a) dr[a] = R[3 * a] * d[0] + R[3 * a + 1] * d[1] + R[3 * a + 2] * d[2];
+        ylm_all(g.lmax, dr, Y.data());
+        cplx* ab = alm + (int64_t)b * nlm;
+        for (int k = 0; k < nlm; ++k) ab[k] += w[j] * Y[k];
+        if (counts) counts[b] += 1;
+    }
+}
+
+// zeta += wi * a a^H (per m block), alm of one primary in [b][lm] layout.
+void zeta_accumulate(int nbins, int lmax, const cplx* alm, double wi, cplx* zeta) {
+    const int nlm = n_lm(lmax);
+    for (int m = 0; m <= lmax; ++m) {
+        const int64_t K = (int64_t)nbins * (lmax + 1 - m);
+        cplx* Z = zeta + zeta_block_offset(nbins, lmax, m);
+        for (int l = m; l <= lmax; ++l)
+            for (int b1 = 0; b1 < nbins; ++b1) {
+                const int64_t r = (int64_t)(l - m) * nbins + b1;
+                const cplx a1 = wi * alm[(int64_t)b1 * nlm + lm_index(l, m)];
+                for (int lp = m; lp <= lmax; ++lp)
+                    for (int b2 = 0; b2 < nbins; ++b2) {
+                        const int64_t c = (int64_t)(lp - m) * nbins + b2;
+                        Z[r * K + c] += a1 * std::conj(alm[(int64_t)b2 * nlm + lm_index(lp, m)]);
+                    }
+            }
+    }
+}
+
+int threads_of(int nthreads) {
+#ifdef _OPENMP
+    return nthreads > 0 ? nthreads : omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
+
+}  // namespace
+
+extern "C" {
+
+// Number of complex entries of the zeta output.
+int64_t orc_zeta_size(int nbins, int lmax) { return zeta_size(nbins, lmax); }
+
+int orc_edges(int nbins, double rmin, double rmax, double* edges2) {
+    Geom g;
+    if (make_geom(g, nbins, rmin, rmax, 0, 1.0, 1) != 0) return -1;
+    for (int k = 0; k <= nbins; ++k) edges2[k] = g.e2[k];
+    return 0;
+}
+
+// Y_lm at n directions d (n x 3, need not be unit): out n x nlm complex.
+int orc_ylm(int lmax, const double* d, int64_t n, double* out) {
+    const int nlm = n_lm(lmax);
+    for (int64_t k = 0; k < n; ++k)
+        ylm_all(lmax, d + 3 * k, reinterpret_cast<cplx*>(out) + k * nlm);
+    return 0;
+}
+
+// grad_d Y_lm(d/|d|): out n x nlm x 3 complex.
+int orc_ylm_grad(int lmax, const double* d, int64_t n, double* out) {
+    const int nlm = n_lm(lmax + 1);
+    std::vector<cplx> Y(nlm);
+    for (int64_t k = 0; k < n; ++k) {
+        ylm_all(lmax, d + 3 * k, Y.data());
+        ylm_grad_all(lmax, d + 3 * k, Y.data(), reinterpret_cast<cplx*>(out) + k * 3 * n_lm(lmax));
+    }
+    return 0;
+}
+
+// Per-primary multipoles for the listed primaries: alm np x nbins x nlm
+// complex; counts (nbins int64, may be null) accumulates their pair counts.
+int orc_alm(const double* pos, const double* w, int64_t n, const int64_t* prim, int64_t np,
+            double box, int los_mode, int nbins, double rmin, double rmax, int lmax,
+            double* alm, int64_t* counts, int nthreads) {
+    Geom g;
+    if (make_geom(g, nbins, rmin, rmax, lmax, box, los_mode) != 0) return -1;
+    const int nlm = n_lm(lmax);
+    const int nt = threads_of(nthreads);
+    std::vector<std::vector<int64_t>> tc(nt, std::vector<int64_t>(nbins, 0));
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int64_t k = 0; k < np; ++k) {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        alm_one(g, pos, nullptr, w, n, prim[k],
+                reinterpret_cast<cplx*>(alm) + k * (int64_t)nbins * nlm, tc[t].data());
+    }
+    if (counts)
+        for (int t = 0; t < nt; ++t)
+            for (int b = 0; b < nbins; ++b) counts[b] += tc[t][b];
+    return 0;
+}
+
+// zeta over primaries 0..n_primary-1 (all n points are secondaries).
+// pos_bins: optional frozen pair geometry (see alm_one), may be null.
+int orc_zeta(const double* pos, const double* pos_bins, const double* w, int64_t n,
+             int64_t n_primary, double box, int los_mode, int nbins, double rmin, double rmax,
+             int lmax, double* zeta, int64_t* counts, int nthreads) {
+    Geom g;
+    if (make_geom(g, nbins, rmin, rmax, lmax, box, los_mode) != 0) return -1;
+    const int nlm = n_lm(lmax);
+    const int64_t zs = zeta_size(nbins, lmax);
+    const int nt = threads_of(nthreads);
+    std::vector<std::vector<cplx>> tz(nt, std::vector<cplx>(zs, cplx(0.0, 0.0)));
+    std::vector<std::vector<int64_t>> tc(nt, std::vector<int64_t>(nbins, 0));
+#pragma omp parallel num_threads(nt)
+    {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        std::vector<cplx> alm((int64_t)nbins * nlm);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t i = 0; i < n_primary; ++i) {
+            alm_one(g, pos, pos_bins, w, n, i, alm.data(), tc[t].data());
+            zeta_accumulate(nbins, lmax, alm.data(), w[i], tz[t].data());
+        }
+    }
+    cplx* Z = reinterpret_cast<cplx*>(zeta);
+    std::fill(Z, Z + zs, cplx(0.0, 0.0));
+    for (int t = 0; t < nt; ++t)
+        for (int64_t k = 0; k < zs; ++k) Z[k] += tz[t][k];
+    if (counts)
+        for (int t = 0; t < nt; ++t)
+            for (int b = 0; b < nbins; ++b) counts[b] += tc[t][b];
+    return 0;
+}
+
+// zeta from given per-primary multipoles (np x nbins x nlm complex) and weights.
+int orc_zeta_from_alm(const double* alm, const double* wprim, int64_t np, int nbins,
+                      int lmax, double* zeta) {
+    const int nlm = n_lm(lmax);
+    const int64_t zs = zeta_size(nbins, lmax);
+    cplx* Z = reinterpret_cast<cplx*>(zeta);
+    std::fill(Z, Z + zs, cplx(0.0, 0.0));
+    for (int64_t i = 0; i < np; ++i)
+        zeta_accumulate(nbins, lmax, reinterpret_cast<const cplx*>(alm) + i * (int64_t)nbins * nlm,
+                        wprim[i], Z);
+    return 0;
+}
+
+// O(N^3) triplet sum: zeta^m_{ll'}(b1,b2) = sum_i w_i sum_{j in b1} sum_{k in b2}
+// w_j w_k Y_lm(rhat_ij) conj(Y_l'm(rhat_ik)), j = k included.  Tiny N only.
+int orc_zeta_triplets(const double* pos, const double* w, int64_t n, double box, int los_mode,
+                      int nbins, double rmin, double rmax, int lmax, double* zeta) {
+    Geom g;
+    if (make_geom(g, nbins, rmin, rmax, lmax, box, los_mode) != 0) return -1;
+    const int nlm = n_lm(lmax);
+    cplx* Z = reinterpret_cast<cplx*>(zeta);
+    std::fill(Z, Z + zeta_size(nbins, lmax), cplx(0.0, 0.0));
+    std::vector<cplx> Yj(nlm), Yk(nlm);
+    for (int64_t i = 0; i < n; ++i) {
+        double R[9];
+        los_rotation(g, pos + 3 * i, R);
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dj[3], rj[3];
+            int sj[3];
+            int bj = pair_bin(g, pos + 3 * i, pos + 3 * j, dj, sj);
+            if (bj < 0) continue;
+            for (int a = 0; a < 3; ++a) rj[a] = R[3 * a] * dj[0] + R[3 * a + 1] * dj[1] + R[3 * a + 2] * dj[2];
+            ylm_all(lmax, rj, Yj.data());
+            for (int64_t k = 0; k < n; ++k) {
+                if (k == i) continue;
+                double dk[3], rk[3];
+                int sk[3];
+                int bk = pair_bin(g, pos + 3 * i, pos + 3 * k, dk, sk);
+                if (bk < 0) continue;
+                for (int a = 0; a < 3; ++a) rk[a] = R[3 * a] * dk[0] + R[3 * a + 1] * dk[1] + R[3 * a + 2] * dk[2];
+                ylm_all(lmax, rk, Yk.data());
+                const double wt = w[i] * w[j] * w[k];
+                for (int m = 0; m <= lmax; ++m) {
+                    const int64_t K = (int64_t)nbins * (lmax + 1 - m);
+                    cplx* Zm = Z + zeta_block_offset(nbins, lmax, m);
+                    for (int l = m; l <= lmax; ++l)
+                        for (int lp = m; lp <= lmax; ++lp)
+                            Zm[((int64_t)(l - m) * nbins + bj) * K + (int64_t)(lp - m) * nbins + bk] +=
+                                wt * Yj[lm_index(l, m)] * std::conj(Yk[lm_index(lp, m)]);
+                }
+            }
+        }
+    }
+    return 0;
+}
+
+// Isotropic Legendre 3PCF by brute force over pairs of pairs (Section 2.2):
+// iso[l][b1][b2] = (2l+1)/(4 pi) sum_i w_i sum_{j in b1, k in b2} w_j w_k
+// P_l(rhat_ij . rhat_ik), j = k included.  Output (lmax+1) x nbins x nbins.
+int orc_iso_legendre(const double* pos, const double* w, int64_t n, double box, int los_mode,
+                     int nbins, double rmin, double rmax, int lmax, double* iso) {
+    Geom g;
+    if (make_geom(g, nbins, rmin, rmax, lmax, box, los_mode) != 0) return -1;
+    std::fill(iso, iso + (int64_t)(lmax + 1) * nbins * nbins, 0.0);
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dj[3];
+            int sj[3];
+            int bj = pair_bin(g, pos + 3 * i, pos + 3 * j, dj, sj);
+            if (bj < 0) continue;
+            double rj = std::sqrt(dj[0] * dj[0] + dj[1] * dj[1] + dj[2] * dj[2]);
+            for (int64_t k = 0; k < n; ++k) {
+                if (k == i) continue;
+                double dk[3];
+                int sk[3];
+                int bk = pair_bin(g, pos + 3 * i, pos + 3 * k, dk, sk);
+                if (bk < 0) continue;
+                double rk = std::sqrt(dk[0] * dk[0] + dk[1] * dk[1] + dk[2] * dk[2]);
+                double mu = (dj[0] * dk[0] + dj[1] * dk[1] + dj[2] * dk[2]) / (rj * rk);
+                if (mu > 1.0) mu = 1.0;
+                if (mu < -1.0) mu = -1.0;
+                const double wt = w[i] * w[j] * w[k];
+                for (int l = 0; l <= lmax; ++l)
+                    iso[((int64_t)l * nbins + bj) * nbins + bk] +=
+                        (2.0 * l + 1.0) / (4.0 * kPi) * wt * std::legendre((unsigned)l, mu);
+            }
+        }
+    }
+    return 0;
+}
+
+// Reference gradient of L = sum over all stored entries |zeta - zeta_t|^2,
+// given G = zeta - zeta_t (same layout as zeta), LOS = z modes only, every
+// point a primary (n_primary = n).  Pair set and bins are held fixed.
+//   H_{i,m} = w_i (G_m + G_m^H) A_{i,m}
+//   dL/dw_i      += 2 sum_m Re(A_{i,m}^H G_m A_{i,m})
+//   dL/dw_j      += sum_i 2 Re sum_lm conj(H_{i,lm,b}) Y_lm(rhat_ij)
+//   dL/dd_ij      = 2 w_j Re sum_lm conj(H_{i,lm,b}) grad_d Y_lm(d_ij)
+//   dpos_j += dL/dd_ij, dpos_i -= dL/dd_ij
+int orc_grad(const double* pos, const double* w, int64_t n, double box, int los_mode, int nbins,
+             double rmin, double rmax, int lmax, const double* Gz, double* dpos, double* dw,
+             int nthreads) {
+    Geom g;
+    if (make_geom(g, nbins, rmin, rmax, lmax, box, los_mode) != 0) return -1;
+    if (g.radial) return -2;
+    const int nlm = n_lm(lmax);
+    const cplx* G = reinterpret_cast<const cplx*>(Gz);
+    const int nt = threads_of(nthreads);
+    std::vector<std::vector<double>> tdpos(nt, std::vector<double>(3 * n, 0.0));
+    std::vector<std::vector<double>> tdw(nt, std::vector<double>(n, 0.0));
+#pragma omp parallel num_threads(nt)
+    {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        std::vector<cplx> alm((int64_t)nbins * nlm), H((int64_t)nbins * nlm);
+        std::vector<cplx> Y(n_lm(lmax + 1)), gY(3 * (int64_t)nlm);
+        double* mydpos = tdpos[t].data();
+        double* mydw = tdw[t].data();
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t i = 0; i < n; ++i) {
+            alm_one(g, pos, nullptr, w, n, i, alm.data(), nullptr);
+            // H and the primary-weight term, block by block.
+            std::fill(H.begin(), H.end(), cplx(0.0, 0.0));
+            double dwi = 0.0;
+            for (int m = 0; m <= lmax; ++m) {
+                const int64_t K = (int64_t)nbins * (lmax + 1 - m);
+                const cplx* Gm = G + zeta_block_offset(nbins, lmax, m);
+                for (int l = m; l <= lmax; ++l)
+                    for (int b1 = 0; b1 < nbins; ++b1) {
+                        const int64_t r = (int64_t)(l - m) * nbins + b1;
+                        cplx acc(0.0, 0.0), accG(0.0, 0.0);
+                        for (int lp = m; lp <= lmax; ++lp)
+                            for (int b2 = 0; b2 < nbins; ++b2) {
+                                const int64_t c = (int64_t)(lp - m) * nbins + b2;
+                                const cplx a = alm[(int64_t)b2 * nlm + lm_index(lp, m)];
+                                acc += (Gm[r * K + c] + std::conj(Gm[c * K + r])) * a;
+                                accG += Gm[r * K + c] * a;
+                            }
+                        const cplx ar = alm[(int64_t)b1 * nlm + lm_index(l, m)];
+                        H[(int64_t)b1 * nlm + lm_index(l, m)] = w[i] * acc;
+                        dwi += 2.0 * std::real(std::conj(ar) * accG);
+                    }
+            }
+            mydw[i] += dwi;
+            // Pair pass: secondary weights and separations.
+            for (int64_t j = 0; j < n; ++j) {
+                if (j == i) continue;
+                double d[3];
+                int sh[3];
+                int b = pair_bin(g, pos + 3 * i, pos + 3 * j, d, sh);
+                if (b < 0) continue;
+                ylm_all(lmax, d, Y.data());
+                ylm_grad_all(lmax, d, Y.data(), gY.data());
+                double sw = 0.0, sd[3] = {0.0, 0.0, 0.0};
+                for (int l = 0; l <= lmax; ++l)
+                    for (int m = 0; m <= l; ++m) {
+                        const cplx h = std::conj(H[(int64_t)b * nlm + lm_index(l, m)]);
+                        sw += std::real(h * Y[lm_index(l, m)]);
+                        for (int a = 0; a < 3; ++a) sd[a] += std::real(h * gY[3 * lm_index(l, m) + a]);
+                    }
+                mydw[j] += 2.0 * sw;
+                for (int a = 0; a < 3; ++a) {
+                    const double v = 2.0 * w[j] * sd[a];
+                    mydpos[3 * j + a] += v;
+                    mydpos[3 * i + a] -= v;
+                }
+            }
+        }
+    }
+    std::fill(dpos, dpos + 3 * n, 0.0);
+    std::fill(dw, dw + n, 0.0);
+    for (int t = 0; t < nt; ++t) {
+        for (int64_t k = 0; k < 3 * n; ++k) dpos[k] += tdpos[t][k];
+        for (int64_t k = 0; k < n; ++k) dw[k] += tdw[t][k];
+    }
+    return 0;
+}
+
+}  // extern "C"
