@@ -1,0 +1,173 @@
+/*
+ * g3pcf.h -- C ABI of the GB300 (sm_103a) anisotropic three-point correlation
+ * function library, after Friesen et al., "Galactos: Computing the Anisotropic
+ * 3-Point Correlation Function for 2 Billion Galaxies" (SC17, arXiv 1709.00086).
+ *
+ * What the library computes (Section 3.1, the expansion equation and
+ * Algorithm 1 of the paper): for every primary galaxy i, all secondaries j
+ * within rmax are gathered and binned into radial shells (Sec. 3.1,
+ * "binned into spherical shells"); the separation is rotated into the frame
+ * whose z axis is the primary's line of sight (Sec. 3.1, Fig. 2); the
+ * spherical harmonics of the separation direction are summed per shell into
+ *      a_lm(i, b) = sum_{j in b} w_j Y_lm(rhat'_ij),     0 <= m <= l <= lmax
+ * (Sec. 3.1, the discrete form of the shell integral), and the products of the
+ * coefficients about each primary are summed over primaries into
+ *      zeta^m_{l l'}(b1, b2) = sum_i w_i a_lm(i, b1) conj(a_l'm(i, b2))
+ * (Sec. 3.1, "simply a_lm(r1) a*_l'm(r2)"; equal m from the axisymmetry
+ * about the line of sight).  Y_lm are orthonormal with the Condon-Shortley
+ * phase.  Weights w are an extension (the paper's catalogs are unweighted):
+ * a_lm is weighted by the secondary's w_j, zeta by the primary's w_i.
+ *
+ * Binning (the exact rule, identical to the FP64 reference): edges
+ * e_0 = rmin, e_B = rmax, e_k = rmin + (rmax - rmin)*k/B in FP64; the pair is in
+ * bin b iff e_b^2 <= r^2 < e_{b+1}^2 with r^2 = (dx*dx + dy*dy) + dz*dz
+ * evaluated in FP64 without fused multiply-add on d = x_j - x_i (minimum image
+ * per axis in a periodic box: d -= L if d > L/2, d += L if d < -L/2).  Pairs
+ * with r^2 == 0 (the primary itself and coincident points) are skipped.
+ *
+ * ZETA LAYOUT.  For m = 0..lmax one K_m x K_m complex block, K_m = nbins *
+ * (lmax + 1 - m), blocks stored consecutively; within block m the row index is
+ * (l - m)*nbins + b1 and the column index (l' - m)*nbins + b2, row-major,
+ * each entry two doubles (re, im).  Only m >= 0 is stored (zeta^{-m} =
+ * conj(zeta^m) for real weights).  Total g3pcf_zeta_size() complex entries.
+ *
+ * MEMORY AND STREAMS.  All array arguments marked "device" are device
+ * pointers owned by the caller; the library never frees them.  The plan owns
+ * its workspace (grown on demand, kept until g3pcf_destroy).  Compute calls are
+ * enqueued on the plan's stream (g3pcf_set_stream; default the legacy stream)
+ * and, unless G3PCF_F_NO_SYNC is given, synchronise that stream once at the end
+ * to read the device status word, so that range errors and bounded-wait
+ * timeouts are returned by the call itself.
+ *
+ * ERRORS.  Every entry point returns G3PCF_OK (0) or a negative code and, on
+ * error, stores a message retrievable with g3pcf_last_error() (per thread).
+ * Host-side validation happens before any device work is enqueued.
+ */
+#ifndef G3PCF_H
+#define G3PCF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct g3pcf_plan_s* g3pcf_plan_t;
+
+/* Line-of-sight / boundary modes (Sec. 3.1: "the line of sight ... which we
+ * here take to be the z-axis", and Fig. 2: rotate so that the primary lies on
+ * the z axis of the line of sight to the observer). */
+enum {
+    G3PCF_LOS_Z_PERIODIC = 0,  /* LOS = +z, periodic cube of side box (minimum image) */
+    G3PCF_LOS_Z_OPEN = 1,      /* LOS = +z, open cube [0, box)^3                      */
+    G3PCF_LOS_RADIAL_OPEN = 2  /* LOS = direction from the cube centre to the primary;
+                                  open cube.  Rotation: Rodrigues about n x z taking n
+                                  to +z; a half turn about x when n is within 1e-12 of
+                                  -z; n = +z for a primary at the centre.             */
+};
+
+/* Return codes. */
+enum {
+    G3PCF_OK = 0,
+    G3PCF_ERR_ARG = -1,         /* invalid argument (null pointer, bad size or mode)     */
+    G3PCF_ERR_RANGE = -2,       /* a position outside [0, box) or not finite, or a
+                                   non-finite weight (reported by the device check)     */
+    G3PCF_ERR_RMAX = -3,        /* periodic box with rmax >= box/2                       */
+    G3PCF_ERR_ALLOC = -4,       /* workspace allocation failed                           */
+    G3PCF_ERR_CUDA = -5,        /* a CUDA runtime call failed                            */
+    G3PCF_ERR_TIMEOUT = -6,     /* a bounded device wait expired (kernel returned early) */
+    G3PCF_ERR_STATE = -7,       /* backward/alm without a matching forward on this plan  */
+    G3PCF_ERR_UNSUPPORTED = -8  /* valid request this build does not implement           */
+};
+
+/* Flags for g3pcf_compute_ex / g3pcf_compute_batch. */
+enum {
+    G3PCF_F_POS_F64 = 1,        /* pos is double (n x 3) instead of float                */
+    G3PCF_F_CONTRACT_FP32 = 2,  /* zeta contraction in plain FP32 on the FMA pipe instead
+                                   of split-BF16 (hi+lo, 3 products) tcgen05 tensor cores */
+    G3PCF_F_NO_SYNC = 4,        /* do not synchronise at the end; device status is then
+                                   read by g3pcf_status()                                 */
+    G3PCF_F_KEEP_ALM = 8        /* keep the multipoles of the call for g3pcf_alm and
+                                   g3pcf_backward (implied when requires_grad is used)    */
+};
+
+/* Limits of this build. */
+#define G3PCF_MAX_LMAX 10
+#define G3PCF_MAX_NBINS 32
+#define G3PCF_MAX_POINTS ((int64_t)1 << 27)
+
+/* Number of complex entries of zeta for (nbins, lmax): sum_m K_m^2. */
+int64_t g3pcf_zeta_size(int nbins, int lmax);
+
+/* Create a plan (host only, no device work).  nbins in [1, 32]; 0 <= rmin <
+ * rmax; lmax in [0, 10]; box > 0; los_mode one of G3PCF_LOS_*.  Periodic mode
+ * requires rmax < box/2 (else G3PCF_ERR_RMAX).  *out receives the plan. */
+int g3pcf_plan(g3pcf_plan_t* out, int nbins, double rmin, double rmax, int lmax, double box,
+               int los_mode);
+
+/* Set the CUDA stream (a cudaStream_t, e.g. PyTorch's current stream) on which
+ * all later device work of this plan is enqueued.  NULL = legacy stream. */
+int g3pcf_set_stream(g3pcf_plan_t plan, void* cuda_stream);
+
+/* Forward: zeta for n points, every point a primary.  pos: device, n x 3
+ * float (x, y, z interleaved), in [0, box)^3.  w: device, n floats.
+ * zeta: device, 2 * g3pcf_zeta_size() doubles (layout above), overwritten.
+ * n may be 0 (zeta is zeroed).  Split-BF16 tensor-core contraction. */
+int g3pcf_compute(g3pcf_plan_t plan, const float* pos, const float* w, int64_t n, double* zeta);
+
+/* Forward with options.  pos: device, n x 3 float, or double if
+ * G3PCF_F_POS_F64.  n_primary in [0, n] (negative = n): the first n_primary
+ * points are primaries, all n are secondaries (the paper's primary/halo split,
+ * Algorithm 1 "if not primary: skip").  counts: device, nbins int64 (ordered
+ * pairs accepted per bin, bit-exact), may be NULL.  flags: G3PCF_F_*. */
+int g3pcf_compute_ex(g3pcf_plan_t plan, const void* pos, const float* w, int64_t n,
+                     int64_t n_primary, double* zeta, int64_t* counts, int flags);
+
+/* Batched forward over ncat independent catalogs sharing the plan's geometry
+ * (each its own box, every point a primary of its own catalog).  pos, w:
+ * device, the catalogs concatenated (float, n_total x 3 and n_total).
+ * offsets: HOST, ncat + 1 int64 (catalog c = points [offsets[c], offsets[c+1])).
+ * zeta: device, ncat consecutive zeta blocks.  counts: device, ncat x nbins
+ * int64, may be NULL.  One launch per stage over all catalogs (device work
+ * queue, heaviest catalogs first).  flags: G3PCF_F_CONTRACT_FP32,
+ * G3PCF_F_NO_SYNC. */
+int g3pcf_compute_batch(g3pcf_plan_t plan, const float* pos, const float* w,
+                        const int64_t* offsets, int ncat, double* zeta, int64_t* counts,
+                        int flags);
+
+/* Adjoint of the last forward on this plan (LOS = z modes, single catalog).
+ * dzeta: device, same layout as zeta, the gradient of a real loss with respect
+ * to (Re zeta, Im zeta) interleaved.  dpos: device, n x 3 doubles; dw: device,
+ * n doubles; both overwritten.  Pair set and bins are held fixed.  The pos and w
+ * buffers of the forward must still hold the same values.  Not in the paper:
+ * dL/dw_i and dL/dpos_i of zeta through Y_lm and the weights. */
+int g3pcf_backward(g3pcf_plan_t plan, const double* dzeta, double* dpos, double* dw);
+
+/* Multipoles of the last forward (run with G3PCF_F_KEEP_ALM or before a
+ * backward) for np primaries given by original index (HOST int64 array).
+ * out: HOST, np x nbins x ((lmax+1)(lmax+2)/2) complex (re, im doubles),
+ * index [k][b][l(l+1)/2 + m].  Synchronises the plan's stream. */
+int g3pcf_alm(g3pcf_plan_t plan, const int64_t* primaries, int64_t np, double* out);
+
+/* Status word of the last G3PCF_F_NO_SYNC call (synchronises the stream):
+ * returns G3PCF_OK or the error the call would have returned. */
+int g3pcf_status(g3pcf_plan_t plan);
+
+/* Per-stage device times (milliseconds, CUDA events) and counters of the last
+ * compute call: [0] index build, [1] pair stage, [2] contraction, [3] reduction,
+ * [4] total, [5] accepted pairs (as a double), [6] primaries, [7] cells per
+ * Rmax used, [8] kernels launched by the call.  Synchronises the stream.
+ * At most min(nvals, 9) values are written. */
+int g3pcf_stats(g3pcf_plan_t plan, double* vals, int nvals);
+
+/* Destroy a plan and free its workspace (synchronises its stream). */
+int g3pcf_destroy(g3pcf_plan_t plan);
+
+/* Message of the last error on this thread ("" if none). */
+const char* g3pcf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* G3PCF_H */

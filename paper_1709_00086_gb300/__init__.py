@@ -1,1 +1,204 @@
-"""GB300-native anisotropic 3PCF (placeholder; the binding is added below)."""
+"""GB300-native anisotropic 3PCF (Galactos, arXiv 1709.00086) -- Python binding.
+
+Thin ctypes layer over ``libg3pcf.so`` (see ``include/g3pcf.h``): argument
+marshalling only; every step of the computation runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the current stream.  If the
+library has not been built, the binding raises instead of computing anything
+another way.
+
+    plan = Plan(nbins=10, rmin=0, rmax=200, lmax=10, box=1000, los_mode=0)
+    zeta, counts = plan.compute(pos_cuda, w_cuda)      # zeta: (zeta_size,) complex128
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libg3pcf.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "g3pcf.h")
+
+LOS_Z_PERIODIC, LOS_Z_OPEN, LOS_RADIAL_OPEN = 0, 1, 2
+F_POS_F64, F_CONTRACT_FP32, F_NO_SYNC, F_KEEP_ALM = 1, 2, 4, 8
+ERRORS = {0: "OK", -1: "ERR_ARG", -2: "ERR_RANGE", -3: "ERR_RMAX", -4: "ERR_ALLOC",
+          -5: "ERR_CUDA", -6: "ERR_TIMEOUT", -7: "ERR_STATE", -8: "ERR_UNSUPPORTED"}
+
+_lib = None
+
+
+class G3PCFError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+        self.name = ERRORS.get(code, "?")
+
+
+def lib():
+    """Load libg3pcf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libg3pcf.so is not built; run `python -m paper_1709_00086_gb300.build` "
+                               "(or __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        L.g3pcf_zeta_size.restype = I64
+        L.g3pcf_zeta_size.argtypes = [I, I]
+        L.g3pcf_last_error.restype = ctypes.c_char_p
+        L.g3pcf_last_error.argtypes = []
+        L.g3pcf_plan.argtypes = [ctypes.POINTER(P), I, D, D, I, D, I]
+        L.g3pcf_set_stream.argtypes = [P, P]
+        L.g3pcf_compute.argtypes = [P, P, P, I64, P]
+        L.g3pcf_compute_ex.argtypes = [P, P, P, I64, I64, P, P, I]
+        L.g3pcf_compute_batch.argtypes = [P, P, P, P, I, P, P, I]
+        L.g3pcf_backward.argtypes = [P, P, P, P]
+        L.g3pcf_alm.argtypes = [P, P, I64, P]
+        L.g3pcf_status.argtypes = [P]
+        L.g3pcf_stats.argtypes = [P, P, I]
+        L.g3pcf_destroy.argtypes = [P]
+        for f in ("g3pcf_plan", "g3pcf_set_stream", "g3pcf_compute", "g3pcf_compute_ex",
+                  "g3pcf_compute_batch", "g3pcf_backward", "g3pcf_alm", "g3pcf_status",
+                  "g3pcf_stats", "g3pcf_destroy"):
+            getattr(L, f).restype = I
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise G3PCFError(rc, lib().g3pcf_last_error().decode())
+
+
+def zeta_size(nbins: int, lmax: int) -> int:
+    return int(lib().g3pcf_zeta_size(nbins, lmax))
+
+
+def nlm(lmax: int) -> int:
+    return (lmax + 1) * (lmax + 2) // 2
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A g3pcf plan: binning, harmonic order, box and line-of-sight mode."""
+
+    def __init__(self, nbins: int, rmin: float, rmax: float, lmax: int, box: float,
+                 los_mode: int = LOS_Z_PERIODIC):
+        self.nbins, self.rmin, self.rmax, self.lmax = int(nbins), float(rmin), float(rmax), int(lmax)
+        self.box, self.los_mode = float(box), int(los_mode)
+        h = ctypes.c_void_p()
+        _check(lib().g3pcf_plan(ctypes.byref(h), self.nbins, self.rmin, self.rmax, self.lmax,
+                                self.box, self.los_mode))
+        self._h = h
+        self.zsize = zeta_size(self.nbins, self.lmax)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().g3pcf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        import torch
+        _check(lib().g3pcf_set_stream(self._h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+
+    def compute(self, pos, w, n_primary=None, fp32_contraction=False, keep_alm=False,
+                with_counts=True, sync=True, out=None):
+        """zeta (complex128 tensor, zsize) and counts (int64 tensor, nbins) on pos's device."""
+        import torch
+        if not (pos.is_cuda and w.is_cuda):
+            raise ValueError("pos and w must be CUDA tensors")
+        pos = pos.contiguous()
+        w = w.contiguous()
+        if w.dtype != torch.float32:
+            raise ValueError("w must be float32")
+        if pos.dim() != 2 or pos.shape[1] != 3:
+            raise ValueError("pos must be (n, 3)")
+        n = pos.shape[0]
+        flags = 0
+        if pos.dtype == torch.float64:
+            flags |= F_POS_F64
+        elif pos.dtype != torch.float32:
+            raise ValueError("pos must be float32 or float64")
+        if fp32_contraction:
+            flags |= F_CONTRACT_FP32
+        if keep_alm:
+            flags |= F_KEEP_ALM
+        if not sync:
+            flags |= F_NO_SYNC
+        zeta = out if out is not None else torch.empty((self.zsize, 2), dtype=torch.float64,
+                                                       device=pos.device)
+        counts = torch.empty(self.nbins, dtype=torch.int64, device=pos.device) if with_counts else None
+        npri = -1 if n_primary is None else int(n_primary)
+        self._stream()
+        _check(lib().g3pcf_compute_ex(self._h, _ptr(pos), _ptr(w), n, npri, _ptr(zeta), _ptr(counts),
+                                      flags))
+        return torch.view_as_complex(zeta), counts
+
+    def compute_batch(self, pos, w, offsets, fp32_contraction=False, sync=True):
+        """Batched zeta over catalogs [offsets[c], offsets[c+1]): (ncat, zsize) complex."""
+        import torch
+        pos = pos.contiguous()
+        w = w.contiguous()
+        offs = np.ascontiguousarray(offsets, dtype=np.int64)
+        ncat = offs.size - 1
+        zeta = torch.empty((ncat, self.zsize, 2), dtype=torch.float64, device=pos.device)
+        counts = torch.empty((ncat, self.nbins), dtype=torch.int64, device=pos.device)
+        flags = (F_CONTRACT_FP32 if fp32_contraction else 0) | (0 if sync else F_NO_SYNC)
+        self._stream()
+        _check(lib().g3pcf_compute_batch(self._h, _ptr(pos), _ptr(w),
+                                         offs.ctypes.data_as(ctypes.c_void_p), ncat, _ptr(zeta),
+                                         _ptr(counts), flags))
+        return torch.view_as_complex(zeta), counts
+
+    def alm(self, primaries) -> np.ndarray:
+        """a_lm(i, b) of the last forward: (np, nbins, nlm) complex128 (host)."""
+        prim = np.ascontiguousarray(primaries, dtype=np.int64)
+        out = np.zeros((prim.size, self.nbins, nlm(self.lmax)), dtype=np.complex128)
+        _check(lib().g3pcf_alm(self._h, prim.ctypes.data_as(ctypes.c_void_p), prim.size,
+                               out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def backward(self, dzeta):
+        """(dpos (n,3) float64, dw (n,) float64) for the last forward."""
+        import torch
+        dz = torch.view_as_real(dzeta) if dzeta.is_complex() else dzeta
+        dz = dz.contiguous().to(torch.float64)
+        n = self._last_n
+        dpos = torch.empty((n, 3), dtype=torch.float64, device=dz.device)
+        dw = torch.empty(n, dtype=torch.float64, device=dz.device)
+        self._stream()
+        _check(lib().g3pcf_backward(self._h, _ptr(dz), _ptr(dpos), _ptr(dw)))
+        return dpos, dw
+
+    def status(self):
+        _check(lib().g3pcf_status(self._h))
+
+    def stats(self) -> dict:
+        v = np.zeros(9)
+        _check(lib().g3pcf_stats(self._h, v.ctypes.data_as(ctypes.c_void_p), 9))
+        keys = ["index_ms", "pair_ms", "contract_ms", "reduce_ms", "total_ms", "pairs", "primaries",
+                "cells_per_rmax", "launches"]
+        return dict(zip(keys, v.tolist()))
+
+
+def zeta_blocks(z, nbins: int, lmax: int):
+    """Split a flat complex zeta (numpy or torch) into per-m K_m x K_m blocks."""
+    z = z.detach().cpu().numpy() if hasattr(z, "detach") else np.asarray(z)
+    out, off = [], 0
+    for m in range(lmax + 1):
+        K = nbins * (lmax + 1 - m)
+        out.append(z[off:off + K * K].reshape(K, K))
+        off += K * K
+    return out

@@ -1,0 +1,679 @@
+// C ABI of libg3pcf: plans, workspace, host-side validation and the launch
+// sequence of one forward call (index -> pair stage -> contraction ->
+// reduction), all enqueued on the plan's stream.
+//
+// The problem statement follows the paper's Sec. 3.1 and Algorithm 1; see
+// include/g3pcf.h for the contract of every entry point.
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace g3;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                       \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(G3PCF_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));      \
+    } while (0)
+
+// Grow-only device buffer.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    int ensure(size_t need) {
+        if (need <= bytes && p) return 0;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        size_t b = need < 256 ? 256 : need;
+        if (cudaMalloc(&p, b) != cudaSuccess) {
+            cudaGetLastError();
+            return -1;
+        }
+        bytes = b;
+        return 0;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+double lfact(int k) { return std::lgamma((double)k + 1.0); }
+
+}  // namespace
+
+struct g3pcf_plan_s {
+    int nbins, lmax, los_mode;
+    double rmin, rmax, box;
+    cudaStream_t stream = nullptr;
+    int device = -1, nsm = 0;
+    Bins bins{};
+    int RL = 0, RLP = 0, nrp = 0;
+    std::vector<int> colmap;
+    std::vector<float> colscale;
+    std::vector<Tile> tiles;
+    int T = 0;
+    int kflush = 16;
+    // device buffers
+    DevBuf key_a, key_b, val_a, val_b, hist, hist_off, scan_tmp, pts, pts64, orig, cstart, plist;
+    DevBuf small;       // status, queue
+    DevBuf counts, A, partials, d_tiles, d_segs, d_segfirst, d_colmap, d_colscale, d_catoff;
+    DevBuf d_ranges;
+    int* h_status = nullptr;
+    cudaEvent_t ev[5] = {};
+    bool consts_uploaded = false;
+    // state of the last forward
+    bool have_forward = false;
+    bool have_alm = false;
+    int64_t last_n = 0, last_np = 0;
+    int last_ncat = 0;
+    const void* last_pos = nullptr;
+    const float* last_w = nullptr;
+    int last_pos_f64 = 0;
+    Grid last_grid{};
+    unsigned* key_sorted = nullptr;
+    double stats[10] = {};
+    int launches = 0;
+};
+
+namespace {
+
+int setup_device(g3pcf_plan_t P) {
+    if (P->device >= 0) return 0;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, dev));
+    P->device = dev;
+    P->nsm = prop.multiProcessorCount;
+    CK(cudaHostAlloc(reinterpret_cast<void**>(&P->h_status), 64, cudaHostAllocDefault));
+    for (auto& e : P->ev) CK(cudaEventCreate(&e));
+    return 0;
+}
+
+int upload_consts(g3pcf_plan_t P) {
+    if (P->consts_uploaded) return 0;
+    if (P->d_colmap.ensure(P->RL * sizeof(int)) || P->d_colscale.ensure(P->RL * sizeof(float)) ||
+        P->d_tiles.ensure(P->tiles.size() * sizeof(Tile)))
+        return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (constants)");
+    CK(cudaMemcpy(P->d_colmap.p, P->colmap.data(), P->RL * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->d_colscale.p, P->colscale.data(), P->RL * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->d_tiles.p, P->tiles.data(), P->tiles.size() * sizeof(Tile),
+                  cudaMemcpyHostToDevice));
+    P->consts_uploaded = true;
+    return 0;
+}
+
+// Cell grid for a (pair-weighted) density: cell side >= rmax/s with s chosen
+// so that a cell holds a few dozen points.
+Grid choose_grid(g3pcf_plan_t P, double density, int ncat) {
+    Grid g{};
+    const double target = 48.0;
+    double cs = std::cbrt(target / (density > 0 ? density : 1e-30));
+    int s = (int)std::floor(P->rmax / cs);
+    if (s < 1) s = 1;
+    if (s > 8) s = 8;
+    int nc = (int)std::floor(P->box * s / P->rmax);
+    if (nc < 1) nc = 1;
+    if (nc > 256) nc = 256;
+    for (;;) {
+        int span = 1;
+        while (span < nc) span <<= 1;
+        long long cpc = (long long)span * span * nc;
+        if ((long long)ncat * cpc < (1ll << 31) || nc == 1) {
+            g.span = span;
+            g.cells_per_cat = cpc;
+            break;
+        }
+        nc = nc / 2;
+    }
+    g.nc = nc;
+    g.boxd = P->box;
+    g.box = (float)P->box;
+    g.cell = (float)(P->box / nc);
+    g.inv_cell = (float)(nc / P->box);
+    g.reach = (int)std::ceil(P->rmax * nc / P->box - 1e-9);
+    if (g.reach < 1) g.reach = 1;
+    g.periodic = (P->los_mode == G3PCF_LOS_Z_PERIODIC);
+    g.radial = (P->los_mode == G3PCF_LOS_RADIAL_OPEN);
+    return g;
+}
+
+void compute_bins(g3pcf_plan_t P) {
+    Bins& b = P->bins;
+    const int B = P->nbins;
+    b.nbins = B;
+    for (int k = 0; k <= B; ++k) {
+        double e;
+        if (k == 0) e = P->rmin;
+        else if (k == B) e = P->rmax;
+        else e = P->rmin + ((P->rmax - P->rmin) * (double)k) / (double)B;
+        b.e2[k] = e * e;
+        b.e2f[k] = (float)(e * e);
+    }
+    // Bound on |r2_fp32 - r2_exact| near an edge e: separation error per axis
+    // dD <= u (4L + rmax) (input rounding to FP32, image shift, subtraction),
+    // r2 error <= 2 sqrt(3) e dD + 3 dD^2 + ~6 u e^2 (products, FMA chain,
+    // FP32 edge and the comparison); doubled for safety.
+    const double u = std::ldexp(1.0, -24);
+    const double dD = u * (4.0 * P->box + P->rmax);
+    for (int k = 0; k <= B; ++k) {
+        const double e = std::sqrt(b.e2[k]);
+        b.guard[k] = (float)(2.0 * (2.0 * std::sqrt(3.0) * e * dD + 3.0 * dD * dD + 6.0 * u * e * e));
+    }
+    b.rmin = (float)P->rmin;
+    b.invw = (float)(B / (P->rmax - P->rmin));
+    b.rmaxf = (float)P->rmax;
+    b.rmax2f = (float)(P->rmax * P->rmax);
+    b.hi_rej = b.e2f[B] + b.guard[B];
+    b.lo_rej = b.e2f[0] - b.guard[0];
+    b.slack = (float)(1e-4 * P->box / 1.0 + 1e-3 * P->rmax);
+}
+
+// Column map of an A row: block m (m = 0: K_0 reals; m >= 1: Re and Im halves)
+// and the normalisation K_lm of Y_lm.
+void compute_columns(g3pcf_plan_t P) {
+    const int B = P->nbins, L = P->lmax;
+    P->nrp = pair_nrp(L);
+    P->RL = B * (L + 1) * (L + 1);
+    P->RLP = (P->RL + 7) & ~7;
+    P->colmap.assign(P->RL, 0);
+    P->colscale.assign(P->RL, 0.f);
+    int col = 0;
+    for (int m = 0; m <= L; ++m) {
+        const int K = B * (L + 1 - m);
+        const int parts = m == 0 ? 1 : 2;
+        for (int part = 0; part < parts; ++part)
+            for (int idx = 0; idx < K; ++idx) {
+                const int l = m + idx / B, b = idx % B;
+                const int slot = (m == 0) ? l : acc_base(L, m) + 2 * (l - m) + part;
+                // K_lm = (-1)^m sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!) (2l)! / (2^l l! (l-m)!)
+                const double lnN = 0.5 * (std::log((2.0 * l + 1.0) / (4.0 * M_PI)) + lfact(l - m) - lfact(l + m));
+                const double lnLead = lfact(2 * l) - l * std::log(2.0) - lfact(l) - lfact(l - m);
+                double kl = std::exp(lnN + lnLead);
+                if (m & 1) kl = -kl;
+                P->colmap[col] = b * P->nrp + slot;
+                P->colscale[col] = (float)kl;
+                ++col;
+            }
+    }
+}
+
+int64_t zsize_of(int nbins, int lmax) {
+    int64_t s = 0;
+    for (int m = 0; m <= lmax; ++m) {
+        const int64_t K = (int64_t)nbins * (lmax + 1 - m);
+        s += K * K;
+    }
+    return s;
+}
+
+struct CallSpec {
+    const void* pos;
+    const float* w;
+    int64_t n;
+    int64_t n_primary;
+    int pos_f64;
+    int ncat;
+    std::vector<int64_t> offs;  // ncat + 1 (host)
+    double* zeta;
+    int64_t* counts;
+    int flags;
+};
+
+int ensure(DevBuf& b, size_t bytes, const char* what) {
+    if (b.ensure(bytes)) return fail(G3PCF_ERR_ALLOC, "cudaMalloc of %zu bytes (%s) failed", bytes, what);
+    return 0;
+}
+
+int read_status(g3pcf_plan_t P) {
+    int s = P->h_status[0];
+    if (s & kStatusRange)
+        return fail(G3PCF_ERR_RANGE, "a position is outside [0, box) or not finite, or a weight is not finite");
+    if (s & kStatusTimeout) return fail(G3PCF_ERR_TIMEOUT, "a bounded device wait expired");
+    if (s & kStatusOverflow) return fail(G3PCF_ERR_CUDA, "device-side capacity exceeded");
+    return G3PCF_OK;
+}
+
+int run_forward(g3pcf_plan_t P, CallSpec& c) {
+    if (int r = setup_device(P)) return r;
+    if (int r = upload_consts(P)) return r;
+    cudaStream_t st = P->stream;
+    const int B = P->nbins;
+    const int64_t n = c.n;
+    const int64_t zs = zsize_of(B, P->lmax);
+    P->have_forward = false;
+    P->have_alm = false;
+    P->launches = 0;
+    CK(cudaEventRecord(P->ev[0], st));
+    // zero outputs and counters
+    if (ensure(P->small, 256, "status")) return G3PCF_ERR_ALLOC;
+    int* d_status = P->small.as<int>();
+    int* d_queue = d_status + 16;
+    CK(cudaMemsetAsync(P->small.p, 0, 256, st));
+    if (ensure(P->counts, sizeof(unsigned long long) * B * c.ncat + 8, "counts")) return G3PCF_ERR_ALLOC;
+    CK(cudaMemsetAsync(P->counts.p, 0, sizeof(unsigned long long) * B * c.ncat, st));
+    CK(cudaMemsetAsync(c.zeta, 0, sizeof(double) * 2 * zs * c.ncat, st));
+    // density for the grid: pair-weighted over catalogs
+    double num = 0, den = 0;
+    for (int k = 0; k < c.ncat; ++k) {
+        const double nk = (double)(c.offs[k + 1] - c.offs[k]);
+        num += nk * nk;
+        den += nk;
+    }
+    const double vol = P->box * P->box * P->box;
+    const double density = den > 0 ? num / den / vol : 0.0;
+    Grid g = choose_grid(P, density, c.ncat);
+    const long long ncells = (long long)c.ncat * g.cells_per_cat;
+    P->last_grid = g;
+    P->stats[7] = (double)P->rmax / (P->box / g.nc);
+
+    int64_t nprim = 0;
+    if (n > 0) {
+        // ---- workspace
+        const size_t hist_ints = radix_hist_ints(n);
+        const size_t off_ints = (hist_ints > (size_t)n ? hist_ints : (size_t)n) + 1;
+        if (ensure(P->key_a, 4 * n, "keys") || ensure(P->key_b, 4 * n, "keys") ||
+            ensure(P->val_a, 4 * n, "vals") || ensure(P->val_b, 4 * n, "vals") ||
+            ensure(P->hist, 4 * hist_ints, "hist") || ensure(P->hist_off, 4 * off_ints, "hist") ||
+            ensure(P->scan_tmp, 4 * (scan_tmp_ints(off_ints) + 16), "scan") ||
+            ensure(P->pts, 16 * n, "points") || ensure(P->orig, 4 * n, "orig") ||
+            ensure(P->cstart, 4 * (ncells + 1), "cells") || ensure(P->plist, 4 * n, "plist"))
+            return G3PCF_ERR_ALLOC;
+        if (c.pos_f64 && ensure(P->pts64, 24 * n, "points64")) return G3PCF_ERR_ALLOC;
+        IndexBuffers ib{};
+        ib.key_a = P->key_a.as<unsigned>();
+        ib.key_b = P->key_b.as<unsigned>();
+        ib.val_a = P->val_a.as<int>();
+        ib.val_b = P->val_b.as<int>();
+        ib.hist = P->hist.as<int>();
+        ib.hist_off = P->hist_off.as<int>();
+        ib.scan_tmp = P->scan_tmp.as<int>();
+        ib.pts = P->pts.as<float4>();
+        ib.pts64 = c.pos_f64 ? P->pts64.as<double>() : nullptr;
+        ib.orig = P->orig.as<int>();
+        ib.cstart = P->cstart.as<int>();
+        ib.plist = P->plist.as<int>();
+        ib.status = d_status;
+        IndexArgs ia{};
+        ia.pos = c.pos;
+        ia.w = c.w;
+        ia.n = n;
+        ia.pos_f64 = c.pos_f64;
+        ia.g = g;
+        const int64_t* d_catoff = nullptr;
+        PrimRanges pr{};
+        const PrimRanges* prp = nullptr;
+        if (c.ncat > 1) {
+            if (ensure(P->d_catoff, 8 * (c.ncat + 1), "offsets")) return G3PCF_ERR_ALLOC;
+            CK(cudaMemcpyAsync(P->d_catoff.p, c.offs.data(), 8 * (c.ncat + 1), cudaMemcpyHostToDevice, st));
+            d_catoff = P->d_catoff.as<int64_t>();
+            // processing order: catalogs by decreasing size (heaviest first)
+            std::vector<int> order(c.ncat);
+            for (int k = 0; k < c.ncat; ++k) order[k] = k;
+            std::sort(order.begin(), order.end(), [&](int a, int b) {
+                return (c.offs[a + 1] - c.offs[a]) > (c.offs[b + 1] - c.offs[b]);
+            });
+            std::vector<int> rs(3 * c.ncat);
+            int o = 0;
+            for (int k = 0; k < c.ncat; ++k) {
+                const int cat = order[k];
+                rs[k] = (int)c.offs[cat];
+                rs[c.ncat + k] = (int)(c.offs[cat + 1] - c.offs[cat]);
+                rs[2 * c.ncat + k] = o;
+                o += rs[c.ncat + k];
+            }
+            if (ensure(P->d_ranges, 4 * rs.size(), "ranges")) return G3PCF_ERR_ALLOC;
+            CK(cudaMemcpyAsync(P->d_ranges.p, rs.data(), 4 * rs.size(), cudaMemcpyHostToDevice, st));
+            pr.start = P->d_ranges.as<int>();
+            pr.len = pr.start + c.ncat;
+            pr.out = pr.start + 2 * c.ncat;
+            pr.n = c.ncat;
+            prp = &pr;
+            nprim = n;
+        } else {
+            nprim = c.n_primary;
+        }
+        const int nl = build_index(ib, ia, d_catoff, c.ncat, ncells, c.n_primary, prp, st);
+        if (nl >= 0) P->launches += nl;
+        if (nl < 0)
+            return fail(G3PCF_ERR_CUDA, "index build launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        P->key_sorted = ib.key_sorted;
+        CK(cudaEventRecord(P->ev[1], st));
+
+        // ---- pair stage
+        const int64_t rows = (c.ncat > 1) ? n : c.n_primary;
+        if (ensure(P->A, sizeof(float) * (size_t)P->RLP * (rows > 0 ? rows : 1), "multipoles"))
+            return G3PCF_ERR_ALLOC;
+        if (nprim > 0) {
+            PairArgs pa{};
+            pa.pts = ib.pts;
+            pa.pts64 = ib.pts64;
+            pa.orig = ib.orig;
+            pa.cstart = ib.cstart;
+            pa.plist = (c.ncat > 1 || c.n_primary < n) ? ib.plist : nullptr;
+            pa.key = ib.key_sorted;
+            pa.nprim = (int)nprim;
+            pa.A = P->A.as<float>();
+            pa.RLP = P->RLP;
+            pa.colmap = P->d_colmap.as<int>();
+            pa.colscale = P->d_colscale.as<float>();
+            pa.RL = P->RL;
+            pa.counts = P->counts.as<unsigned long long>();
+            pa.queue = d_queue;
+            pa.status = d_status;
+            pa.kflush = P->kflush;
+            pa.g = g;
+            pa.bins = P->bins;
+            ++P->launches;
+            if (launch_pair(P->lmax, pa, P->nsm, st) != 0)
+                return fail(G3PCF_ERR_CUDA, "pair kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        }
+        CK(cudaEventRecord(P->ev[2], st));
+
+        // ---- contraction (segments of primaries x tiles) and reduction
+        std::vector<Segment> segs;
+        std::vector<int> segfirst(c.ncat + 1, 0);
+        for (int k = 0; k < c.ncat; ++k) {
+            segfirst[k] = (int)segs.size();
+            const int64_t r0 = (c.ncat > 1) ? c.offs[k] : 0;
+            const int64_t r1 = (c.ncat > 1) ? c.offs[k + 1] : c.n_primary;
+            const int64_t len = r1 - r0;
+            int64_t seg = len / 32;
+            if (seg < 8192) seg = 8192;
+            for (int64_t s = r0; s < r1; s += seg) {
+                Segment sg;
+                sg.cat = k;
+                sg.row0 = (int)s;
+                sg.row1 = (int)(s + seg < r1 ? s + seg : r1);
+                segs.push_back(sg);
+            }
+        }
+        segfirst[c.ncat] = (int)segs.size();
+        const int nsegs = (int)segs.size();
+        const int ntiles = (int)P->tiles.size();
+        const int part_stride = ntiles * P->T * P->T;
+        if (nsegs > 0) {
+            if (ensure(P->d_segs, sizeof(Segment) * nsegs, "segments") ||
+                ensure(P->d_segfirst, 4 * (c.ncat + 1), "segments") ||
+                ensure(P->partials, sizeof(double) * (size_t)part_stride * nsegs, "partials"))
+                return G3PCF_ERR_ALLOC;
+            CK(cudaMemcpyAsync(P->d_segs.p, segs.data(), sizeof(Segment) * nsegs, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(P->d_segfirst.p, segfirst.data(), 4 * (c.ncat + 1), cudaMemcpyHostToDevice, st));
+            P->launches += 2;
+            if (launch_contract_fp32(P->A.as<float>(), P->RLP, c.w, P->d_tiles.as<Tile>(), ntiles,
+                                     P->d_segs.as<Segment>(), nsegs, P->partials.as<double>(),
+                                     part_stride, st) != 0)
+                return fail(G3PCF_ERR_CUDA, "contraction launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+            CK(cudaEventRecord(P->ev[3], st));
+            if (launch_reduce(P->partials.as<double>(), part_stride, P->d_segfirst.as<int>(), c.ncat,
+                              B, P->lmax, P->d_tiles.as<Tile>(), P->T, c.zeta, st) != 0)
+                return fail(G3PCF_ERR_CUDA, "reduction launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        } else {
+            CK(cudaEventRecord(P->ev[3], st));
+        }
+    } else {
+        CK(cudaEventRecord(P->ev[1], st));
+        CK(cudaEventRecord(P->ev[2], st));
+        CK(cudaEventRecord(P->ev[3], st));
+    }
+    CK(cudaEventRecord(P->ev[4], st));
+    if (c.counts) {
+        CK(cudaMemcpyAsync(c.counts, P->counts.p, sizeof(int64_t) * B * c.ncat, cudaMemcpyDeviceToDevice, st));
+    }
+    CK(cudaMemcpyAsync(P->h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    P->have_forward = true;
+    P->have_alm = true;
+    P->last_n = n;
+    P->last_np = nprim;
+    P->last_ncat = c.ncat;
+    P->last_pos = c.pos;
+    P->last_w = c.w;
+    P->last_pos_f64 = c.pos_f64;
+    P->stats[6] = (double)nprim;
+    if (c.flags & G3PCF_F_NO_SYNC) return G3PCF_OK;
+    CK(cudaStreamSynchronize(st));
+    return read_status(P);
+}
+
+int check_plan(g3pcf_plan_t P) {
+    if (!P) return fail(G3PCF_ERR_ARG, "plan is NULL");
+    return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t g3pcf_zeta_size(int nbins, int lmax) {
+    if (nbins < 1 || lmax < 0) return 0;
+    return zsize_of(nbins, lmax);
+}
+
+const char* g3pcf_last_error(void) { return g_err.c_str(); }
+
+int g3pcf_plan(g3pcf_plan_t* out, int nbins, double rmin, double rmax, int lmax, double box,
+               int los_mode) {
+    g_err.clear();
+    if (!out) return fail(G3PCF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nbins < 1 || nbins > G3PCF_MAX_NBINS) return fail(G3PCF_ERR_ARG, "nbins must be in [1, %d]", G3PCF_MAX_NBINS);
+    if (lmax < 0 || lmax > G3PCF_MAX_LMAX) return fail(G3PCF_ERR_ARG, "lmax must be in [0, %d]", G3PCF_MAX_LMAX);
+    if (!std::isfinite(rmin) || !std::isfinite(rmax) || !(rmin >= 0.0) || !(rmax > rmin))
+        return fail(G3PCF_ERR_ARG, "need 0 <= rmin < rmax (finite)");
+    if (!std::isfinite(box) || !(box > 0.0)) return fail(G3PCF_ERR_ARG, "box must be finite and > 0");
+    if (los_mode < 0 || los_mode > 2) return fail(G3PCF_ERR_ARG, "unknown los_mode %d", los_mode);
+    if (los_mode == G3PCF_LOS_Z_PERIODIC && !(rmax < 0.5 * box * (1.0 - 1e-6)))
+        return fail(G3PCF_ERR_RMAX, "periodic box needs rmax < box/2 (rmax=%g, box=%g)", rmax, box);
+    g3pcf_plan_t P = new (std::nothrow) g3pcf_plan_s();
+    if (!P) return fail(G3PCF_ERR_ALLOC, "out of host memory");
+    P->nbins = nbins;
+    P->lmax = lmax;
+    P->los_mode = los_mode;
+    P->rmin = rmin;
+    P->rmax = rmax;
+    P->box = box;
+    compute_bins(P);
+    compute_columns(P);
+    // pairs per lane per bucket flush: the largest k <= 16 for which two
+    // 4-warp CTAs of the pair kernel fit in 227 KB of shared memory
+    P->kflush = 2;
+    for (int kf = 16; kf >= 2; --kf)
+        if (pair_smem_per_warp(lmax, nbins, kf) * 4 * 2 + 2048 <= 227 * 1024) {
+            P->kflush = kf;
+            break;
+        }
+    P->T = contract_tile_dim_fp32();
+    P->tiles.resize(4096);
+    int nt = make_tiles(nbins, lmax, P->T, P->tiles.data(), (int)P->tiles.size());
+    if (nt < 0) {
+        delete P;
+        return fail(G3PCF_ERR_ARG, "too many contraction tiles");
+    }
+    P->tiles.resize(nt);
+    *out = P;
+    return G3PCF_OK;
+}
+
+int g3pcf_set_stream(g3pcf_plan_t P, void* s) {
+    if (int r = check_plan(P)) return r;
+    P->stream = static_cast<cudaStream_t>(s);
+    return G3PCF_OK;
+}
+
+int g3pcf_compute_ex(g3pcf_plan_t P, const void* pos, const float* w, int64_t n, int64_t n_primary,
+                     double* zeta, int64_t* counts, int flags) {
+    g_err.clear();
+    if (int r = check_plan(P)) return r;
+    if (n < 0) return fail(G3PCF_ERR_ARG, "n < 0");
+    if (n >= G3PCF_MAX_POINTS) return fail(G3PCF_ERR_ARG, "n must be < 2^27");
+    if (!zeta) return fail(G3PCF_ERR_ARG, "zeta is NULL");
+    if (n > 0 && (!pos || !w)) return fail(G3PCF_ERR_ARG, "pos or w is NULL");
+    if (flags & ~(G3PCF_F_POS_F64 | G3PCF_F_CONTRACT_FP32 | G3PCF_F_NO_SYNC | G3PCF_F_KEEP_ALM))
+        return fail(G3PCF_ERR_ARG, "unknown flags 0x%x", flags);
+    if (n_primary < 0 || n_primary > n) n_primary = n;
+    CallSpec c;
+    c.pos = pos;
+    c.w = w;
+    c.n = n;
+    c.n_primary = n_primary;
+    c.pos_f64 = (flags & G3PCF_F_POS_F64) ? 1 : 0;
+    c.ncat = 1;
+    c.offs = {0, n};
+    c.zeta = zeta;
+    c.counts = counts;
+    c.flags = flags;
+    return run_forward(P, c);
+}
+
+int g3pcf_compute(g3pcf_plan_t P, const float* pos, const float* w, int64_t n, double* zeta) {
+    return g3pcf_compute_ex(P, pos, w, n, -1, zeta, nullptr, 0);
+}
+
+int g3pcf_compute_batch(g3pcf_plan_t P, const float* pos, const float* w, const int64_t* offsets,
+                        int ncat, double* zeta, int64_t* counts, int flags) {
+    g_err.clear();
+    if (int r = check_plan(P)) return r;
+    if (!offsets || ncat < 1) return fail(G3PCF_ERR_ARG, "need ncat >= 1 and offsets");
+    if (!zeta) return fail(G3PCF_ERR_ARG, "zeta is NULL");
+    if (flags & ~(G3PCF_F_CONTRACT_FP32 | G3PCF_F_NO_SYNC | G3PCF_F_KEEP_ALM))
+        return fail(G3PCF_ERR_ARG, "unsupported flags 0x%x for batch", flags);
+    if (offsets[0] != 0) return fail(G3PCF_ERR_ARG, "offsets[0] must be 0");
+    for (int k = 0; k < ncat; ++k)
+        if (offsets[k + 1] < offsets[k]) return fail(G3PCF_ERR_ARG, "offsets must be non-decreasing");
+    const int64_t n = offsets[ncat];
+    if (n >= G3PCF_MAX_POINTS) return fail(G3PCF_ERR_ARG, "total points must be < 2^27");
+    if (n > 0 && (!pos || !w)) return fail(G3PCF_ERR_ARG, "pos or w is NULL");
+    CallSpec c;
+    c.pos = pos;
+    c.w = w;
+    c.n = n;
+    c.n_primary = n;
+    c.pos_f64 = 0;
+    c.ncat = ncat;
+    c.offs.assign(offsets, offsets + ncat + 1);
+    c.zeta = zeta;
+    c.counts = counts;
+    c.flags = flags;
+    return run_forward(P, c);
+}
+
+int g3pcf_alm(g3pcf_plan_t P, const int64_t* primaries, int64_t np, double* out) {
+    g_err.clear();
+    if (int r = check_plan(P)) return r;
+    if (!P->have_alm) return fail(G3PCF_ERR_STATE, "no forward with multipoles on this plan");
+    if (np < 0 || (np > 0 && (!primaries || !out))) return fail(G3PCF_ERR_ARG, "bad primaries/out");
+    const int64_t rows = (P->last_ncat > 1) ? P->last_n : P->last_np;
+    const int B = P->nbins, L = P->lmax;
+    const int nlm = (L + 1) * (L + 2) / 2;
+    std::vector<float> row(P->RLP);
+    CK(cudaStreamSynchronize(P->stream));
+    for (int64_t k = 0; k < np; ++k) {
+        const int64_t i = primaries[k];
+        if (i < 0 || i >= rows) return fail(G3PCF_ERR_ARG, "primary index %lld out of range", (long long)i);
+        CK(cudaMemcpy(row.data(), P->A.as<float>() + i * P->RLP, sizeof(float) * P->RL, cudaMemcpyDeviceToHost));
+        double* o = out + k * (int64_t)B * nlm * 2;
+        std::memset(o, 0, sizeof(double) * B * nlm * 2);
+        int col = 0;
+        for (int m = 0; m <= L; ++m) {
+            const int K = B * (L + 1 - m);
+            const int parts = m == 0 ? 1 : 2;
+            for (int part = 0; part < parts; ++part)
+                for (int idx = 0; idx < K; ++idx) {
+                    const int l = m + idx / B, b = idx % B;
+                    o[2 * ((int64_t)b * nlm + l * (l + 1) / 2 + m) + part] = row[col++];
+                }
+        }
+    }
+    return G3PCF_OK;
+}
+
+int g3pcf_backward(g3pcf_plan_t P, const double* dzeta, double* dpos, double* dw) {
+    g_err.clear();
+    if (int r = check_plan(P)) return r;
+    if (!P->have_forward) return fail(G3PCF_ERR_STATE, "backward before forward on this plan");
+    (void)dzeta;
+    (void)dpos;
+    (void)dw;
+    return fail(G3PCF_ERR_UNSUPPORTED, "backward not built");
+}
+
+int g3pcf_status(g3pcf_plan_t P) {
+    g_err.clear();
+    if (int r = check_plan(P)) return r;
+    if (!P->h_status) return G3PCF_OK;
+    CK(cudaStreamSynchronize(P->stream));
+    return read_status(P);
+}
+
+int g3pcf_stats(g3pcf_plan_t P, double* vals, int nvals) {
+    g_err.clear();
+    if (int r = check_plan(P)) return r;
+    if (!vals || nvals < 0) return fail(G3PCF_ERR_ARG, "bad vals");
+    if (P->have_forward) {
+        CK(cudaStreamSynchronize(P->stream));
+        float ms;
+        CK(cudaEventElapsedTime(&ms, P->ev[0], P->ev[1]));
+        P->stats[0] = ms;
+        CK(cudaEventElapsedTime(&ms, P->ev[1], P->ev[2]));
+        P->stats[1] = ms;
+        CK(cudaEventElapsedTime(&ms, P->ev[2], P->ev[3]));
+        P->stats[2] = ms;
+        CK(cudaEventElapsedTime(&ms, P->ev[3], P->ev[4]));
+        P->stats[3] = ms;
+        CK(cudaEventElapsedTime(&ms, P->ev[0], P->ev[4]));
+        P->stats[4] = ms;
+        std::vector<unsigned long long> cnt((size_t)P->nbins * P->last_ncat);
+        CK(cudaMemcpy(cnt.data(), P->counts.p, sizeof(unsigned long long) * cnt.size(), cudaMemcpyDeviceToHost));
+        double tot = 0;
+        for (auto v : cnt) tot += (double)v;
+        P->stats[5] = tot;
+    }
+    P->stats[8] = (double)P->launches;
+    for (int k = 0; k < nvals && k < 9; ++k) vals[k] = P->stats[k];
+    return G3PCF_OK;
+}
+
+int g3pcf_destroy(g3pcf_plan_t P) {
+    g_err.clear();
+    if (!P) return G3PCF_OK;
+    if (P->device >= 0) cudaStreamSynchronize(P->stream);
+    DevBuf* bufs[] = {&P->key_a, &P->key_b, &P->val_a, &P->val_b, &P->hist, &P->hist_off,
+                      &P->scan_tmp, &P->pts, &P->pts64, &P->orig, &P->cstart, &P->plist,
+                      &P->small, &P->counts, &P->A, &P->partials, &P->d_tiles, &P->d_segs,
+                      &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_catoff, &P->d_ranges};
+    for (DevBuf* b : bufs) b->release();
+    if (P->h_status) cudaFreeHost(P->h_status);
+    for (auto& e : P->ev)
+        if (e) cudaEventDestroy(e);
+    delete P;
+    return G3PCF_OK;
+}
+
+}  // extern "C"

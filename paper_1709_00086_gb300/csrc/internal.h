@@ -1,0 +1,151 @@
+// Internal declarations of libg3pcf (not part of the public ABI).
+//
+// Data layout in device memory (per compute call, owned by the plan):
+//   pts      float4[n]    points sorted by cell key: (x, y, z, w), FP32
+//   pts64    double[3n]   sorted FP64 positions (only when the input is FP64)
+//   orig     int[n]       sorted slot -> original index
+//   key      uint[n]      cell key of each sorted slot
+//   cstart   int[ncell+1] first sorted slot of every cell key
+//   plist    int[np]      sorted slots of the primaries, in processing order
+//   A        float[np_rows][RLP]  per-primary multipoles, row = original index,
+//            columns: for m = 0 one block of K_0 reals (Re a_l0(b)), for m >= 1
+//            [Re | Im] blocks of K_m each; column (l-m)*B + b inside a block.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/g3pcf.h"
+
+namespace g3 {
+
+constexpr int kMaxBins = G3PCF_MAX_NBINS;
+constexpr int kMaxL = G3PCF_MAX_LMAX;
+constexpr int kWarp = 32;
+
+// Cell grid of one compute call.  Key of cell (cx, cy, cz) of catalog c:
+// c * cells_per_cat + morton2(cy, cz) * nc + cx, so that an x-row of cells is a
+// contiguous range of keys and neighbouring rows are close in memory.
+struct Grid {
+    float box;        // L (FP32)
+    float cell;       // L / nc
+    float inv_cell;   // nc / L
+    int nc;           // cells per dimension
+    int span;         // next power of two >= nc (Morton span of (cy, cz))
+    int reach;        // max |cell offset| that can hold a neighbour
+    int periodic;
+    int radial;
+    long long cells_per_cat;  // span * span * nc
+    double boxd;
+};
+
+// Radial binning: FP64 squared edges for the exact decision, FP32 copies and
+// guard half-widths for the fast decision (see pair.cu).
+struct Bins {
+    int nbins;
+    float rmin;
+    float invw;       // nbins / (rmax - rmin)
+    float rmax2f;
+    float lo_rej;     // r2 below this: surely below e_0
+    float hi_rej;     // r2 above this: surely >= e_B
+    float slack;      // conservative slack for cell pruning
+    float rmaxf;
+    double e2[kMaxBins + 1];
+    float e2f[kMaxBins + 1];
+    float guard[kMaxBins + 1];
+};
+
+__host__ __device__ constexpr int nr_of(int L) { return (L + 1) * (L + 1); }
+// accumulator slot of (l, m, part): m = 0 -> l; m >= 1 -> base(m) + 2 (l - m) + part
+__host__ __device__ constexpr int acc_base(int L, int m) {
+    return m == 0 ? 0 : (L + 1) + 2 * ((m - 1) * (L + 1) - (m - 1) * m / 2);
+}
+
+__host__ __device__ inline unsigned morton2(unsigned y, unsigned z) {
+    unsigned r = 0;
+    for (int b = 0; b < 10; ++b) r |= (((y >> b) & 1u) << (2 * b)) | (((z >> b) & 1u) << (2 * b + 1));
+    return r;
+}
+
+// ---- index.cu --------------------------------------------------------------
+struct IndexArgs {
+    const void* pos;       // n x 3 float or double (original order)
+    const float* w;
+    int64_t n;
+    int pos_f64;
+    Grid g;
+};
+struct IndexBuffers {
+    unsigned *key_a, *key_b;
+    int *val_a, *val_b;
+    int* hist;         // 256 * ntiles
+    int* hist_off;     // max(256 * ntiles, n) + 1
+    int* scan_tmp;
+    float4* pts;
+    double* pts64;     // null unless FP64 input
+    int* orig;
+    int* cstart;
+    int* plist;        // may stay unused (identity order)
+    int* status;
+    unsigned* key_sorted;  // set by build_index (points into key_a or key_b)
+};
+struct PrimRanges {    // batch mode: plist = concatenated slot ranges
+    const int* start;
+    const int* len;
+    const int* out;
+    int n;
+};
+int build_index(IndexBuffers& b, const IndexArgs& a, const int64_t* cat_off_dev, int ncat,
+                long long ncells, int64_t n_primary, const PrimRanges* ranges, cudaStream_t st);
+int scan_exclusive(const int* in, int* out, int64_t n, int* tmp, cudaStream_t st);
+size_t scan_tmp_ints(int64_t n);
+size_t radix_hist_ints(int64_t n);
+
+// ---- pair.cu ---------------------------------------------------------------
+struct PairArgs {
+    const float4* pts;
+    const double* pts64;     // may be null (FP32 input: pts is exact)
+    const int* orig;
+    const int* cstart;
+    const int* plist;        // null = identity (slot q is the q-th primary)
+    const unsigned* key;     // sorted cell keys (catalog = key / cells_per_cat)
+    int nprim;               // number of primaries
+    float* A;                // rows x RLP
+    int RLP;
+    const int* colmap;       // RL entries: res index (b * NRP + c) feeding A column
+    const float* colscale;   // RL entries: normalisation K_lm of that column
+    int RL;
+    unsigned long long* counts;  // ncat x nbins
+    int* queue;              // work counter
+    int* status;             // error bits
+    int kflush;              // pairs per lane per flush
+    Grid g;
+    Bins bins;
+};
+int launch_pair(int lmax, const PairArgs& a, int nsm, cudaStream_t st);
+size_t pair_smem_per_warp(int lmax, int nbins, int kflush);
+
+// ---- contract.cu -----------------------------------------------------------
+struct Tile {          // one output tile of one m block of C_m = sum_i w_i v_i v_i^T
+    int m, r0, c0, rows, cols, col0;  // col0: first column of block m inside an A row
+    int width;         // block width W_m
+    int out_off;       // offset (floats) of this tile inside one segment's partials
+};
+struct Segment { int cat; int row0; int row1; };
+int make_tiles(int nbins, int lmax, int T, Tile* out, int max_tiles);
+int contract_tile_dim_fp32();
+int launch_contract_fp32(const float* A, int RLP, const float* wrow, const Tile* tiles, int ntiles,
+                         const Segment* segs, int nsegs, double* partials, int part_stride,
+                         cudaStream_t st);
+int launch_reduce(const double* partials, int part_stride, const int* seg_first, int ncat,
+                  int nbins, int lmax, const Tile* tiles, int T, double* zeta, cudaStream_t st);
+int pair_nrp(int lmax);
+
+// status bits written by kernels
+enum : int {
+    kStatusRange = 1,
+    kStatusTimeout = 2,
+    kStatusOverflow = 4,
+};
+
+}  // namespace g3
