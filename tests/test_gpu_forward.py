@@ -154,7 +154,7 @@ def test_deterministic_reruns():
 
 
 def test_batch_matches_single_catalog_calls():
-    cats = catalogs.batched(ncat=5, seed=3, sizes=[1500, 400, 2500, 0, 900], box=300.0)
+    cats = catalogs.batched(ncat=5, seed=3, sizes=[1500, 400, 1200, 0, 900], box=400.0)
     plan = g3.Plan(**cats[0].params())
     pos = torch.from_numpy(np.concatenate([c.pos for c in cats])).cuda()
     w = torch.from_numpy(np.concatenate([c.w for c in cats])).cuda()
