@@ -116,7 +116,7 @@ def dist_info():
 def make_catalog(args):
     from paper_1709_00086_gb300 import catalogs
     if args.workload == "clustered2m":
-        return catalogs.clustered_2m(n=args.n or 2_000_000)
+        return catalogs.clustered_2m(n=args.n or 2_000_000, box=args.box or 1500.0)
     if args.workload == "uniform20k":
         return catalogs.plain_uniform(n=args.n or 20000)
     raise SystemExit("unknown workload")
@@ -298,7 +298,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="clustered2m")
-    ap.add_argument("--n", type=int, default=0)
+    ap.add_argument("--n", type=int, default=0, help="override N (profiling cases)")
+    ap.add_argument("--box", type=float, default=0.0, help="override the box side (profiling cases)")
     ap.add_argument("--cpu-primaries", type=int, default=300)
     ap.add_argument("--ref-primaries", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
