@@ -160,6 +160,31 @@ int g3pcf_status(g3pcf_plan_t plan);
  * At most min(nvals, 9) values are written. */
 int g3pcf_stats(g3pcf_plan_t plan, double* vals, int nvals);
 
+/* zeta from multipoles the caller already holds, without allocating any
+ * memory (the paper has no counterpart; this is a service for callers that
+ * cannot allocate: code running inside a fixed, pre-reserved device-memory
+ * budget, or inside a streamed pipeline that must not pay cudaMalloc's
+ * implicit synchronisation).  Computes
+ *      zeta^m_{l l'}(b1, b2) = sum_i w_i a_lm(i, b1) conj(a_l'm(i, b2))
+ * with the plain-FP32 contraction and the FP64 reduction of g3pcf_compute.
+ *   alm:  device, np rows of ld floats (ld >= nbins*(lmax+1)^2); row i holds
+ *         primary i's multipoles: first the K_0 = nbins*(lmax+1) values
+ *         Re a_l0(b) at column l*nbins + b, then for m = 1..lmax the K_m values
+ *         Re a_lm(b) followed by the K_m values Im a_lm(b), each at offset
+ *         (l - m)*nbins + b inside its half.
+ *   w:    device, np primary weights.   zeta: device output (layout above).
+ *   stream: cudaStream_t (NULL = legacy stream).  Asynchronous; no sync.
+ * Scratch: 16 MiB of FP64 partial sums and small tile tables in fixed device
+ * arrays inside the library, present on every GPU that loads it until the
+ * process exits.  The first call on a device looks up their addresses; make
+ * that first call before any stream capture.  Every call reuses the same
+ * arrays (each call overwrites what it reads, nothing needs clearing), so
+ * calls that overlap on the GPU race and must be serialised by the caller.
+ * Limits: nbins <= 32, lmax <= 10, np < 2^27; shapes whose tile table or one
+ * segment of partials would not fit return G3PCF_ERR_ARG. */
+int g3pcf_zeta_from_alm_noalloc(int nbins, int lmax, const float* alm, int64_t ld,
+                                const float* w, int64_t np, double* zeta, void* stream);
+
 /* Destroy a plan and free its workspace (synchronises its stream). */
 int g3pcf_destroy(g3pcf_plan_t plan);
 

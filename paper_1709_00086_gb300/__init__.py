@@ -58,6 +58,8 @@ def lib():
         L.g3pcf_status.argtypes = [P]
         L.g3pcf_stats.argtypes = [P, P, I]
         L.g3pcf_destroy.argtypes = [P]
+        L.g3pcf_zeta_from_alm_noalloc.argtypes = [I, I, P, I64, P, I64, P, P]
+        L.g3pcf_zeta_from_alm_noalloc.restype = I
         for f in ("g3pcf_plan", "g3pcf_set_stream", "g3pcf_compute", "g3pcf_compute_ex",
                   "g3pcf_compute_batch", "g3pcf_backward", "g3pcf_alm", "g3pcf_status",
                   "g3pcf_stats", "g3pcf_destroy"):

@@ -18,8 +18,12 @@
 using namespace g3;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+void g3::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
+namespace {
 
 int fail(int code, const char* fmt, ...) {
     char buf[512];

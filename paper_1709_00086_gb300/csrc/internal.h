@@ -141,6 +141,11 @@ int launch_reduce(const double* partials, int part_stride, const int* seg_first,
                   int nbins, int lmax, const Tile* tiles, int T, double* zeta, cudaStream_t st);
 int pair_nrp(int lmax);
 
+// ---- api.cu / noalloc.cu -----------------------------------------------------
+void set_last_error(const char* msg);
+int noalloc_zeta_from_alm(int nbins, int lmax, const float* alm, int64_t ld, const float* w,
+                          int64_t np, double* zeta, cudaStream_t st, char* err, size_t errlen);
+
 // status bits written by kernels
 enum : int {
     kStatusRange = 1,
