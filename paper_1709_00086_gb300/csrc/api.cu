@@ -81,14 +81,15 @@ struct g3pcf_plan_s {
     int RL = 0, RLP = 0, nrp = 0;
     std::vector<int> colmap;
     std::vector<float> colscale;
-    std::vector<Tile> tiles;
-    int T = 0;
+    std::vector<Tile> tiles;      // FP32 contraction tiles (edge T)
+    std::vector<Tile> tiles_tc;   // tensor-core contraction tiles (edge T_tc)
+    int T = 0, T_tc = 0;
     int kflush = 16;
     // device buffers
     DevBuf key_a, key_b, val_a, val_b, hist, hist_off, scan_tmp, pts, pts64, orig, cstart, plist;
     DevBuf small;       // status, queue
     DevBuf counts, A, partials, d_tiles, d_segs, d_segfirst, d_colmap, d_colscale, d_catoff;
-    DevBuf d_ranges;
+    DevBuf d_ranges, d_tiles_tc, ops, d_cats;
     int* h_status = nullptr;
     cudaEvent_t ev[5] = {};
     bool consts_uploaded = false;
@@ -124,8 +125,11 @@ int setup_device(g3pcf_plan_t P) {
 int upload_consts(g3pcf_plan_t P) {
     if (P->consts_uploaded) return 0;
     if (P->d_colmap.ensure(P->RL * sizeof(int)) || P->d_colscale.ensure(P->RL * sizeof(float)) ||
-        P->d_tiles.ensure(P->tiles.size() * sizeof(Tile)))
+        P->d_tiles.ensure(P->tiles.size() * sizeof(Tile)) ||
+        P->d_tiles_tc.ensure(P->tiles_tc.size() * sizeof(Tile)))
         return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (constants)");
+    CK(cudaMemcpy(P->d_tiles_tc.p, P->tiles_tc.data(), P->tiles_tc.size() * sizeof(Tile),
+                  cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->d_colmap.p, P->colmap.data(), P->RL * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->d_colscale.p, P->colscale.data(), P->RL * sizeof(float), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->d_tiles.p, P->tiles.data(), P->tiles.size() * sizeof(Tile),
@@ -402,27 +406,50 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
         CK(cudaEventRecord(P->ev[2], st));
 
         // ---- contraction (segments of primaries x tiles) and reduction
+        const bool use_tc = !(c.flags & G3PCF_F_CONTRACT_FP32);
         std::vector<Segment> segs;
         std::vector<int> segfirst(c.ncat + 1, 0);
+        int64_t P_pad = 0;
+        std::vector<int> cats;  // int4 per catalog: padded offset, first row, rows, 0
+        const int KB = contract_tc_kblock();
         for (int k = 0; k < c.ncat; ++k) {
             segfirst[k] = (int)segs.size();
             const int64_t r0 = (c.ncat > 1) ? c.offs[k] : 0;
             const int64_t r1 = (c.ncat > 1) ? c.offs[k + 1] : c.n_primary;
             const int64_t len = r1 - r0;
-            int64_t seg = len / 32;
-            if (seg < 8192) seg = 8192;
-            for (int64_t s = r0; s < r1; s += seg) {
-                Segment sg;
-                sg.cat = k;
-                sg.row0 = (int)s;
-                sg.row1 = (int)(s + seg < r1 ? s + seg : r1);
-                segs.push_back(sg);
+            if (use_tc) {
+                // padded primary coordinates: every catalog starts on a k-block
+                const int64_t plen = (len + KB - 1) / KB * KB;
+                cats.insert(cats.end(), {(int)P_pad, (int)r0, (int)len, 0});
+                int64_t seg = (plen / 8 + KB - 1) / KB * KB;
+                if (seg < 64 * KB) seg = 64 * KB;
+                for (int64_t s = 0; s < plen; s += seg) {
+                    Segment sg;
+                    sg.cat = k;
+                    sg.row0 = (int)(P_pad + s);
+                    sg.row1 = (int)(P_pad + (s + seg < plen ? s + seg : plen));
+                    segs.push_back(sg);
+                }
+                P_pad += plen;
+            } else {
+                int64_t seg = len / 32;
+                if (seg < 8192) seg = 8192;
+                for (int64_t s = r0; s < r1; s += seg) {
+                    Segment sg;
+                    sg.cat = k;
+                    sg.row0 = (int)s;
+                    sg.row1 = (int)(s + seg < r1 ? s + seg : r1);
+                    segs.push_back(sg);
+                }
             }
         }
         segfirst[c.ncat] = (int)segs.size();
         const int nsegs = (int)segs.size();
-        const int ntiles = (int)P->tiles.size();
-        const int part_stride = ntiles * P->T * P->T;
+        const std::vector<Tile>& tl = use_tc ? P->tiles_tc : P->tiles;
+        const int T = use_tc ? P->T_tc : P->T;
+        Tile* d_tl = use_tc ? P->d_tiles_tc.as<Tile>() : P->d_tiles.as<Tile>();
+        const int ntiles = (int)tl.size();
+        const int part_stride = ntiles * T * T;
         if (nsegs > 0) {
             if (ensure(P->d_segs, sizeof(Segment) * nsegs, "segments") ||
                 ensure(P->d_segfirst, 4 * (c.ncat + 1), "segments") ||
@@ -430,14 +457,31 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
                 return G3PCF_ERR_ALLOC;
             CK(cudaMemcpyAsync(P->d_segs.p, segs.data(), sizeof(Segment) * nsegs, cudaMemcpyHostToDevice, st));
             CK(cudaMemcpyAsync(P->d_segfirst.p, segfirst.data(), 4 * (c.ncat + 1), cudaMemcpyHostToDevice, st));
-            P->launches += 2;
-            if (launch_contract_fp32(P->A.as<float>(), P->RLP, c.w, P->d_tiles.as<Tile>(), ntiles,
-                                     P->d_segs.as<Segment>(), nsegs, P->partials.as<double>(),
-                                     part_stride, st) != 0)
-                return fail(G3PCF_ERR_CUDA, "contraction launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+            if (use_tc) {
+                if (ensure(P->d_cats, 4 * cats.size(), "catalog table") ||
+                    ensure(P->ops, (size_t)4 * P->RL * P_pad * 2, "tensor-core operands"))
+                    return G3PCF_ERR_ALLOC;
+                CK(cudaMemcpyAsync(P->d_cats.p, cats.data(), 4 * cats.size(), cudaMemcpyHostToDevice, st));
+                P->launches += 3;
+                if (launch_split(P->A.as<float>(), P->RLP, P->RL, c.w, P->d_cats.as<int4>(), c.ncat,
+                                 P_pad, P->ops.p, st) != 0)
+                    return fail(G3PCF_ERR_CUDA, "operand split launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+                const int rc = launch_contract_tc(P->ops.p, P_pad, P->RL, d_tl, ntiles,
+                                                  P->d_segs.as<Segment>(), nsegs, P->partials.as<double>(),
+                                                  part_stride, d_status, st);
+                if (rc == -2) return fail(G3PCF_ERR_CUDA, "cuTensorMapEncodeTiled unavailable or failed");
+                if (rc != 0)
+                    return fail(G3PCF_ERR_CUDA, "tensor-core contraction launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+            } else {
+                P->launches += 2;
+                if (launch_contract_fp32(P->A.as<float>(), P->RLP, c.w, d_tl, ntiles,
+                                         P->d_segs.as<Segment>(), nsegs, P->partials.as<double>(),
+                                         part_stride, st) != 0)
+                    return fail(G3PCF_ERR_CUDA, "contraction launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+            }
             CK(cudaEventRecord(P->ev[3], st));
             if (launch_reduce(P->partials.as<double>(), part_stride, P->d_segfirst.as<int>(), c.ncat,
-                              B, P->lmax, P->d_tiles.as<Tile>(), P->T, c.zeta, st) != 0)
+                              B, P->lmax, d_tl, T, c.zeta, st) != 0)
                 return fail(G3PCF_ERR_CUDA, "reduction launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         } else {
             CK(cudaEventRecord(P->ev[3], st));
@@ -521,6 +565,14 @@ int g3pcf_plan(g3pcf_plan_t* out, int nbins, double rmin, double rmax, int lmax,
         return fail(G3PCF_ERR_ARG, "too many contraction tiles");
     }
     P->tiles.resize(nt);
+    P->T_tc = contract_tile_dim_tc();
+    P->tiles_tc.resize(4096);
+    nt = make_tiles(nbins, lmax, P->T_tc, P->tiles_tc.data(), (int)P->tiles_tc.size());
+    if (nt < 0) {
+        delete P;
+        return fail(G3PCF_ERR_ARG, "too many contraction tiles");
+    }
+    P->tiles_tc.resize(nt);
     *out = P;
     return G3PCF_OK;
 }
@@ -671,7 +723,8 @@ int g3pcf_destroy(g3pcf_plan_t P) {
     DevBuf* bufs[] = {&P->key_a, &P->key_b, &P->val_a, &P->val_b, &P->hist, &P->hist_off,
                       &P->scan_tmp, &P->pts, &P->pts64, &P->orig, &P->cstart, &P->plist,
                       &P->small, &P->counts, &P->A, &P->partials, &P->d_tiles, &P->d_segs,
-                      &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_catoff, &P->d_ranges};
+                      &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_catoff, &P->d_ranges,
+                      &P->d_tiles_tc, &P->ops, &P->d_cats};
     for (DevBuf* b : bufs) b->release();
     if (P->h_status) cudaFreeHost(P->h_status);
     for (auto& e : P->ev)

@@ -1,0 +1,370 @@
+// zeta contraction on the 5th-generation tensor cores (tcgen05, sm_103a),
+// split-BF16 form.
+//
+// Paper: Sec. 3.1 -- the coefficient about one primary is a_lm(r1) a*_l'm(r2),
+// summed over all primaries; per m this is the Gram matrix
+//      C_m = sum_i w_i v_i v_i^T        (v_i the A-row block of m),
+// a dense GEMM with the primaries as the reduction dimension.
+//
+// Precision.  Each FP32 operand x is split into x_hi = bf16(x) and
+// x_lo = bf16(x - x_hi); C = L_hi R_hi^T + L_hi R_lo^T + L_lo R_hi^T with FP32
+// accumulation in tensor memory (the lo*lo product, ~2^-16 relative, is
+// dropped).  L = A (unweighted), R = w (.) A.
+//
+// Data flow.  k_split writes the four operands K-major (primaries contiguous)
+// as bf16 [column][primary].  k_contract_tc: one CTA per (128 x 128 output
+// tile, segment of primaries); one thread issues TMA tile loads (128B
+// swizzle, 3-stage mbarrier ring) and the tcgen05.mma instructions, the
+// accumulator lives in 128 TMEM columns, and four warps read it back with
+// tcgen05.ld and write FP64 partials (one per (segment, tile)) that the FP64
+// reduction adds in a fixed order.  Every wait is bounded: on expiry the
+// kernel records a timeout in the status word, drains its own copies (again
+// bounded), frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <cstdio>
+
+#include "internal.h"
+
+namespace g3 {
+
+namespace {
+
+constexpr int kTT = 128;          // output tile edge (M = N = 128)
+constexpr int kKB = 64;           // primaries per k-block (one 128-byte swizzle row of bf16)
+constexpr int kStages = 3;
+constexpr int kOpBytes = kTT * kKB * 2;          // one operand tile: 16 KB
+constexpr int kStageBytes = 4 * kOpBytes;        // L_hi, L_lo, R_hi, R_lo
+constexpr int kTcThreads = 128;
+constexpr unsigned kSpinLimit = 1u << 26;        // bounded waits
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false on expiry.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+    for (unsigned it = 0; it < kSpinLimit; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap* map, int x, int y,
+                                            unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major operand with 128-byte swizzle:
+// start address >> 4 (bits 0-13), leading byte offset (unused for this
+// layout, 1), stride byte offset 1024 B >> 4 between 8-row groups (bits
+// 32-45), descriptor version 1 (bits 46-47), swizzle mode 2 = 128B (61-63).
+__device__ __forceinline__ unsigned long long make_desc(unsigned saddr) {
+    unsigned long long d = 0;
+    d |= (unsigned long long)((saddr & 0x3FFFF) >> 4);
+    d |= (unsigned long long)1 << 16;
+    d |= (unsigned long long)(1024 >> 4) << 32;
+    d |= (unsigned long long)1 << 46;
+    d |= (unsigned long long)2 << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and B
+// BF16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at
+// bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr unsigned make_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) |
+           ((unsigned)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(unsigned tmem_d, unsigned long long a, unsigned long long b,
+                                         unsigned idesc, unsigned accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(unsigned bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+struct TcArgs {
+    const Tile* tiles;
+    const Segment* segs;   // row ranges in padded primary coordinates (multiples of kKB)
+    double* partials;
+    int part_stride;
+    int* status;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_contract_tc(const __grid_constant__ CUtensorMap mLh, const __grid_constant__ CUtensorMap mLl,
+                  const __grid_constant__ CUtensorMap mRh, const __grid_constant__ CUtensorMap mRl,
+                  TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    __shared__ __align__(8) unsigned long long bars[2 * kStages + 1];
+    __shared__ unsigned tmem_slot;
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Tile t = a.tiles[blockIdx.x];
+    const Segment sg = a.segs[blockIdx.y];
+    const int kb0 = sg.row0 / kKB;
+    const int nkb = (sg.row1 - sg.row0 + kKB - 1) / kKB;
+    // 1024-byte aligned stage buffers
+    const unsigned raw = smem_u32(tc_smem_raw);
+    const unsigned sbase = (raw + 1023u) & ~1023u;
+    const unsigned full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[kStages]),
+                   done = smem_u32(&bars[2 * kStages]);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(done, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_slot)),
+                     "r"(kTT)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tmem_slot;
+
+    const int xrow = t.col0 + t.r0;  // first operand row (A column) of the tile's rows
+    const int xcol = t.col0 + t.c0;  // ... of the tile's columns
+    if (threadIdx.x == 0 && nkb > 0) {
+        const unsigned idesc = make_idesc(kTT, kTT);
+        bool ok = true;
+        int issued = 0;  // k-blocks whose loads were issued
+        auto issue_load = [&](int kb) {
+            const int s = kb % kStages;
+            const unsigned st = sbase + s * kStageBytes;
+            const int x = (kb0 + kb) * kKB;
+            mbar_expect_tx(full0 + 8 * s, kStageBytes);
+            tma_load_2d(st + 0 * kOpBytes, &mLh, x, xrow, full0 + 8 * s);
+            tma_load_2d(st + 1 * kOpBytes, &mLl, x, xrow, full0 + 8 * s);
+            tma_load_2d(st + 2 * kOpBytes, &mRh, x, xcol, full0 + 8 * s);
+            tma_load_2d(st + 3 * kOpBytes, &mRl, x, xcol, full0 + 8 * s);
+        };
+        for (; issued < kStages && issued < nkb; ++issued) issue_load(issued);
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+            const int s = kb % kStages;
+            if (!mbar_wait(full0 + 8 * s, (kb / kStages) & 1)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned st = sbase + s * kStageBytes;
+            const unsigned Lh = st, Ll = st + kOpBytes, Rh = st + 2 * kOpBytes, Rl = st + 3 * kOpBytes;
+#pragma unroll
+            for (int k = 0; k < kKB / 16; ++k) {
+                const unsigned off = k * 32;  // 16 bf16 along K inside the swizzled row
+                const unsigned acc0 = (kb > 0 || k > 0) ? 1u : 0u;
+                mma_bf16(tmem, make_desc(Lh + off), make_desc(Rh + off), idesc, acc0);
+                mma_bf16(tmem, make_desc(Lh + off), make_desc(Rl + off), idesc, 1u);
+                mma_bf16(tmem, make_desc(Ll + off), make_desc(Rh + off), idesc, 1u);
+            }
+            mma_commit(empty0 + 8 * s);  // frees stage s when these MMAs have read it
+            if (kb >= 1 && issued < nkb) {
+                // refill the stage freed by the previous k-block (its MMAs were
+                // issued one block earlier, so this wait rarely blocks)
+                const int ps = issued % kStages;
+                if (!mbar_wait(empty0 + 8 * ps, ((issued / kStages) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                issue_load(issued);
+                ++issued;
+            }
+        }
+        if (ok) {
+            mma_commit(done);
+        } else {
+            abort_flag = 1;
+            atomicOr(a.status, kStatusTimeout);
+            // drain this CTA's own copies still in flight (bounded)
+            for (int kb = 0; kb < issued; ++kb) mbar_wait(full0 + 8 * (kb % kStages), (kb / kStages) & 1);
+            mma_commit(done);
+        }
+    }
+    __syncthreads();
+    double* out = a.partials + (int64_t)blockIdx.y * a.part_stride + t.out_off;
+    const int row = warp * 32 + lane;  // TMEM lane = output row
+    if (nkb > 0) {
+        const bool ok = mbar_wait(done, 0);
+        if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const bool valid = ok && !abort_flag;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kTT; c0 += 32) {
+            unsigned r[32];
+            const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+                "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                  "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+                  "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+                  "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+                  "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+                  "=r"(r[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < t.rows) {
+                double* o = out + (int64_t)row * kTT + c0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (c0 + j < t.cols) o[j] = valid ? (double)__uint_as_float(r[j]) : 0.0;
+            }
+        }
+    } else {
+        if (row < t.rows)
+            for (int c = 0; c < t.cols; ++c) out[(int64_t)row * kTT + c] = 0.0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTT)
+                     : "memory");
+}
+
+// A (rows x RLP, FP32) -> K-major bf16 operands [col][pr] for the split
+// product.  pr is the padded primary position: catalog c occupies
+// [cats[c].x, cats[c].x + cats[c].z) with its rows starting at cats[c].y,
+// and every catalog starts on a multiple of kKB; the gaps are written as 0.
+__global__ void k_split(const float* __restrict__ A, int RLP, int RL, const float* __restrict__ w,
+                        const int4* __restrict__ cats, int ncat, int64_t P_pad,
+                        __nv_bfloat16* Lh, __nv_bfloat16* Ll, __nv_bfloat16* Rh,
+                        __nv_bfloat16* Rl) {
+    __shared__ float tl[32][33];
+    __shared__ float tw[32];
+    __shared__ int trow[32];
+    const int64_t p0 = (int64_t)blockIdx.x * 32;  // padded primary positions
+    const int c0 = blockIdx.y * 32;               // A columns
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+    if (ty == 0) {
+        const int64_t pr = p0 + tx;
+        int lo = 0, hi = ncat - 1;  // last catalog starting at or before pr
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cats[mid].x <= pr) lo = mid; else hi = mid - 1;
+        }
+        const int4 ct = cats[lo];
+        const int64_t k = pr - ct.x;
+        trow[tx] = (pr < P_pad && k >= 0 && k < ct.z) ? (int)(ct.y + k) : -1;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int r = trow[k];
+        const int c = c0 + tx;
+        tl[k][tx] = (r >= 0 && c < RL) ? A[(int64_t)r * RLP + c] : 0.f;
+    }
+    if (ty == 0) tw[tx] = trow[tx] >= 0 ? w[trow[tx]] : 0.f;
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int c = c0 + k;
+        const int64_t pr = p0 + tx;
+        if (c >= RL || pr >= P_pad) continue;
+        const float x = tl[tx][k];
+        const float y = x * tw[tx];
+        const __nv_bfloat16 xh = __float2bfloat16_rn(x), yh = __float2bfloat16_rn(y);
+        const int64_t o = (int64_t)c * P_pad + pr;
+        Lh[o] = xh;
+        Ll[o] = __float2bfloat16_rn(x - __bfloat162float(xh));
+        Rh[o] = yh;
+        Rl[o] = __float2bfloat16_rn(y - __bfloat162float(yh));
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+int make_map(CUtensorMap* m, void* base, int64_t P_pad, int RL) {
+    auto fn = encode_fn();
+    if (!fn) return -1;
+    cuuint64_t dims[2] = {(cuuint64_t)P_pad, (cuuint64_t)RL};
+    cuuint64_t strides[1] = {(cuuint64_t)P_pad * 2};
+    cuuint32_t box[2] = {kKB, kTT};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+}  // namespace
+
+int contract_tile_dim_tc() { return kTT; }
+int contract_tc_kblock() { return kKB; }
+
+int launch_split(const float* A, int RLP, int RL, const float* w, const int4* cats, int ncat,
+                 int64_t P_pad, void* ops, cudaStream_t st) {
+    if (P_pad <= 0) return 0;
+    __nv_bfloat16* base = static_cast<__nv_bfloat16*>(ops);
+    const int64_t n1 = (int64_t)RL * P_pad;
+    dim3 grid((unsigned)((P_pad + 31) / 32), (unsigned)((RL + 31) / 32));
+    k_split<<<grid, 256, 0, st>>>(A, RLP, RL, w, cats, ncat, P_pad, base, base + n1, base + 2 * n1,
+                                  base + 3 * n1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_contract_tc(const void* ops, int64_t P_pad, int RL, const Tile* tiles, int ntiles,
+                       const Segment* segs, int nsegs, double* partials, int part_stride,
+                       int* status, cudaStream_t st) {
+    if (ntiles <= 0 || nsegs <= 0) return 0;
+    const __nv_bfloat16* base = static_cast<const __nv_bfloat16*>(ops);
+    const int64_t n1 = (int64_t)RL * P_pad;
+    CUtensorMap m[4];
+    for (int k = 0; k < 4; ++k)
+        if (make_map(&m[k], const_cast<__nv_bfloat16*>(base + k * n1), P_pad, RL) != 0) return -2;
+    const int smem = kStages * kStageBytes + 1024;
+    if (cudaFuncSetAttribute(k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess)
+        return -1;
+    TcArgs a{tiles, segs, partials, part_stride, status};
+    dim3 grid(ntiles, nsegs);
+    k_contract_tc<<<grid, kTcThreads, smem, st>>>(m[0], m[1], m[2], m[3], a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace g3

@@ -140,6 +140,14 @@ int launch_contract_fp32(const float* A, int RLP, const float* wrow, const Tile*
 int launch_reduce(const double* partials, int part_stride, const int* seg_first, int ncat,
                   int nbins, int lmax, const Tile* tiles, int T, double* zeta, cudaStream_t st);
 int pair_nrp(int lmax);
+// contract_tc.cu: split-BF16 tcgen05 contraction
+int contract_tile_dim_tc();
+int contract_tc_kblock();
+int launch_split(const float* A, int RLP, int RL, const float* w, const int4* cats, int ncat,
+                 int64_t P_pad, void* ops, cudaStream_t st);
+int launch_contract_tc(const void* ops, int64_t P_pad, int RL, const Tile* tiles, int ntiles,
+                       const Segment* segs, int nsegs, double* partials, int part_stride,
+                       int* status, cudaStream_t st);
 
 // ---- api.cu / noalloc.cu -----------------------------------------------------
 void set_last_error(const char* msg);
