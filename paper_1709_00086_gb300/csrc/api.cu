@@ -481,7 +481,7 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
             }
             CK(cudaEventRecord(P->ev[3], st));
             if (launch_reduce(P->partials.as<double>(), part_stride, P->d_segfirst.as<int>(), c.ncat,
-                              B, P->lmax, d_tl, T, c.zeta, st) != 0)
+                              B, P->lmax, d_tl, T, c.zeta, st, use_tc ? 1 : 0) != 0)
                 return fail(G3PCF_ERR_CUDA, "reduction launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         } else {
             CK(cudaEventRecord(P->ev[3], st));

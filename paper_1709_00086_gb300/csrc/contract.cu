@@ -99,7 +99,7 @@ struct BlockInfo {
 
 __device__ __forceinline__ double c_lookup(const double* part, const Tile* tiles,
                                            const BlockInfo& bi, int m, int a, int b, int T,
-                                           int tile_floats) {
+                                           int colmajor) {
     if (a > b) {
         const int t = a;
         a = b;
@@ -108,12 +108,12 @@ __device__ __forceinline__ double c_lookup(const double* part, const Tile* tiles
     const int ti = a / T, tj = b / T, nt = bi.ntile[m];
     const int idx = bi.tile_base[m] + ti * nt - ti * (ti - 1) / 2 + (tj - ti);
     const Tile& tl = tiles[idx];
-    return part[tl.out_off + (a - tl.r0) * T + (b - tl.c0)];
-    (void)tile_floats;
+    return colmajor ? part[tl.out_off + (b - tl.c0) * T + (a - tl.r0)]
+                    : part[tl.out_off + (a - tl.r0) * T + (b - tl.c0)];
 }
 
 __global__ void k_reduce(const double* partials, int part_stride, const int* seg_first, int ncat,
-                         const Tile* tiles, BlockInfo bi, int nbins, int lmax, int T,
+                         const Tile* tiles, BlockInfo bi, int nbins, int lmax, int T, int cm,
                          int64_t zsize, double* zeta) {
     const int cat = blockIdx.y;
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -127,10 +127,10 @@ __global__ void k_reduce(const double* partials, int part_stride, const int* seg
     for (int s = seg_first[cat]; s < seg_first[cat + 1]; ++s) {
         const double* p = partials + (int64_t)s * part_stride;
         if (m == 0) {
-            re += c_lookup(p, tiles, bi, 0, r, c, T, 0);
+            re += c_lookup(p, tiles, bi, 0, r, c, T, cm);
         } else {
-            re += c_lookup(p, tiles, bi, m, r, c, T, 0) + c_lookup(p, tiles, bi, m, K + r, K + c, T, 0);
-            im += c_lookup(p, tiles, bi, m, K + r, c, T, 0) - c_lookup(p, tiles, bi, m, r, K + c, T, 0);
+            re += c_lookup(p, tiles, bi, m, r, c, T, cm) + c_lookup(p, tiles, bi, m, K + r, K + c, T, cm);
+            im += c_lookup(p, tiles, bi, m, K + r, c, T, cm) - c_lookup(p, tiles, bi, m, r, K + c, T, cm);
         }
     }
     double* z = zeta + 2 * ((int64_t)cat * zsize + e);
@@ -178,7 +178,8 @@ int launch_contract_fp32(const float* A, int RLP, const float* wrow, const Tile*
 }
 
 int launch_reduce(const double* partials, int part_stride, const int* seg_first, int ncat,
-                  int nbins, int lmax, const Tile* tiles, int T, double* zeta, cudaStream_t st) {
+                  int nbins, int lmax, const Tile* tiles, int T, double* zeta, cudaStream_t st,
+                  int colmajor) {
     BlockInfo bi;
     int base = 0;
     int64_t zo = 0;
@@ -196,7 +197,7 @@ int launch_reduce(const double* partials, int part_stride, const int* seg_first,
     const int64_t zsize = zo;
     dim3 grid((unsigned)((zsize + 255) / 256), ncat);
     k_reduce<<<grid, 256, 0, st>>>(partials, part_stride, seg_first, ncat, tiles, bi, nbins, lmax,
-                                   T, zsize, zeta);
+                                   T, colmajor, zsize, zeta);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

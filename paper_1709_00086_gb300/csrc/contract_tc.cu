@@ -37,7 +37,6 @@ constexpr int kKB = 64;           // primaries per k-block (one 128-byte swizzle
 constexpr int kStages = 3;
 constexpr int kOpBytes = kTT * kKB * 2;          // one operand tile: 16 KB
 constexpr int kStageBytes = 4 * kOpBytes;        // L_hi, L_lo, R_hi, R_lo
-constexpr int kTcThreads = 128;
 constexpr unsigned kSpinLimit = 1u << 26;        // bounded waits
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -116,17 +115,39 @@ __device__ __forceinline__ void mma_commit(unsigned bar) {
 struct TcArgs {
     const Tile* tiles;
     const Segment* segs;   // row ranges in padded primary coordinates (multiples of kKB)
-    double* partials;
+    double* partials;      // per (segment, tile): 128 x 128 doubles, column-major [c][r]
     int part_stride;
     int* status;
 };
 
-__global__ void __launch_bounds__(kTcThreads, 1)
+constexpr int kSubKB = 32;          // k-blocks per FP32 accumulation run (2048 primaries)
+constexpr int kTcWarps = 5;         // warps 0-3: TMEM drain (lanes 0-127); warp 4: TMA + MMA
+
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, unsigned (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+        "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// One CTA = one (tile, segment).  The segment's k-blocks are accumulated in
+// runs of kSubKB into one of two TMEM buffers (columns [0,128) and
+// [128,256)); while the MMA warp fills one buffer the drain warps add the
+// other into the FP64 partial, which bounds every FP32 accumulation run to
+// 3 * kSubKB * 4 MMA steps whatever the segment length.
+__global__ void __launch_bounds__(kTcWarps * 32, 1)
     k_contract_tc(const __grid_constant__ CUtensorMap mLh, const __grid_constant__ CUtensorMap mLl,
                   const __grid_constant__ CUtensorMap mRh, const __grid_constant__ CUtensorMap mRl,
                   TcArgs a) {
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
-    __shared__ __align__(8) unsigned long long bars[2 * kStages + 1];
+    __shared__ __align__(8) unsigned long long bars[2 * kStages + 4];
     __shared__ unsigned tmem_slot;
     __shared__ int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -134,24 +155,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const Segment sg = a.segs[blockIdx.y];
     const int kb0 = sg.row0 / kKB;
     const int nkb = (sg.row1 - sg.row0 + kKB - 1) / kKB;
-    // 1024-byte aligned stage buffers
+    const int nsub = (nkb + kSubKB - 1) / kSubKB;
     const unsigned raw = smem_u32(tc_smem_raw);
-    const unsigned sbase = (raw + 1023u) & ~1023u;
+    const unsigned sbase = (raw + 1023u) & ~1023u;  // 1024-byte aligned stage buffers
     const unsigned full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[kStages]),
-                   done = smem_u32(&bars[2 * kStages]);
+                   ready0 = smem_u32(&bars[2 * kStages]), drained0 = smem_u32(&bars[2 * kStages + 2]);
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
-        mbar_init(done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(ready0 + 8 * b, 1);
+            mbar_init(drained0 + 8 * b, 4);  // one arrival per drain warp
+        }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_slot)),
-                     "r"(kTT)
+                     "r"(2 * kTT)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -160,101 +184,112 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = tmem_slot;
 
-    const int xrow = t.col0 + t.r0;  // first operand row (A column) of the tile's rows
-    const int xcol = t.col0 + t.c0;  // ... of the tile's columns
-    if (threadIdx.x == 0 && nkb > 0) {
-        const unsigned idesc = make_idesc(kTT, kTT);
-        bool ok = true;
-        int issued = 0;  // k-blocks whose loads were issued
-        auto issue_load = [&](int kb) {
-            const int s = kb % kStages;
-            const unsigned st = sbase + s * kStageBytes;
-            const int x = (kb0 + kb) * kKB;
-            mbar_expect_tx(full0 + 8 * s, kStageBytes);
-            tma_load_2d(st + 0 * kOpBytes, &mLh, x, xrow, full0 + 8 * s);
-            tma_load_2d(st + 1 * kOpBytes, &mLl, x, xrow, full0 + 8 * s);
-            tma_load_2d(st + 2 * kOpBytes, &mRh, x, xcol, full0 + 8 * s);
-            tma_load_2d(st + 3 * kOpBytes, &mRl, x, xcol, full0 + 8 * s);
-        };
-        for (; issued < kStages && issued < nkb; ++issued) issue_load(issued);
-        for (int kb = 0; kb < nkb && ok; ++kb) {
-            const int s = kb % kStages;
-            if (!mbar_wait(full0 + 8 * s, (kb / kStages) & 1)) {
-                ok = false;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned st = sbase + s * kStageBytes;
-            const unsigned Lh = st, Ll = st + kOpBytes, Rh = st + 2 * kOpBytes, Rl = st + 3 * kOpBytes;
-#pragma unroll
-            for (int k = 0; k < kKB / 16; ++k) {
-                const unsigned off = k * 32;  // 16 bf16 along K inside the swizzled row
-                const unsigned acc0 = (kb > 0 || k > 0) ? 1u : 0u;
-                mma_bf16(tmem, make_desc(Lh + off), make_desc(Rh + off), idesc, acc0);
-                mma_bf16(tmem, make_desc(Lh + off), make_desc(Rl + off), idesc, 1u);
-                mma_bf16(tmem, make_desc(Ll + off), make_desc(Rh + off), idesc, 1u);
-            }
-            mma_commit(empty0 + 8 * s);  // frees stage s when these MMAs have read it
-            if (kb >= 1 && issued < nkb) {
-                // refill the stage freed by the previous k-block (its MMAs were
-                // issued one block earlier, so this wait rarely blocks)
-                const int ps = issued % kStages;
-                if (!mbar_wait(empty0 + 8 * ps, ((issued / kStages) - 1) & 1)) {
+    if (warp == 4) {
+        if (lane == 0 && nkb > 0) {
+            const int xrow = t.col0 + t.r0;  // first operand row (A column) of the tile's rows
+            const int xcol = t.col0 + t.c0;  // ... of the tile's columns
+            const unsigned idesc = make_idesc(kTT, kTT);
+            bool ok = true;
+            int issued = 0;
+            auto issue_load = [&](int kb) {
+                const int s = kb % kStages;
+                const unsigned st = sbase + s * kStageBytes;
+                const int x = (kb0 + kb) * kKB;
+                mbar_expect_tx(full0 + 8 * s, kStageBytes);
+                tma_load_2d(st + 0 * kOpBytes, &mLh, x, xrow, full0 + 8 * s);
+                tma_load_2d(st + 1 * kOpBytes, &mLl, x, xrow, full0 + 8 * s);
+                tma_load_2d(st + 2 * kOpBytes, &mRh, x, xcol, full0 + 8 * s);
+                tma_load_2d(st + 3 * kOpBytes, &mRl, x, xcol, full0 + 8 * s);
+            };
+            for (; issued < kStages && issued < nkb; ++issued) issue_load(issued);
+            for (int kb = 0; kb < nkb && ok; ++kb) {
+                const int sub = kb / kSubKB, buf = sub & 1;
+                const bool first = (kb % kSubKB) == 0;
+                const bool last = (kb % kSubKB) == kSubKB - 1 || kb == nkb - 1;
+                if (first && sub >= 2 && !mbar_wait(drained0 + 8 * buf, ((sub >> 1) - 1) & 1)) {
                     ok = false;
                     break;
                 }
-                issue_load(issued);
-                ++issued;
-            }
-        }
-        if (ok) {
-            mma_commit(done);
-        } else {
-            abort_flag = 1;
-            atomicOr(a.status, kStatusTimeout);
-            // drain this CTA's own copies still in flight (bounded)
-            for (int kb = 0; kb < issued; ++kb) mbar_wait(full0 + 8 * (kb % kStages), (kb / kStages) & 1);
-            mma_commit(done);
-        }
-    }
-    __syncthreads();
-    double* out = a.partials + (int64_t)blockIdx.y * a.part_stride + t.out_off;
-    const int row = warp * 32 + lane;  // TMEM lane = output row
-    if (nkb > 0) {
-        const bool ok = mbar_wait(done, 0);
-        if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const bool valid = ok && !abort_flag;
-#pragma unroll 1
-        for (int c0 = 0; c0 < kTT; c0 += 32) {
-            unsigned r[32];
-            const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-                "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                  "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-                  "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-                  "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-                  "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-                  "=r"(r[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < t.rows) {
-                double* o = out + (int64_t)row * kTT + c0;
+                const int s = kb % kStages;
+                if (!mbar_wait(full0 + 8 * s, (kb / kStages) & 1)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned st = sbase + s * kStageBytes;
+                const unsigned Lh = st, Ll = st + kOpBytes, Rh = st + 2 * kOpBytes, Rl = st + 3 * kOpBytes;
+                const unsigned d = tmem + (unsigned)(buf * kTT);
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (c0 + j < t.cols) o[j] = valid ? (double)__uint_as_float(r[j]) : 0.0;
+                for (int k = 0; k < kKB / 16; ++k) {
+                    const unsigned off = k * 32;  // 16 bf16 along K inside the swizzled row
+                    mma_bf16(d, make_desc(Lh + off), make_desc(Rh + off), idesc,
+                             (first && k == 0) ? 0u : 1u);
+                    mma_bf16(d, make_desc(Lh + off), make_desc(Rl + off), idesc, 1u);
+                    mma_bf16(d, make_desc(Ll + off), make_desc(Rh + off), idesc, 1u);
+                }
+                mma_commit(empty0 + 8 * s);  // frees stage s when these MMAs have read it
+                if (last) mma_commit(ready0 + 8 * buf);
+                if (kb >= 1 && issued < nkb) {
+                    // refill the stage freed by the previous k-block
+                    const int ps = issued % kStages;
+                    if (!mbar_wait(empty0 + 8 * ps, ((issued / kStages) - 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    issue_load(issued);
+                    ++issued;
+                }
+            }
+            if (!ok) {
+                abort_flag = 1;
+                __threadfence_block();
+                atomicOr(a.status, kStatusTimeout);
+                // drain this CTA's own copies still in flight (bounded), then
+                // release the drain warps
+                for (int kb = 0; kb < issued; ++kb)
+                    mbar_wait(full0 + 8 * (kb % kStages), (kb / kStages) & 1);
+                mma_commit(ready0);
+                mma_commit(ready0 + 8);
             }
         }
     } else {
-        if (row < t.rows)
-            for (int c = 0; c < t.cols; ++c) out[(int64_t)row * kTT + c] = 0.0;
+        // drain warps: TMEM lane (= output row) warp*32 + lane
+        const int row = warp * 32 + lane;
+        double* out = a.partials + (int64_t)blockIdx.y * a.part_stride + t.out_off;
+        for (int sub = 0; sub < nsub; ++sub) {
+            const int buf = sub & 1;
+            const bool ok = mbar_wait(ready0 + 8 * buf, (sub >> 1) & 1);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (!ok || abort_flag) {
+                if (lane == 0) atomicOr(a.status, kStatusTimeout);
+                break;
+            }
+#pragma unroll 1
+            for (int c0 = 0; c0 < kTT; c0 += 32) {
+                unsigned r[32];
+                tmem_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(buf * kTT + c0), r);
+                if (row < t.rows) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        if (c0 + j < t.cols) {
+                            double* o = out + (int64_t)(c0 + j) * kTT + row;  // column-major
+                            const double v = (double)__uint_as_float(r[j]);
+                            *o = (sub == 0) ? v : *o + v;
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(drained0 + 8 * buf) : "memory");
+        }
+        if (nsub == 0 && row < t.rows)
+            for (int c = 0; c < t.cols; ++c) out[(int64_t)c * kTT + row] = 0.0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTT)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTT)
                      : "memory");
 }
 
@@ -363,7 +398,7 @@ int launch_contract_tc(const void* ops, int64_t P_pad, int RL, const Tile* tiles
         return -1;
     TcArgs a{tiles, segs, partials, part_stride, status};
     dim3 grid(ntiles, nsegs);
-    k_contract_tc<<<grid, kTcThreads, smem, st>>>(m[0], m[1], m[2], m[3], a);
+    k_contract_tc<<<grid, kTcWarps * 32, smem, st>>>(m[0], m[1], m[2], m[3], a);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -137,8 +137,10 @@ int contract_tile_dim_fp32();
 int launch_contract_fp32(const float* A, int RLP, const float* wrow, const Tile* tiles, int ntiles,
                          const Segment* segs, int nsegs, double* partials, int part_stride,
                          cudaStream_t st);
+// colmajor: partial tiles stored [c][r] (tensor-core path) instead of [r][c]
 int launch_reduce(const double* partials, int part_stride, const int* seg_first, int ncat,
-                  int nbins, int lmax, const Tile* tiles, int T, double* zeta, cudaStream_t st);
+                  int nbins, int lmax, const Tile* tiles, int T, double* zeta, cudaStream_t st,
+                  int colmajor = 0);
 int pair_nrp(int lmax);
 // contract_tc.cu: split-BF16 tcgen05 contraction
 int contract_tile_dim_tc();
