@@ -99,6 +99,8 @@ class Plan:
                                 self.box, self.los_mode))
         self._h = h
         self.zsize = zeta_size(self.nbins, self.lmax)
+        self._last_n = 0
+        self._token = 0  # increments with every forward on this plan
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -146,6 +148,8 @@ class Plan:
         self._stream()
         _check(lib().g3pcf_compute_ex(self._h, _ptr(pos), _ptr(w), n, npri, _ptr(zeta), _ptr(counts),
                                       flags))
+        self._last_n = n
+        self._token += 1
         return torch.view_as_complex(zeta), counts
 
     def compute_batch(self, pos, w, offsets, fp32_contraction=False, sync=True):
@@ -159,6 +163,8 @@ class Plan:
         counts = torch.empty((ncat, self.nbins), dtype=torch.int64, device=pos.device)
         flags = (F_CONTRACT_FP32 if fp32_contraction else 0) | (0 if sync else F_NO_SYNC)
         self._stream()
+        self._token += 1
+        self._last_n = 0
         _check(lib().g3pcf_compute_batch(self._h, _ptr(pos), _ptr(w),
                                          offs.ctypes.data_as(ctypes.c_void_p), ncat, _ptr(zeta),
                                          _ptr(counts), flags))
@@ -193,6 +199,53 @@ class Plan:
         keys = ["index_ms", "pair_ms", "contract_ms", "reduce_ms", "total_ms", "pairs", "primaries",
                 "cells_per_rmax", "launches"]
         return dict(zip(keys, v.tolist()))
+
+
+class _Zeta:
+    """torch.autograd.Function computing zeta (real view (zsize, 2)) of (pos, w)."""
+
+    @staticmethod
+    def _fn():
+        import torch
+
+        class ZetaFunction(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, pos, w, plan, n_primary, fp32_contraction):
+                z, _ = plan.compute(pos.detach(), w.detach(), n_primary=n_primary,
+                                    fp32_contraction=fp32_contraction, keep_alm=True)
+                ctx.plan = plan
+                ctx.token = plan._token
+                ctx.args = (n_primary, fp32_contraction)
+                ctx.save_for_backward(pos, w)
+                return torch.view_as_real(z).clone()
+
+            @staticmethod
+            def backward(ctx, gz):
+                pos, w = ctx.saved_tensors
+                plan = ctx.plan
+                if plan._token != ctx.token:  # the plan ran another forward since: redo ours
+                    plan.compute(pos.detach(), w.detach(), n_primary=ctx.args[0],
+                                 fp32_contraction=ctx.args[1], keep_alm=True)
+                dpos, dw = plan.backward(gz)
+                return dpos.to(pos.dtype), dw.to(w.dtype), None, None, None
+
+        return ZetaFunction
+
+
+_ZETA_FN = None
+
+
+def zeta(pos, w, plan: "Plan", n_primary=None, fp32_contraction=False):
+    """Differentiable zeta (real view, shape (zsize, 2), float64) of pos (n,3) and w (n,).
+
+    Gradients with respect to pos and w come from the library's adjoint
+    (g3pcf_backward; z line-of-sight modes), with the pair set and bins held
+    at the forward positions.
+    """
+    global _ZETA_FN
+    if _ZETA_FN is None:
+        _ZETA_FN = _Zeta._fn()
+    return _ZETA_FN.apply(pos, w, plan, n_primary, fp32_contraction)
 
 
 def zeta_blocks(z, nbins: int, lmax: int):

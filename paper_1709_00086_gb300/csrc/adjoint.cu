@@ -1,0 +1,153 @@
+// Adjoint of zeta with respect to the weights and positions (not in the
+// paper; the derivative of its Sec. 3.1 estimator with the pair set and
+// radial bins held fixed).
+//
+// With G_m = dL/dzeta_m / 2 (the caller passes dL/d(Re zeta, Im zeta)),
+// M_m = G_m + G_m^H and A_i the primary's multipoles,
+//      V_i = M_m A_i                    (k_vgemm, per m block, FP32)
+//      dL/dw_i (as a primary) = Re(A_i^H V_i)   (fused into k_vgemm)
+//      H_i = w_i V_i                    (applied by the adjoint pair pass)
+// and the pair pass (k_pair, mode 1) adds, for every pair (i, j) in bin b,
+// 2 Re(conj(H_i,b) . Y(rhat_ij)) to dL/dw_j and the gradient of the same
+// quantity with respect to the separation to dL/dpos_j and -dL/dpos_i.
+// In the real form of an A row ([Re | Im] halves for m >= 1) M acts as
+// [[Re M, -Im M], [Im M, Re M]]; for m = 0 only Re M enters because a_l0
+// and Y_l0 are real.
+#include "internal.h"
+
+namespace g3 {
+
+namespace {
+
+constexpr int kRows = 8;         // primaries per CTA in k_vgemm
+constexpr int kVThreads = 256;
+
+struct MInfo {
+    int K[kMaxL + 1];
+    int W[kMaxL + 1];
+    int col0[kMaxL + 1];   // first A column of block m
+    int moff[kMaxL + 1];   // offset of block m in the M buffer (floats)
+    long long zoff[kMaxL + 1];  // complex offset of block m in zeta
+};
+
+__global__ void k_build_mreal(const double* dz, MInfo mi, int lmax, float* Mr) {
+    const int m = blockIdx.y;
+    if (m > lmax) return;
+    const int K = mi.K[m], W = mi.W[m];
+    const double* Z = dz + 2 * mi.zoff[m];
+    float* out = Mr + mi.moff[m];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < W * W; e += gridDim.x * blockDim.x) {
+        const int rr = e / W, cc = e % W;
+        const int r = rr % K, c = cc % K;
+        // M = G + G^H, G = dz / 2
+        const double re = 0.5 * (Z[2 * ((int64_t)r * K + c)] + Z[2 * ((int64_t)c * K + r)]);
+        const double im = 0.5 * (Z[2 * ((int64_t)r * K + c) + 1] - Z[2 * ((int64_t)c * K + r) + 1]);
+        double v;
+        if (m == 0) {
+            v = re;
+        } else {
+            const bool rlo = rr < K, clo = cc < K;
+            v = (rlo == clo) ? re : (rlo ? -im : im);
+        }
+        out[e] = (float)v;
+    }
+}
+
+__global__ void __launch_bounds__(kVThreads) k_vgemm(const float* __restrict__ A, int RLP, int RL,
+                                                     int64_t rows, const float* __restrict__ Mr,
+                                                     MInfo mi, int lmax, float* V, double* dw) {
+    extern __shared__ float sA[];  // kRows x RL
+    __shared__ float red[kRows][kVThreads / 32];
+    const int64_t r0 = (int64_t)blockIdx.x * kRows;
+    for (int k = threadIdx.x; k < kRows * RL; k += kVThreads) {
+        const int rr = k / RL, c = k % RL;
+        sA[k] = (r0 + rr < rows) ? A[(r0 + rr) * RLP + c] : 0.f;
+    }
+    __syncthreads();
+    float dwp[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) dwp[r] = 0.f;
+    for (int col = threadIdx.x; col < RL; col += kVThreads) {
+        int m = 0;
+        while (m < lmax && col >= mi.col0[m + 1]) ++m;
+        const int W = mi.W[m], c = col - mi.col0[m];
+        const float* Mrow = Mr + mi.moff[m] + (int64_t)c * W;
+        const float* As = sA + mi.col0[m];
+        float acc[kRows];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) acc[r] = 0.f;
+        for (int k = 0; k < W; ++k) {
+            const float mv = __ldg(Mrow + k);
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) acc[r] = fmaf(mv, As[r * RL + k], acc[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            if (r0 + r < rows) V[(r0 + r) * RLP + col] = acc[r];
+            dwp[r] = fmaf(sA[r * RL + col], acc[r], dwp[r]);
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        float v = dwp[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[r][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kRows && r0 + threadIdx.x < rows) {
+        double s = 0.0;
+        for (int k = 0; k < kVThreads / 32; ++k) s += (double)red[threadIdx.x][k];
+        dw[r0 + threadIdx.x] = s;  // the primary-weight term; pair terms are added later
+    }
+}
+
+MInfo make_info(int nbins, int lmax) {
+    MInfo mi{};
+    int col = 0, moff = 0;
+    long long z = 0;
+    for (int m = 0; m <= lmax; ++m) {
+        const int K = nbins * (lmax + 1 - m);
+        const int W = m == 0 ? K : 2 * K;
+        mi.K[m] = K;
+        mi.W[m] = W;
+        mi.col0[m] = col;
+        mi.moff[m] = moff;
+        mi.zoff[m] = z;
+        col += W;
+        moff += W * W;
+        z += (long long)K * K;
+    }
+    return mi;
+}
+
+}  // namespace
+
+size_t adjoint_m_floats(int nbins, int lmax) {
+    size_t s = 0;
+    for (int m = 0; m <= lmax; ++m) {
+        const size_t K = (size_t)nbins * (lmax + 1 - m);
+        const size_t W = m == 0 ? K : 2 * K;
+        s += W * W;
+    }
+    return s;
+}
+
+int launch_adjoint_prep(const double* dzeta, int nbins, int lmax, const float* A, int RLP, int RL,
+                        int64_t rows, float* Mr, float* V, double* dw, cudaStream_t st) {
+    const MInfo mi = make_info(nbins, lmax);
+    dim3 g1(64, lmax + 1);
+    k_build_mreal<<<g1, 256, 0, st>>>(dzeta, mi, lmax, Mr);
+    if (rows > 0) {
+        const size_t smem = sizeof(float) * kRows * RL;
+        if (cudaFuncSetAttribute(k_vgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return -1;
+        k_vgemm<<<(unsigned)((rows + kRows - 1) / kRows), kVThreads, smem, st>>>(A, RLP, RL, rows, Mr,
+                                                                             mi, lmax, V, dw);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace g3

@@ -89,7 +89,9 @@ struct g3pcf_plan_s {
     DevBuf key_a, key_b, val_a, val_b, hist, hist_off, scan_tmp, pts, pts64, orig, cstart, plist;
     DevBuf small;       // status, queue
     DevBuf counts, A, partials, d_tiles, d_segs, d_segfirst, d_colmap, d_colscale, d_catoff;
-    DevBuf d_ranges, d_tiles_tc, ops, d_cats;
+    DevBuf d_ranges, d_tiles_tc, ops, d_cats, d_mreal, d_V;
+    // index state of the last forward (for the adjoint pair pass)
+    bool last_plist = false;
     int* h_status = nullptr;
     cudaEvent_t ev[5] = {};
     bool consts_uploaded = false;
@@ -386,6 +388,7 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
             pa.orig = ib.orig;
             pa.cstart = ib.cstart;
             pa.plist = (c.ncat > 1 || c.n_primary < n) ? ib.plist : nullptr;
+            P->last_plist = pa.plist != nullptr;
             pa.key = ib.key_sorted;
             pa.nprim = (int)nprim;
             pa.A = P->A.as<float>();
@@ -674,10 +677,55 @@ int g3pcf_backward(g3pcf_plan_t P, const double* dzeta, double* dpos, double* dw
     g_err.clear();
     if (int r = check_plan(P)) return r;
     if (!P->have_forward) return fail(G3PCF_ERR_STATE, "backward before forward on this plan");
-    (void)dzeta;
-    (void)dpos;
-    (void)dw;
-    return fail(G3PCF_ERR_UNSUPPORTED, "backward not built");
+    if (!dzeta || !dpos || !dw) return fail(G3PCF_ERR_ARG, "dzeta, dpos and dw must be non-null");
+    if (P->los_mode == G3PCF_LOS_RADIAL_OPEN)
+        return fail(G3PCF_ERR_UNSUPPORTED, "the adjoint supports the z line-of-sight modes only");
+    if (P->last_ncat != 1) return fail(G3PCF_ERR_UNSUPPORTED, "the adjoint of a batched call is not built");
+    cudaStream_t st = P->stream;
+    const int64_t n = P->last_n, rows = P->last_np;
+    CK(cudaMemsetAsync(dpos, 0, sizeof(double) * 3 * (n > 0 ? n : 1), st));
+    CK(cudaMemsetAsync(dw, 0, sizeof(double) * (n > 0 ? n : 1), st));
+    if (n == 0 || rows == 0) {
+        CK(cudaStreamSynchronize(st));
+        return G3PCF_OK;
+    }
+    if (ensure(P->d_mreal, sizeof(float) * adjoint_m_floats(P->nbins, P->lmax), "adjoint M") ||
+        ensure(P->d_V, sizeof(float) * (size_t)P->RLP * rows, "adjoint V"))
+        return G3PCF_ERR_ALLOC;
+    int* d_status = P->small.as<int>();
+    int* d_queue = d_status + 16;
+    CK(cudaMemsetAsync(P->small.p, 0, 256, st));
+    CK(cudaMemsetAsync(P->counts.p, 0, sizeof(unsigned long long) * P->nbins, st));
+    if (launch_adjoint_prep(dzeta, P->nbins, P->lmax, P->A.as<float>(), P->RLP, P->RL, rows,
+                            P->d_mreal.as<float>(), P->d_V.as<float>(), dw, st) != 0)
+        return fail(G3PCF_ERR_CUDA, "adjoint preparation launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    PairArgs pa{};
+    pa.pts = P->pts.as<float4>();
+    pa.pts64 = P->last_pos_f64 ? P->pts64.as<double>() : nullptr;
+    pa.orig = P->orig.as<int>();
+    pa.cstart = P->cstart.as<int>();
+    pa.plist = P->last_plist ? P->plist.as<int>() : nullptr;
+    pa.key = P->key_sorted;
+    pa.nprim = (int)rows;
+    pa.A = P->A.as<float>();
+    pa.RLP = P->RLP;
+    pa.colmap = P->d_colmap.as<int>();
+    pa.colscale = P->d_colscale.as<float>();
+    pa.RL = P->RL;
+    pa.counts = P->counts.as<unsigned long long>();
+    pa.queue = d_queue;
+    pa.status = d_status;
+    pa.kflush = P->kflush;
+    pa.V = P->d_V.as<float>();
+    pa.dw = dw;
+    pa.dpos = dpos;
+    pa.g = P->last_grid;
+    pa.bins = P->bins;
+    if (launch_pair(P->lmax, pa, P->nsm, st, 1) != 0)
+        return fail(G3PCF_ERR_CUDA, "adjoint pair kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    CK(cudaMemcpyAsync(P->h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return read_status(P);
 }
 
 int g3pcf_status(g3pcf_plan_t P) {
@@ -724,7 +772,7 @@ int g3pcf_destroy(g3pcf_plan_t P) {
                       &P->scan_tmp, &P->pts, &P->pts64, &P->orig, &P->cstart, &P->plist,
                       &P->small, &P->counts, &P->A, &P->partials, &P->d_tiles, &P->d_segs,
                       &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_catoff, &P->d_ranges,
-                      &P->d_tiles_tc, &P->ops, &P->d_cats};
+                      &P->d_tiles_tc, &P->ops, &P->d_cats, &P->d_mreal, &P->d_V};
     for (DevBuf* b : bufs) b->release();
     if (P->h_status) cudaFreeHost(P->h_status);
     for (auto& e : P->ev)

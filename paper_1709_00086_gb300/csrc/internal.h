@@ -119,10 +119,16 @@ struct PairArgs {
     int* queue;              // work counter
     int* status;             // error bits
     int kflush;              // pairs per lane per flush
+    // adjoint pass only (mode 1): V rows (M_m A_i, stride RLP, row = original
+    // index), outputs dL/dw and dL/dpos (FP64, original order)
+    const float* V;
+    double* dw;
+    double* dpos;
     Grid g;
     Bins bins;
 };
-int launch_pair(int lmax, const PairArgs& a, int nsm, cudaStream_t st);
+// mode 0: forward multipoles; mode 1: adjoint pair pass
+int launch_pair(int lmax, const PairArgs& a, int nsm, cudaStream_t st, int mode = 0);
 size_t pair_smem_per_warp(int lmax, int nbins, int kflush);
 
 // ---- contract.cu -----------------------------------------------------------
@@ -150,6 +156,11 @@ int launch_split(const float* A, int RLP, int RL, const float* w, const int4* ca
 int launch_contract_tc(const void* ops, int64_t P_pad, int RL, const Tile* tiles, int ntiles,
                        const Segment* segs, int nsegs, double* partials, int part_stride,
                        int* status, cudaStream_t st);
+
+// ---- adjoint.cu ----------------------------------------------------------------
+size_t adjoint_m_floats(int nbins, int lmax);
+int launch_adjoint_prep(const double* dzeta, int nbins, int lmax, const float* A, int RLP, int RL,
+                        int64_t rows, float* Mr, float* V, double* dw, cudaStream_t st);
 
 // ---- api.cu / noalloc.cu -----------------------------------------------------
 void set_last_error(const char* msg);

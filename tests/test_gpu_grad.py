@@ -1,0 +1,139 @@
+"""Parity of the CUDA adjoint (g3pcf_backward / autograd) with the FP64 oracle.
+
+The adjoint is the derivative of zeta (Sec. 3.1) with respect to the weights
+and positions, with the pair set and bins held fixed; the oracle's reference
+gradient is itself pinned to finite differences in test_oracle_grad.py.  The
+target zeta comes from the oracle on a second catalog, so no expected value
+comes from the CUDA path.  Tolerance: max |g - g_ref| / max |g_ref| per
+quantity.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_1709_00086_gb300 as g3  # noqa: E402
+from paper_1709_00086_gb300 import catalogs  # noqa: E402
+
+from gpu_util import maxrel, oracle_zeta, to_dev  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL_GRAD = 1e-5
+
+
+def _case(seed, n=2500, box=300.0, los_mode=0):
+    # the differentiation recipe (clustered, Rmax=120 -> scaled, 8 bins, lmax=6)
+    return catalogs.small_case("clustered", n, seed=seed, box=box, nbins=8, rmin=0.0, rmax=60.0,
+                               lmax=6, los_mode=los_mode)
+
+
+@pytest.mark.parametrize("los_mode", [0, 1])
+def test_backward_matches_oracle_gradient_given_dzeta(los_mode):
+    # a fixed, seeded Hermitian dL/dzeta fed to both sides isolates the adjoint
+    cat = _case(41 + los_mode, los_mode=los_mode)
+    plan = g3.Plan(**cat.params())
+    pos, w = to_dev(cat, torch)
+    plan.compute(pos, w, keep_alm=True)
+    rng = np.random.default_rng(7)
+    G = rng.normal(size=plan.zsize) + 1j * rng.normal(size=plan.zsize)
+    blocks = oracle.zeta_blocks(G, cat.nbins, cat.lmax)
+    G = np.concatenate([(b + b.conj().T).ravel() for b in blocks])  # Hermitian blocks
+    dz = torch.from_numpy(np.stack([2 * G.real, 2 * G.imag], axis=1)).cuda()
+    dpos, dw = plan.backward(dz)
+    rpos, rw = oracle.grad(cat.pos.astype(np.float64), cat.w.astype(np.float64), G, cat.box,
+                           cat.nbins, cat.rmin, cat.rmax, cat.lmax, los_mode=los_mode)
+    assert maxrel(dw.cpu().numpy(), rw) < TOL_GRAD
+    assert maxrel(dpos.cpu().numpy(), rpos) < TOL_GRAD
+
+
+def test_autograd_loss_gradient_matches_oracle():
+    cat = _case(51)
+    tgt = _case(52)
+    zt, _ = oracle_zeta(tgt)
+    plan = g3.Plan(**cat.params())
+    pos, w = to_dev(cat, torch)
+    pos.requires_grad_(True)
+    w.requires_grad_(True)
+    z = g3.zeta(pos, w, plan, fp32_contraction=True)
+    zt_t = torch.from_numpy(np.stack([zt.real, zt.imag], axis=1)).cuda()
+    loss = ((z - zt_t) ** 2).sum()
+    gpos, gw = torch.autograd.grad(loss, [pos, w])
+    zo, _ = oracle_zeta(cat)
+    rpos, rw = oracle.grad(cat.pos.astype(np.float64), cat.w.astype(np.float64), zo - zt, cat.box,
+                           cat.nbins, cat.rmin, cat.rmax, cat.lmax)
+    assert maxrel(gw.double().cpu().numpy(), rw) < TOL_GRAD
+    assert maxrel(gpos.double().cpu().numpy(), rpos) < TOL_GRAD
+
+
+def test_backward_with_subset_of_primaries_and_state_errors():
+    cat = _case(61, n=1500)
+    plan = g3.Plan(**cat.params())
+    pos, w = to_dev(cat, torch)
+    with pytest.raises(g3.G3PCFError) as ei:
+        plan.backward(torch.zeros((plan.zsize, 2), dtype=torch.float64, device="cuda"))
+    assert ei.value.name == "ERR_STATE"
+    npri = 400
+    plan.compute(pos, w, n_primary=npri, keep_alm=True)
+    rng = np.random.default_rng(9)
+    G = rng.normal(size=plan.zsize) + 1j * rng.normal(size=plan.zsize)
+    blocks = oracle.zeta_blocks(G, cat.nbins, cat.lmax)
+    G = np.concatenate([(b + b.conj().T).ravel() for b in blocks])
+    dz = torch.from_numpy(np.stack([2 * G.real, 2 * G.imag], axis=1)).cuda()
+    dpos, dw = plan.backward(dz)
+    # oracle with only the first npri points as primaries: reorder-free check
+    # through the definition -- primaries beyond npri contribute nothing
+    sub = catalogs.Catalog(cat.pos, cat.w, cat.box, cat.nbins, cat.rmin, cat.rmax, cat.lmax, 0)
+    rpos, rw = _oracle_grad_subset(sub, G, npri)
+    assert maxrel(dw.cpu().numpy(), rw) < TOL_GRAD
+    assert maxrel(dpos.cpu().numpy(), rpos) < TOL_GRAD
+
+
+def _oracle_grad_subset(cat, G, npri):
+    """Oracle gradient when only the first npri points are primaries: the
+    full-catalog oracle gradient minus the contribution of the others, computed
+    as the gradient of a catalog whose non-primaries have primary weight 0 is
+    not expressible (w enters both roles), so assemble it from the definition
+    using per-primary oracle multipoles."""
+    pos = cat.pos.astype(np.float64)
+    w = cat.w.astype(np.float64)
+    n = pos.shape[0]
+    # finite differences of <G, zeta> would be slow; use linearity: the
+    # gradient is sum over primaries of the gradient of w_i a_i^H M a_i / 2
+    # with M = G + G^H ... which is exactly the oracle's formula restricted.
+    # The oracle exposes the all-primary case only, so emulate a subset by
+    # moving the non-primaries into a second copy of the catalog that acts
+    # only as secondaries: not possible either.  Fall back to an explicit
+    # O(N * pairs) assembly in numpy.
+    nb, L = cat.nbins, cat.lmax
+    e2 = oracle.edges2(nb, cat.rmin, cat.rmax)
+    blocks = oracle.zeta_blocks(G, nb, L)
+    a = oracle.alm(pos, w, np.arange(npri), cat.box, nb, cat.rmin, cat.rmax, L)
+    nl = oracle.nlm(L)
+    dpos = np.zeros((n, 3))
+    dw = np.zeros(n)
+    for i in range(npri):
+        H = np.zeros((nb, nl), dtype=complex)
+        for m in range(L + 1):
+            M = blocks[m] + blocks[m].conj().T
+            idx = [oracle.lm_index(l, m) for l in range(m, L + 1)]
+            vec = a[i][:, idx].T.reshape(-1)          # (l - m) * nb + b
+            hv = w[i] * (M @ vec)
+            H[:, idx] = hv.reshape(len(idx), nb).T
+            dw[i] += np.real(np.conj(vec) @ (M @ vec))
+        d = pos - pos[i]
+        d -= cat.box * np.round(d / cat.box)
+        r2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+        ok = (r2 > 0) & (r2 >= e2[0]) & (r2 < e2[-1])
+        js = np.nonzero(ok)[0]
+        bins = np.searchsorted(e2, r2[js], side="right") - 1
+        Y = oracle.ylm(L, d[js])
+        gY = oracle.ylm_grad(L, d[js])
+        hc = np.conj(H[bins])                          # (npairs, nl)
+        dw[js] += 2 * np.real(np.sum(hc * Y, axis=1))
+        dd = 2 * w[js][:, None] * np.real(np.einsum("pk,pka->pa", hc, gY))
+        np.add.at(dpos, js, dd)
+        dpos[i] -= dd.sum(axis=0)
+    return dpos, dw
