@@ -92,21 +92,12 @@ def test_backward_with_subset_of_primaries_and_state_errors():
 
 
 def _oracle_grad_subset(cat, G, npri):
-    """Oracle gradient when only the first npri points are primaries: the
-    full-catalog oracle gradient minus the contribution of the others, computed
-    as the gradient of a catalog whose non-primaries have primary weight 0 is
-    not expressible (w enters both roles), so assemble it from the definition
-    using per-primary oracle multipoles."""
+    """Reference gradient when only the first npri points are primaries,
+    assembled in numpy from the oracle's multipoles, Y_lm and grad Y_lm
+    (orc_grad itself treats every point as a primary)."""
     pos = cat.pos.astype(np.float64)
     w = cat.w.astype(np.float64)
     n = pos.shape[0]
-    # finite differences of <G, zeta> would be slow; use linearity: the
-    # gradient is sum over primaries of the gradient of w_i a_i^H M a_i / 2
-    # with M = G + G^H ... which is exactly the oracle's formula restricted.
-    # The oracle exposes the all-primary case only, so emulate a subset by
-    # moving the non-primaries into a second copy of the catalog that acts
-    # only as secondaries: not possible either.  Fall back to an explicit
-    # O(N * pairs) assembly in numpy.
     nb, L = cat.nbins, cat.lmax
     e2 = oracle.edges2(nb, cat.rmin, cat.rmax)
     blocks = oracle.zeta_blocks(G, nb, L)
