@@ -89,7 +89,9 @@ struct g3pcf_plan_s {
     DevBuf key_a, key_b, val_a, val_b, hist, hist_off, scan_tmp, pts, pts64, orig, cstart, plist;
     DevBuf small;       // status, queue
     DevBuf counts, A, partials, d_tiles, d_segs, d_segfirst, d_colmap, d_colscale, d_catoff;
-    DevBuf d_ranges, d_tiles_tc, ops, d_cats, d_mreal, d_V;
+    DevBuf d_ranges, d_tiles_tc, ops, d_cats, d_mreal, d_V, d_bintab;
+    std::vector<unsigned char> bintab;  // r^2 -> bin lookup (see compute_bins)
+    float bin_tscale = 0.f;
     // index state of the last forward (for the adjoint pair pass)
     bool last_plist = false;
     int* h_status = nullptr;
@@ -132,6 +134,8 @@ int upload_consts(g3pcf_plan_t P) {
         return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (constants)");
     CK(cudaMemcpy(P->d_tiles_tc.p, P->tiles_tc.data(), P->tiles_tc.size() * sizeof(Tile),
                   cudaMemcpyHostToDevice));
+    if (P->d_bintab.ensure(P->bintab.size())) return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (bin table)");
+    CK(cudaMemcpy(P->d_bintab.p, P->bintab.data(), P->bintab.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->d_colmap.p, P->colmap.data(), P->RL * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->d_colscale.p, P->colscale.data(), P->RL * sizeof(float), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->d_tiles.p, P->tiles.data(), P->tiles.size() * sizeof(Tile),
@@ -204,6 +208,28 @@ void compute_bins(g3pcf_plan_t P) {
     b.hi_rej = b.e2f[B] + b.guard[B];
     b.lo_rej = b.e2f[0] - b.guard[0];
     b.slack = (float)(1e-4 * P->box / 1.0 + 1e-3 * P->rmax);
+    // r^2 -> bin table over [0, e_B^2): cell t covers [t D, (t+1) D).  An entry
+    // names bin b only if the cell, widened by 1% of a cell on each side (far
+    // more than the FP32 error of the kernel's index r2 * T / e_B^2), lies
+    // inside b's decided interval (e_b^2 + g_b, e_{b+1}^2 - g_{b+1}); 254 if it
+    // lies below e_0^2 - g_0 (surely outside); 255 otherwise (checked per pair).
+    const int T = G3_BIN_TABLE;
+    P->bintab.assign(T + 2, 255);
+    const double r2max = b.e2[B];
+    P->bin_tscale = (float)(T / r2max);
+    const double D = r2max / T;
+    for (int t = 0; t < T + 2; ++t) {
+        const double lo = (t - 0.01) * D, hi = (t + 1.01) * D;
+        if (hi < b.e2[0] - b.guard[0] && lo >= 0.0) {
+            P->bintab[t] = 254;
+            continue;
+        }
+        for (int k = 0; k < B; ++k)
+            if (lo > b.e2[k] + b.guard[k] && hi < b.e2[k + 1] - b.guard[k + 1]) {
+                P->bintab[t] = (unsigned char)k;
+                break;
+            }
+    }
 }
 
 // Column map of an A row: block m (m = 0: K_0 reals; m >= 1: Re and Im halves)
@@ -402,6 +428,8 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
             pa.kflush = P->kflush;
             pa.g = g;
             pa.bins = P->bins;
+            pa.bintab = P->d_bintab.as<unsigned char>();
+            pa.bin_tscale = P->bin_tscale;
             ++P->launches;
             if (launch_pair(P->lmax, pa, P->nsm, st) != 0)
                 return fail(G3PCF_ERR_CUDA, "pair kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -721,6 +749,8 @@ int g3pcf_backward(g3pcf_plan_t P, const double* dzeta, double* dpos, double* dw
     pa.dpos = dpos;
     pa.g = P->last_grid;
     pa.bins = P->bins;
+    pa.bintab = P->d_bintab.as<unsigned char>();
+    pa.bin_tscale = P->bin_tscale;
     if (launch_pair(P->lmax, pa, P->nsm, st, 1) != 0)
         return fail(G3PCF_ERR_CUDA, "adjoint pair kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     CK(cudaMemcpyAsync(P->h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -772,7 +802,7 @@ int g3pcf_destroy(g3pcf_plan_t P) {
                       &P->scan_tmp, &P->pts, &P->pts64, &P->orig, &P->cstart, &P->plist,
                       &P->small, &P->counts, &P->A, &P->partials, &P->d_tiles, &P->d_segs,
                       &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_catoff, &P->d_ranges,
-                      &P->d_tiles_tc, &P->ops, &P->d_cats, &P->d_mreal, &P->d_V};
+                      &P->d_tiles_tc, &P->ops, &P->d_cats, &P->d_mreal, &P->d_V, &P->d_bintab};
     for (DevBuf* b : bufs) b->release();
     if (P->h_status) cudaFreeHost(P->h_status);
     for (auto& e : P->ev)

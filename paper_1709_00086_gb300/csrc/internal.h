@@ -22,6 +22,7 @@ namespace g3 {
 constexpr int kMaxBins = G3PCF_MAX_NBINS;
 constexpr int kMaxL = G3PCF_MAX_LMAX;
 constexpr int kWarp = 32;
+#define G3_BIN_TABLE 2048
 
 // Cell grid of one compute call.  Key of cell (cx, cy, cz) of catalog c:
 // c * cells_per_cat + morton2(cy, cz) * nc + cx, so that an x-row of cells is a
@@ -119,6 +120,8 @@ struct PairArgs {
     int* queue;              // work counter
     int* status;             // error bits
     int kflush;              // pairs per lane per flush
+    const unsigned char* bintab;  // G3_BIN_TABLE + 2 entries over r^2 in [0, table_r2max)
+    float bin_tscale;        // G3_BIN_TABLE / table_r2max
     // adjoint pass only (mode 1): V rows (M_m A_i, stride RLP, row = original
     // index), outputs dL/dw and dL/dpos (FP64, original order)
     const float* V;
