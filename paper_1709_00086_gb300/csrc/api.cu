@@ -582,9 +582,10 @@ int g3pcf_plan(g3pcf_plan_t* out, int nbins, double rmin, double rmax, int lmax,
     compute_columns(P);
     // pairs per lane per bucket flush: the largest k <= 16 for which two
     // 4-warp CTAs of the pair kernel fit in 227 KB of shared memory
+    // (dynamic per warp x 4 warps + ~2.6 KB static + 1 KB reserved, per CTA)
     P->kflush = 2;
     for (int kf = 16; kf >= 2; --kf)
-        if (pair_smem_per_warp(lmax, nbins, kf) * 4 * 2 + 2048 <= 227 * 1024) {
+        if ((pair_smem_per_warp(lmax, nbins, kf) * 4 + 4096) * 2 <= 227 * 1024) {
             P->kflush = kf;
             break;
         }
