@@ -185,6 +185,19 @@ int g3pcf_stats(g3pcf_plan_t plan, double* vals, int nvals);
 int g3pcf_zeta_from_alm_noalloc(int nbins, int lmax, const float* alm, int64_t ld,
                                 const float* w, int64_t np, double* zeta, void* stream);
 
+/* Tuning knobs of a plan (0 = automatic, the default for each):
+ *   G3PCF_OPT_CHUNK_ROWS      primaries per pass of the pair stage + contraction;
+ *                             large catalogs are processed in chunks so that the
+ *                             per-primary multipoles never exceed the memory budget
+ *                             (automatic: all primaries if they fit, else chunks);
+ *                             after a chunked forward g3pcf_alm and g3pcf_backward
+ *                             return G3PCF_ERR_STATE
+ *   G3PCF_OPT_CELLS_PER_RMAX  cell-list resolution s (cell side >= rmax / s, 1..8)
+ *   G3PCF_OPT_KFLUSH          pairs per lane per bucket flush (2..16)
+ * Returns G3PCF_ERR_ARG for unknown options or values out of range. */
+enum { G3PCF_OPT_CHUNK_ROWS = 1, G3PCF_OPT_CELLS_PER_RMAX = 2, G3PCF_OPT_KFLUSH = 3 };
+int g3pcf_set_option(g3pcf_plan_t plan, int option, int64_t value);
+
 /* Destroy a plan and free its workspace (synchronises its stream). */
 int g3pcf_destroy(g3pcf_plan_t plan);
 

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libg3pcf.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "g3pcf.h")
 
 LOS_Z_PERIODIC, LOS_Z_OPEN, LOS_RADIAL_OPEN = 0, 1, 2
+OPT_CHUNK_ROWS, OPT_CELLS_PER_RMAX, OPT_KFLUSH = 1, 2, 3
 F_POS_F64, F_CONTRACT_FP32, F_NO_SYNC, F_KEEP_ALM = 1, 2, 4, 8
 ERRORS = {0: "OK", -1: "ERR_ARG", -2: "ERR_RANGE", -3: "ERR_RMAX", -4: "ERR_ALLOC",
           -5: "ERR_CUDA", -6: "ERR_TIMEOUT", -7: "ERR_STATE", -8: "ERR_UNSUPPORTED"}
@@ -58,6 +59,8 @@ def lib():
         L.g3pcf_status.argtypes = [P]
         L.g3pcf_stats.argtypes = [P, P, I]
         L.g3pcf_destroy.argtypes = [P]
+        L.g3pcf_set_option.argtypes = [P, I, I64]
+        L.g3pcf_set_option.restype = I
         L.g3pcf_zeta_from_alm_noalloc.argtypes = [I, I, P, I64, P, I64, P, P]
         L.g3pcf_zeta_from_alm_noalloc.restype = I
         for f in ("g3pcf_plan", "g3pcf_set_stream", "g3pcf_compute", "g3pcf_compute_ex",
@@ -189,6 +192,10 @@ class Plan:
         self._stream()
         _check(lib().g3pcf_backward(self._h, _ptr(dz), _ptr(dpos), _ptr(dw)))
         return dpos, dw
+
+    def set_option(self, option: int, value: int):
+        """Tuning knob (OPT_CHUNK_ROWS, OPT_CELLS_PER_RMAX, OPT_KFLUSH; 0 = automatic)."""
+        _check(lib().g3pcf_set_option(self._h, int(option), int(value)))
 
     def status(self):
         _check(lib().g3pcf_status(self._h))

@@ -89,7 +89,10 @@ struct g3pcf_plan_s {
     DevBuf key_a, key_b, val_a, val_b, hist, hist_off, scan_tmp, pts, pts64, orig, cstart, plist;
     DevBuf small;       // status, queue
     DevBuf counts, A, partials, d_tiles, d_segs, d_segfirst, d_colmap, d_colscale, d_catoff;
-    DevBuf d_ranges, d_tiles_tc, ops, d_cats, d_mreal, d_V, d_bintab;
+    DevBuf d_ranges, d_tiles_tc, ops, d_cats, d_mreal, d_V, d_bintab, wrow;
+    int64_t opt_chunk = 0;   // G3PCF_OPT_CHUNK_ROWS
+    int opt_cells = 0;       // G3PCF_OPT_CELLS_PER_RMAX
+    bool last_chunked = false;
     std::vector<unsigned char> bintab;  // r^2 -> bin lookup (see compute_bins)
     float bin_tscale = 0.f;
     // index state of the last forward (for the adjoint pair pass)
@@ -153,6 +156,7 @@ Grid choose_grid(g3pcf_plan_t P, double density, int ncat) {
     int s = (int)std::floor(P->rmax / cs);
     if (s < 1) s = 1;
     if (s > 8) s = 8;
+    if (P->opt_cells > 0) s = P->opt_cells;
     int nc = (int)std::floor(P->box * s / P->rmax);
     if (nc < 1) nc = 1;
     if (nc > 256) nc = 256;
@@ -403,120 +407,168 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
         P->key_sorted = ib.key_sorted;
         CK(cudaEventRecord(P->ev[1], st));
 
-        // ---- pair stage
-        const int64_t rows = (c.ncat > 1) ? n : c.n_primary;
-        if (ensure(P->A, sizeof(float) * (size_t)P->RLP * (rows > 0 ? rows : 1), "multipoles"))
-            return G3PCF_ERR_ALLOC;
-        if (nprim > 0) {
-            PairArgs pa{};
-            pa.pts = ib.pts;
-            pa.pts64 = ib.pts64;
-            pa.orig = ib.orig;
-            pa.cstart = ib.cstart;
-            pa.plist = (c.ncat > 1 || c.n_primary < n) ? ib.plist : nullptr;
-            P->last_plist = pa.plist != nullptr;
-            pa.key = ib.key_sorted;
-            pa.nprim = (int)nprim;
-            pa.A = P->A.as<float>();
-            pa.RLP = P->RLP;
-            pa.colmap = P->d_colmap.as<int>();
-            pa.colscale = P->d_colscale.as<float>();
-            pa.RL = P->RL;
-            pa.counts = P->counts.as<unsigned long long>();
-            pa.queue = d_queue;
-            pa.status = d_status;
-            pa.kflush = P->kflush;
-            pa.g = g;
-            pa.bins = P->bins;
-            pa.bintab = P->d_bintab.as<unsigned char>();
-            pa.bin_tscale = P->bin_tscale;
-            ++P->launches;
-            if (launch_pair(P->lmax, pa, P->nsm, st) != 0)
-                return fail(G3PCF_ERR_CUDA, "pair kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
-        }
-        CK(cudaEventRecord(P->ev[2], st));
-
-        // ---- contraction (segments of primaries x tiles) and reduction
+        // ---- pair stage + contraction, one pass per chunk of primaries
         const bool use_tc = !(c.flags & G3PCF_F_CONTRACT_FP32);
-        std::vector<Segment> segs;
-        std::vector<int> segfirst(c.ncat + 1, 0);
-        int64_t P_pad = 0;
-        std::vector<int> cats;  // int4 per catalog: padded offset, first row, rows, 0
         const int KB = contract_tc_kblock();
-        for (int k = 0; k < c.ncat; ++k) {
-            segfirst[k] = (int)segs.size();
-            const int64_t r0 = (c.ncat > 1) ? c.offs[k] : 0;
-            const int64_t r1 = (c.ncat > 1) ? c.offs[k + 1] : c.n_primary;
-            const int64_t len = r1 - r0;
-            if (use_tc) {
-                // padded primary coordinates: every catalog starts on a k-block
-                const int64_t plen = (len + KB - 1) / KB * KB;
-                cats.insert(cats.end(), {(int)P_pad, (int)r0, (int)len, 0});
-                int64_t seg = (plen / 8 + KB - 1) / KB * KB;
-                if (seg < 64 * KB) seg = 64 * KB;
-                for (int64_t s = 0; s < plen; s += seg) {
-                    Segment sg;
-                    sg.cat = k;
-                    sg.row0 = (int)(P_pad + s);
-                    sg.row1 = (int)(P_pad + (s + seg < plen ? s + seg : plen));
-                    segs.push_back(sg);
-                }
-                P_pad += plen;
+        const int64_t rows_all = (c.ncat > 1) ? n : c.n_primary;
+        int64_t C = rows_all;
+        if (c.ncat == 1) {
+            if (P->opt_chunk > 0) {
+                C = P->opt_chunk;
             } else {
-                int64_t seg = len / 32;
-                if (seg < 8192) seg = 8192;
-                for (int64_t s = r0; s < r1; s += seg) {
-                    Segment sg;
-                    sg.cat = k;
-                    sg.row0 = (int)s;
-                    sg.row1 = (int)(s + seg < r1 ? s + seg : r1);
-                    segs.push_back(sg);
-                }
+                size_t fr = 0, tot = 0;
+                CK(cudaMemGetInfo(&fr, &tot));
+                double budget = 0.4 * (double)fr;
+                if (budget > 48e9) budget = 48e9;
+                const double per_row = 4.0 * P->RLP + 4.0 + (use_tc ? 8.0 * P->RL : 0.0);
+                C = (int64_t)(budget / per_row) / KB * KB;
+                if (C < KB) C = KB;
             }
+            if (C > rows_all) C = rows_all;
         }
-        segfirst[c.ncat] = (int)segs.size();
-        const int nsegs = (int)segs.size();
+        const bool chunked = (c.ncat == 1) && C < rows_all;
+        const int64_t nchunks = chunked ? (rows_all + C - 1) / C : 1;
+        const int64_t rows_cap = chunked ? C : rows_all;
+        if (ensure(P->A, sizeof(float) * (size_t)P->RLP * (rows_cap > 0 ? rows_cap : 1), "multipoles") ||
+            ensure(P->wrow, sizeof(float) * (size_t)(rows_cap > 0 ? rows_cap : 1), "row weights"))
+            return G3PCF_ERR_ALLOC;
         const std::vector<Tile>& tl = use_tc ? P->tiles_tc : P->tiles;
         const int T = use_tc ? P->T_tc : P->T;
         Tile* d_tl = use_tc ? P->d_tiles_tc.as<Tile>() : P->d_tiles.as<Tile>();
         const int ntiles = (int)tl.size();
         const int part_stride = ntiles * T * T;
-        if (nsegs > 0) {
-            if (ensure(P->d_segs, sizeof(Segment) * nsegs, "segments") ||
-                ensure(P->d_segfirst, 4 * (c.ncat + 1), "segments") ||
-                ensure(P->partials, sizeof(double) * (size_t)part_stride * nsegs, "partials"))
-                return G3PCF_ERR_ALLOC;
-            CK(cudaMemcpyAsync(P->d_segs.p, segs.data(), sizeof(Segment) * nsegs, cudaMemcpyHostToDevice, st));
-            CK(cudaMemcpyAsync(P->d_segfirst.p, segfirst.data(), 4 * (c.ncat + 1), cudaMemcpyHostToDevice, st));
-            if (use_tc) {
-                if (ensure(P->d_cats, 4 * cats.size(), "catalog table") ||
-                    ensure(P->ops, (size_t)4 * P->RL * P_pad * 2, "tensor-core operands"))
-                    return G3PCF_ERR_ALLOC;
-                CK(cudaMemcpyAsync(P->d_cats.p, cats.data(), 4 * cats.size(), cudaMemcpyHostToDevice, st));
-                P->launches += 3;
-                if (launch_split(P->A.as<float>(), P->RLP, P->RL, c.w, P->d_cats.as<int4>(), c.ncat,
-                                 P_pad, P->ops.p, st) != 0)
-                    return fail(G3PCF_ERR_CUDA, "operand split launch failed: %s", cudaGetErrorString(cudaGetLastError()));
-                const int rc = launch_contract_tc(P->ops.p, P_pad, P->RL, d_tl, ntiles,
-                                                  P->d_segs.as<Segment>(), nsegs, P->partials.as<double>(),
-                                                  part_stride, d_status, st);
-                if (rc == -2) return fail(G3PCF_ERR_CUDA, "cuTensorMapEncodeTiled unavailable or failed");
-                if (rc != 0)
-                    return fail(G3PCF_ERR_CUDA, "tensor-core contraction launch failed: %s", cudaGetErrorString(cudaGetLastError()));
-            } else {
-                P->launches += 2;
-                if (launch_contract_fp32(P->A.as<float>(), P->RLP, c.w, d_tl, ntiles,
-                                         P->d_segs.as<Segment>(), nsegs, P->partials.as<double>(),
-                                         part_stride, st) != 0)
-                    return fail(G3PCF_ERR_CUDA, "contraction launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        // segments of every chunk (partial slots are global across chunks)
+        std::vector<std::vector<Segment>> csegs(nchunks);
+        std::vector<int> segfirst(c.ncat + 1, 0);
+        std::vector<std::vector<int>> ccats(nchunks);
+        std::vector<int64_t> cpad(nchunks, 0);
+        int total_segs = 0;
+        for (int64_t ch = 0; ch < nchunks; ++ch) {
+            const int64_t q0 = ch * C, q1 = chunked ? std::min(rows_all, q0 + C) : rows_all;
+            for (int k = 0; k < c.ncat; ++k) {
+                if (ch == 0) segfirst[k] = total_segs;
+                // rows of catalog k inside this pass (A-row coordinates)
+                const int64_t r0 = chunked ? 0 : ((c.ncat > 1) ? c.offs[k] : 0);
+                const int64_t r1 = chunked ? q1 - q0 : ((c.ncat > 1) ? c.offs[k + 1] : c.n_primary);
+                const int64_t len = r1 - r0;
+                if (use_tc) {
+                    // padded primary coordinates: every catalog starts on a k-block
+                    const int64_t plen = (len + KB - 1) / KB * KB;
+                    ccats[ch].insert(ccats[ch].end(), {(int)cpad[ch], (int)r0, (int)len, 0});
+                    int64_t seg = (plen / 8 + KB - 1) / KB * KB;
+                    if (seg < 64 * KB) seg = 64 * KB;
+                    for (int64_t s0 = 0; s0 < plen; s0 += seg) {
+                        Segment sg;
+                        sg.cat = k;
+                        sg.row0 = (int)(cpad[ch] + s0);
+                        sg.row1 = (int)(cpad[ch] + (s0 + seg < plen ? s0 + seg : plen));
+                        csegs[ch].push_back(sg);
+                    }
+                    cpad[ch] += plen;
+                } else {
+                    int64_t seg = len / 32;
+                    if (seg < 8192) seg = 8192;
+                    for (int64_t s0 = r0; s0 < r1; s0 += seg) {
+                        Segment sg;
+                        sg.cat = k;
+                        sg.row0 = (int)s0;
+                        sg.row1 = (int)(s0 + seg < r1 ? s0 + seg : r1);
+                        csegs[ch].push_back(sg);
+                    }
+                }
             }
-            CK(cudaEventRecord(P->ev[3], st));
+            total_segs += (int)csegs[ch].size();
+        }
+        segfirst[c.ncat] = total_segs;
+        if (total_segs > 0) {
+            size_t max_segs = 0, max_cats = 1;
+            int64_t max_pad = 0;
+            for (int64_t ch = 0; ch < nchunks; ++ch) {
+                max_segs = std::max(max_segs, csegs[ch].size());
+                max_cats = std::max(max_cats, ccats[ch].size());
+                max_pad = std::max(max_pad, cpad[ch]);
+            }
+            if (ensure(P->d_segs, sizeof(Segment) * max_segs, "segments") ||
+                ensure(P->d_segfirst, 4 * (c.ncat + 1), "segments") ||
+                ensure(P->partials, sizeof(double) * (size_t)part_stride * total_segs, "partials"))
+                return G3PCF_ERR_ALLOC;
+            if (use_tc && (ensure(P->d_cats, 4 * max_cats, "catalog table") ||
+                           ensure(P->ops, (size_t)4 * P->RL * (max_pad > 0 ? max_pad : 1) * 2,
+                                  "tensor-core operands")))
+                return G3PCF_ERR_ALLOC;
+            CK(cudaMemcpyAsync(P->d_segfirst.p, segfirst.data(), 4 * (c.ncat + 1), cudaMemcpyHostToDevice, st));
+        }
+        float pair_ms_acc = 0.f;
+        (void)pair_ms_acc;
+        int seg_base = 0;
+        for (int64_t ch = 0; ch < nchunks; ++ch) {
+            const int64_t q0 = ch * C, q1 = chunked ? std::min(rows_all, q0 + C) : nprim;
+            if (ch > 0) CK(cudaMemsetAsync(d_queue, 0, sizeof(int), st));
+            if (nprim > 0 && q1 > q0) {
+                PairArgs pa{};
+                pa.pts = ib.pts;
+                pa.pts64 = ib.pts64;
+                pa.orig = ib.orig;
+                pa.cstart = ib.cstart;
+                pa.plist = (c.ncat > 1 || c.n_primary < n) ? ib.plist : nullptr;
+                P->last_plist = pa.plist != nullptr;
+                pa.key = ib.key_sorted;
+                pa.nprim = (int)q1;
+                pa.q0 = (int)q0;
+                pa.chunked = chunked ? 1 : 0;
+                pa.wrow = P->wrow.as<float>();
+                pa.A = P->A.as<float>();
+                pa.RLP = P->RLP;
+                pa.colmap = P->d_colmap.as<int>();
+                pa.colscale = P->d_colscale.as<float>();
+                pa.RL = P->RL;
+                pa.counts = P->counts.as<unsigned long long>();
+                pa.queue = d_queue;
+                pa.status = d_status;
+                pa.kflush = P->kflush;
+                pa.g = g;
+                pa.bins = P->bins;
+                pa.bintab = P->d_bintab.as<unsigned char>();
+                pa.bin_tscale = P->bin_tscale;
+                ++P->launches;
+                if (launch_pair(P->lmax, pa, P->nsm, st) != 0)
+                    return fail(G3PCF_ERR_CUDA, "pair kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+            }
+            if (ch == 0) CK(cudaEventRecord(P->ev[2], st));
+            const std::vector<Segment>& segs = csegs[ch];
+            const int nsegs = (int)segs.size();
+            if (nsegs > 0) {
+                double* part = P->partials.as<double>() + (size_t)seg_base * part_stride;
+                CK(cudaMemcpyAsync(P->d_segs.p, segs.data(), sizeof(Segment) * nsegs, cudaMemcpyHostToDevice, st));
+                if (use_tc) {
+                    CK(cudaMemcpyAsync(P->d_cats.p, ccats[ch].data(), 4 * ccats[ch].size(), cudaMemcpyHostToDevice, st));
+                    P->launches += 2;
+                    if (launch_split(P->A.as<float>(), P->RLP, P->RL, P->wrow.as<float>(), P->d_cats.as<int4>(),
+                                     (int)(ccats[ch].size() / 4), cpad[ch], P->ops.p, st) != 0)
+                        return fail(G3PCF_ERR_CUDA, "operand split launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+                    const int rc = launch_contract_tc(P->ops.p, cpad[ch], P->RL, d_tl, ntiles,
+                                                      P->d_segs.as<Segment>(), nsegs, part, part_stride,
+                                                      d_status, st);
+                    if (rc == -2) return fail(G3PCF_ERR_CUDA, "cuTensorMapEncodeTiled unavailable or failed");
+                    if (rc != 0)
+                        return fail(G3PCF_ERR_CUDA, "tensor-core contraction launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+                } else {
+                    P->launches += 1;
+                    if (launch_contract_fp32(P->A.as<float>(), P->RLP, P->wrow.as<float>(), d_tl, ntiles,
+                                             P->d_segs.as<Segment>(), nsegs, part, part_stride, st) != 0)
+                        return fail(G3PCF_ERR_CUDA, "contraction launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+                }
+            }
+            seg_base += nsegs;
+        }
+        CK(cudaEventRecord(P->ev[3], st));
+        if (total_segs > 0) {
+            P->launches += 1;
             if (launch_reduce(P->partials.as<double>(), part_stride, P->d_segfirst.as<int>(), c.ncat,
                               B, P->lmax, d_tl, T, c.zeta, st, use_tc ? 1 : 0) != 0)
                 return fail(G3PCF_ERR_CUDA, "reduction launch failed: %s", cudaGetErrorString(cudaGetLastError()));
-        } else {
-            CK(cudaEventRecord(P->ev[3], st));
         }
+        P->last_chunked = chunked;
     } else {
         CK(cudaEventRecord(P->ev[1], st));
         CK(cudaEventRecord(P->ev[2], st));
@@ -676,6 +728,8 @@ int g3pcf_alm(g3pcf_plan_t P, const int64_t* primaries, int64_t np, double* out)
     g_err.clear();
     if (int r = check_plan(P)) return r;
     if (!P->have_alm) return fail(G3PCF_ERR_STATE, "no forward with multipoles on this plan");
+    if (P->last_chunked)
+        return fail(G3PCF_ERR_STATE, "the last forward ran in chunks; its multipoles were not kept");
     if (np < 0 || (np > 0 && (!primaries || !out))) return fail(G3PCF_ERR_ARG, "bad primaries/out");
     const int64_t rows = (P->last_ncat > 1) ? P->last_n : P->last_np;
     const int B = P->nbins, L = P->lmax;
@@ -710,6 +764,8 @@ int g3pcf_backward(g3pcf_plan_t P, const double* dzeta, double* dpos, double* dw
     if (P->los_mode == G3PCF_LOS_RADIAL_OPEN)
         return fail(G3PCF_ERR_UNSUPPORTED, "the adjoint supports the z line-of-sight modes only");
     if (P->last_ncat != 1) return fail(G3PCF_ERR_UNSUPPORTED, "the adjoint of a batched call is not built");
+    if (P->last_chunked)
+        return fail(G3PCF_ERR_STATE, "the last forward ran in chunks; rerun it with all primaries in one chunk");
     cudaStream_t st = P->stream;
     const int64_t n = P->last_n, rows = P->last_np;
     CK(cudaMemsetAsync(dpos, 0, sizeof(double) * 3 * (n > 0 ? n : 1), st));
@@ -759,6 +815,31 @@ int g3pcf_backward(g3pcf_plan_t P, const double* dzeta, double* dpos, double* dw
     return read_status(P);
 }
 
+int g3pcf_set_option(g3pcf_plan_t P, int option, int64_t value) {
+    g_err.clear();
+    if (int r = check_plan(P)) return r;
+    switch (option) {
+        case G3PCF_OPT_CHUNK_ROWS:
+            if (value < 0) return fail(G3PCF_ERR_ARG, "chunk rows must be >= 0");
+            P->opt_chunk = value > 0 ? (value + 63) / 64 * 64 : 0;
+            return G3PCF_OK;
+        case G3PCF_OPT_CELLS_PER_RMAX:
+            if (value < 0 || value > 8) return fail(G3PCF_ERR_ARG, "cells per rmax must be in [0, 8]");
+            P->opt_cells = (int)value;
+            return G3PCF_OK;
+        case G3PCF_OPT_KFLUSH: {
+            if (value == 0) return G3PCF_OK;
+            if (value < 2 || value > 16) return fail(G3PCF_ERR_ARG, "kflush must be in [2, 16]");
+            if ((pair_smem_per_warp(P->lmax, P->nbins, (int)value) * 4 + 4096) > 227 * 1024)
+                return fail(G3PCF_ERR_ARG, "kflush %lld does not fit in shared memory", (long long)value);
+            P->kflush = (int)value;
+            return G3PCF_OK;
+        }
+        default:
+            return fail(G3PCF_ERR_ARG, "unknown option %d", option);
+    }
+}
+
 int g3pcf_status(g3pcf_plan_t P) {
     g_err.clear();
     if (int r = check_plan(P)) return r;
@@ -803,7 +884,8 @@ int g3pcf_destroy(g3pcf_plan_t P) {
                       &P->scan_tmp, &P->pts, &P->pts64, &P->orig, &P->cstart, &P->plist,
                       &P->small, &P->counts, &P->A, &P->partials, &P->d_tiles, &P->d_segs,
                       &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_catoff, &P->d_ranges,
-                      &P->d_tiles_tc, &P->ops, &P->d_cats, &P->d_mreal, &P->d_V, &P->d_bintab};
+                      &P->d_tiles_tc, &P->ops, &P->d_cats, &P->d_mreal, &P->d_V, &P->d_bintab,
+                      &P->wrow};
     for (DevBuf* b : bufs) b->release();
     if (P->h_status) cudaFreeHost(P->h_status);
     for (auto& e : P->ev)

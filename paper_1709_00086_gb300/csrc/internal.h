@@ -110,7 +110,10 @@ struct PairArgs {
     const int* cstart;
     const int* plist;        // null = identity (slot q is the q-th primary)
     const unsigned* key;     // sorted cell keys (catalog = key / cells_per_cat)
-    int nprim;               // number of primaries
+    int nprim;               // processing-order index one past the last primary of this launch
+    int q0;                  // processing-order index of the first primary of this launch
+    int chunked;             // 1: A row = q - q0 (chunk-local), 0: A row = original index
+    float* wrow;             // per A row: the primary's weight (forward)
     float* A;                // rows x RLP
     int RLP;
     const int* colmap;       // RL entries: res index (b * NRP + c) feeding A column

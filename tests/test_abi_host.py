@@ -78,3 +78,17 @@ def test_compute_argument_errors_before_device_work():
     assert lib.g3pcf_set_stream(None, None) == -1
     assert lib.g3pcf_destroy(None) == 0
     p.close()
+
+
+def test_set_option_validation():
+    p = g3.Plan(4, 0.0, 10.0, 2, 100.0, 0)
+    p.set_option(g3.OPT_CHUNK_ROWS, 1000)
+    p.set_option(g3.OPT_CHUNK_ROWS, 0)
+    p.set_option(g3.OPT_CELLS_PER_RMAX, 3)
+    p.set_option(g3.OPT_KFLUSH, 8)
+    for opt, val in [(g3.OPT_CHUNK_ROWS, -1), (g3.OPT_CELLS_PER_RMAX, 9), (g3.OPT_KFLUSH, 1),
+                     (g3.OPT_KFLUSH, 17), (99, 1)]:
+        with pytest.raises(g3.G3PCFError) as ei:
+            p.set_option(opt, val)
+        assert ei.value.name == "ERR_ARG"
+    p.close()

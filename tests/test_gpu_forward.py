@@ -193,3 +193,20 @@ def test_batch_tensor_core_path():
         zo, co = oracle_zeta(cat)
         np.testing.assert_array_equal(cb[k].cpu().numpy(), co)
         assert maxrel(zb[k].cpu().numpy(), zo) < TOL_TC
+
+
+@pytest.mark.parametrize("tc", [False, True])
+def test_chunked_passes_match_single_pass(tc):
+    # primaries processed in 5 chunks (multipoles of earlier chunks are
+    # contracted and dropped) give the zeta of a single pass
+    cat = catalogs.clustered_2m(n=30000, seed=15, box=600.0)
+    plan = g3.Plan(**cat.params())
+    pos, w = to_dev(cat, torch)
+    z1, c1 = plan.compute(pos, w, fp32_contraction=not tc)
+    plan.set_option(g3.OPT_CHUNK_ROWS, 6400)
+    z2, c2 = plan.compute(pos, w, fp32_contraction=not tc)
+    assert torch.equal(c1, c2)
+    assert maxrel(z2.cpu().numpy(), z1.cpu().numpy()) < 1e-6
+    with pytest.raises(g3.G3PCFError) as ei:
+        plan.alm([0])
+    assert ei.value.name == "ERR_STATE"

@@ -1,0 +1,123 @@
+"""Full-size runs of the five measured workloads on the GPU.
+
+At full size the oracle cannot redo every pair, so each workload runs in the
+launch configuration the benchmark uses and is checked on what the oracle can
+compute one by one -- a random subset of primaries moved to the front and
+run as the only primaries (all points stay secondaries) -- or, for the
+whole-catalog runs, on properties that hold at any size (Hermitian zeta,
+pair totals, finiteness).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_1709_00086_gb300 as g3  # noqa: E402
+from paper_1709_00086_gb300 import catalogs  # noqa: E402
+
+from gpu_util import maxrel, oracle_zeta, to_dev  # noqa: E402
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+TOL_FP32, TOL_TC = 1e-5, 1e-4
+
+
+def _front(cat, nsample, seed):
+    """The catalog with nsample random points moved to the front."""
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(cat.n, size=nsample, replace=False)
+    order = np.concatenate([pick, np.setdiff1d(np.arange(cat.n), pick)])
+    return catalogs.Catalog(np.ascontiguousarray(cat.pos[order]), np.ascontiguousarray(cat.w[order]),
+                            cat.box, cat.nbins, cat.rmin, cat.rmax, cat.lmax, cat.los_mode)
+
+
+def _hermitian(z, nb, lmax):
+    err = 0.0
+    for blk in g3.zeta_blocks(z, nb, lmax):
+        err = max(err, np.abs(blk - blk.conj().T).max() / max(np.abs(blk).max(), 1e-300))
+    return err
+
+
+def test_plain_uniform_20k_full_parity():
+    cat = catalogs.plain_uniform()
+    plan = g3.Plan(**cat.params())
+    pos, w = to_dev(cat, torch)
+    zo, co = oracle_zeta(cat)
+    for tc in (False, True):
+        z, c = plan.compute(pos, w, fp32_contraction=not tc)
+        np.testing.assert_array_equal(c.cpu().numpy(), co)
+        assert maxrel(z.cpu().numpy(), zo) < (TOL_TC if tc else TOL_FP32)
+
+
+def test_clustered_2m_sampled_primaries():
+    cat = _front(catalogs.clustered_2m(), 400, seed=101)
+    plan = g3.Plan(**cat.params())
+    pos, w = to_dev(cat, torch)
+    z, c = plan.compute(pos, w, n_primary=400)
+    zo, co = oracle_zeta(cat, n_primary=400)
+    np.testing.assert_array_equal(c.cpu().numpy(), co)
+    assert maxrel(z.cpu().numpy(), zo) < TOL_TC
+    # the whole catalog in the benchmark's configuration: properties
+    z, c = plan.compute(pos, w)
+    zc = z.cpu().numpy()
+    assert np.isfinite(zc).all()
+    assert _hermitian(zc, cat.nbins, cat.lmax) < 1e-12
+    assert c.sum().item() > 3.9e10
+
+
+def test_batched_64_catalogs():
+    cats = catalogs.batched()
+    plan = g3.Plan(**cats[0].params())
+    pos = torch.from_numpy(np.concatenate([c.pos for c in cats])).cuda()
+    w = torch.from_numpy(np.concatenate([c.w for c in cats])).cuda()
+    offs = np.cumsum([0] + [c.n for c in cats])
+    zb, cb = plan.compute_batch(pos, w, offs)
+    small = sorted(range(len(cats)), key=lambda k: cats[k].n)[:3]
+    for k in small:  # the smallest catalogs in full
+        zo, co = oracle_zeta(cats[k])
+        np.testing.assert_array_equal(cb[k].cpu().numpy(), co)
+        assert maxrel(zb[k].cpu().numpy(), zo) < TOL_TC
+    big = max(range(len(cats)), key=lambda k: cats[k].n)
+    sub = _front(cats[big], 200, seed=7)  # the largest one on sampled primaries
+    z1, c1 = g3.Plan(**sub.params()).compute(*to_dev(sub, torch), n_primary=200)
+    zo, co = oracle_zeta(sub, n_primary=200)
+    np.testing.assert_array_equal(c1.cpu().numpy(), co)
+    assert maxrel(z1.cpu().numpy(), zo) < TOL_TC
+    for k in range(len(cats)):
+        assert _hermitian(zb[k].cpu().numpy(), cats[k].nbins, cats[k].lmax) < 1e-12
+
+
+def test_differentiation_500k_forward_and_adjoint():
+    cat = catalogs.differentiation()
+    tgt = catalogs.differentiation(seed=5)
+    plan = g3.Plan(**cat.params())
+    pos, w = to_dev(cat, torch)
+    pos.requires_grad_(True)
+    w.requires_grad_(True)
+    zt = g3.Plan(**tgt.params()).compute(*to_dev(tgt, torch), fp32_contraction=True)[0]
+    z = g3.zeta(pos, w, plan, fp32_contraction=True)
+    loss = ((z - torch.view_as_real(zt)) ** 2).sum()
+    gpos, gw = torch.autograd.grad(loss, [pos, w])
+    assert torch.isfinite(gpos).all() and torch.isfinite(gw).all()
+    # translation invariance of the periodic loss: position gradients sum to ~0
+    s = gpos.double().sum(0).abs().max().item()
+    assert s < 1e-3 * gpos.double().abs().max().item()
+
+
+def test_large_radial_50m():
+    cat = catalogs.large_radial()
+    sub = _front(cat, 150, seed=17)
+    plan = g3.Plan(**sub.params())
+    pos, w = to_dev(sub, torch)
+    z, c = plan.compute(pos, w, n_primary=150)
+    zo, co = oracle_zeta(sub, n_primary=150)
+    np.testing.assert_array_equal(c.cpu().numpy(), co)
+    assert maxrel(z.cpu().numpy(), zo) < TOL_TC
+    # the whole catalog (chunked automatically): properties
+    z, c = plan.compute(pos, w)
+    zc = z.cpu().numpy()
+    assert np.isfinite(zc).all()
+    assert _hermitian(zc, sub.nbins, sub.lmax) < 1e-12
+    assert c.sum().item() > 1e12
