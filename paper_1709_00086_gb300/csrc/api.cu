@@ -446,7 +446,7 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
         for (int64_t ch = 0; ch < nchunks; ++ch) {
             const int64_t q0 = ch * C, q1 = chunked ? std::min(rows_all, q0 + C) : rows_all;
             for (int k = 0; k < c.ncat; ++k) {
-                if (ch == 0) segfirst[k] = total_segs;
+                if (ch == 0) segfirst[k] = total_segs + (int)csegs[ch].size();
                 // rows of catalog k inside this pass (A-row coordinates)
                 const int64_t r0 = chunked ? 0 : ((c.ncat > 1) ? c.offs[k] : 0);
                 const int64_t r1 = chunked ? q1 - q0 : ((c.ncat > 1) ? c.offs[k + 1] : c.n_primary);
