@@ -50,6 +50,12 @@ def zeta_flops_per_primary(nbins: int, L: int) -> int:
     return sum(4 * (nbins * (L + 1 - m)) * (nbins * (L + 1 - m) + 1) for m in range(L + 1))
 
 
+# DRAM bytes of one pair-stage launch per primary, from the ncu capture
+# summarised in profiles/k_pair_clustered_203k_L700.md (0.972 GB for 203,000
+# primaries: one 4.86 KB multipole row each); traffic grows with primaries.
+PAIR_DRAM_BYTES_PER_PRIMARY = 0.972e9 / 203000
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -273,7 +279,8 @@ def run_ours(args):
                       "contract_ms": con_32, "zeta_tflops": zf / (con_32 / 1e3) / 1e12,
                       "max_rel_diff_vs_tc": diff},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": None,
+                     "frac": achieved / fp32_peak,
+                     "traffic": PAIR_DRAM_BYTES_PER_PRIMARY * nprim if L == 10 else None,
                      "kernel": "k_pair (FP32 FMA pipe; peak = 2 x 128 FP32 lanes x %d SMs x %.0f MHz)" % (n_sm, clk_max),
                      "flops_per_pair": pair_flops(L)},
         "e2e": {"value": e2e_val, "unit": "pairs/s",
