@@ -87,8 +87,14 @@ enum {
                                    of split-BF16 (hi+lo, 3 products) tcgen05 tensor cores */
     G3PCF_F_NO_SYNC = 4,        /* do not synchronise at the end; device status is then
                                    read by g3pcf_status()                                 */
-    G3PCF_F_KEEP_ALM = 8        /* keep the multipoles of the call for g3pcf_alm and
+    G3PCF_F_KEEP_ALM = 8,       /* keep the multipoles of the call for g3pcf_alm and
                                    g3pcf_backward (implied when requires_grad is used)    */
+    G3PCF_F_GRAPH = 16          /* replay a captured CUDA graph: the first call with a new
+                                   signature (pointers, sizes, offsets, flags, options) runs
+                                   once and captures its device work on an internal stream;
+                                   later calls with the same signature replay it, ordered
+                                   after the plan's stream.  A call without this flag drops
+                                   the graph.                                             */
 };
 
 /* Limits of this build. */
@@ -148,6 +154,16 @@ int g3pcf_backward(g3pcf_plan_t plan, const double* dzeta, double* dpos, double*
  * out: HOST, np x nbins x ((lmax+1)(lmax+2)/2) complex (re, im doubles),
  * index [k][b][l(l+1)/2 + m].  Synchronises the plan's stream. */
 int g3pcf_alm(g3pcf_plan_t plan, const int64_t* primaries, int64_t np, double* out);
+
+/* Autotuner (a project-written search, not in the paper): times the pair stage
+ * on a bounded sample (the first min(n, 8192) points as primaries, all n as
+ * secondaries) for cell resolutions around the density heuristic and two flush
+ * sizes, and keeps the fastest on the plan (as if set with g3pcf_set_option).
+ * pos/w as for g3pcf_compute_ex (flags: G3PCF_F_POS_F64 only).  chosen (HOST,
+ * may be NULL) receives {cells per rmax, kflush, pair-stage microseconds}.
+ * Allocates a temporary zeta buffer; synchronises the plan's stream. */
+int g3pcf_autotune(g3pcf_plan_t plan, const void* pos, const float* w, int64_t n, int flags,
+                   int64_t* chosen);
 
 /* Status word of the last G3PCF_F_NO_SYNC call (synchronises the stream):
  * returns G3PCF_OK or the error the call would have returned. */

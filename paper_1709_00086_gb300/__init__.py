@@ -22,7 +22,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "g3pcf.h")
 
 LOS_Z_PERIODIC, LOS_Z_OPEN, LOS_RADIAL_OPEN = 0, 1, 2
 OPT_CHUNK_ROWS, OPT_CELLS_PER_RMAX, OPT_KFLUSH = 1, 2, 3
-F_POS_F64, F_CONTRACT_FP32, F_NO_SYNC, F_KEEP_ALM = 1, 2, 4, 8
+F_POS_F64, F_CONTRACT_FP32, F_NO_SYNC, F_KEEP_ALM, F_GRAPH = 1, 2, 4, 8, 16
 ERRORS = {0: "OK", -1: "ERR_ARG", -2: "ERR_RANGE", -3: "ERR_RMAX", -4: "ERR_ALLOC",
           -5: "ERR_CUDA", -6: "ERR_TIMEOUT", -7: "ERR_STATE", -8: "ERR_UNSUPPORTED"}
 
@@ -59,6 +59,8 @@ def lib():
         L.g3pcf_status.argtypes = [P]
         L.g3pcf_stats.argtypes = [P, P, I]
         L.g3pcf_destroy.argtypes = [P]
+        L.g3pcf_autotune.argtypes = [P, P, P, I64, I, P]
+        L.g3pcf_autotune.restype = I
         L.g3pcf_set_option.argtypes = [P, I, I64]
         L.g3pcf_set_option.restype = I
         L.g3pcf_zeta_from_alm_noalloc.argtypes = [I, I, P, I64, P, I64, P, P]
@@ -121,7 +123,7 @@ class Plan:
         _check(lib().g3pcf_set_stream(self._h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
 
     def compute(self, pos, w, n_primary=None, fp32_contraction=False, keep_alm=False,
-                with_counts=True, sync=True, out=None):
+                with_counts=True, sync=True, out=None, graph=False, counts_out=None):
         """zeta (complex128 tensor, zsize) and counts (int64 tensor, nbins) on pos's device."""
         import torch
         if not (pos.is_cuda and w.is_cuda):
@@ -144,9 +146,14 @@ class Plan:
             flags |= F_KEEP_ALM
         if not sync:
             flags |= F_NO_SYNC
+        if graph:
+            flags |= F_GRAPH
         zeta = out if out is not None else torch.empty((self.zsize, 2), dtype=torch.float64,
                                                        device=pos.device)
-        counts = torch.empty(self.nbins, dtype=torch.int64, device=pos.device) if with_counts else None
+        counts = None
+        if with_counts:
+            counts = counts_out if counts_out is not None else torch.empty(
+                self.nbins, dtype=torch.int64, device=pos.device)
         npri = -1 if n_primary is None else int(n_primary)
         self._stream()
         _check(lib().g3pcf_compute_ex(self._h, _ptr(pos), _ptr(w), n, npri, _ptr(zeta), _ptr(counts),
@@ -155,16 +162,23 @@ class Plan:
         self._token += 1
         return torch.view_as_complex(zeta), counts
 
-    def compute_batch(self, pos, w, offsets, fp32_contraction=False, sync=True):
-        """Batched zeta over catalogs [offsets[c], offsets[c+1]): (ncat, zsize) complex."""
+    def compute_batch(self, pos, w, offsets, fp32_contraction=False, sync=True, graph=False,
+                      out=None, counts_out=None):
+        """Batched zeta over catalogs [offsets[c], offsets[c+1]): (ncat, zsize) complex.
+
+        graph=True replays a captured CUDA graph for repeated calls with the same
+        buffers (pass the same out/counts_out tensors)."""
         import torch
         pos = pos.contiguous()
         w = w.contiguous()
         offs = np.ascontiguousarray(offsets, dtype=np.int64)
         ncat = offs.size - 1
-        zeta = torch.empty((ncat, self.zsize, 2), dtype=torch.float64, device=pos.device)
-        counts = torch.empty((ncat, self.nbins), dtype=torch.int64, device=pos.device)
-        flags = (F_CONTRACT_FP32 if fp32_contraction else 0) | (0 if sync else F_NO_SYNC)
+        zeta = out if out is not None else torch.empty((ncat, self.zsize, 2), dtype=torch.float64,
+                                                       device=pos.device)
+        counts = counts_out if counts_out is not None else torch.empty(
+            (ncat, self.nbins), dtype=torch.int64, device=pos.device)
+        flags = ((F_CONTRACT_FP32 if fp32_contraction else 0) | (0 if sync else F_NO_SYNC) |
+                 (F_GRAPH if graph else 0))
         self._stream()
         self._token += 1
         self._last_n = 0
@@ -192,6 +206,18 @@ class Plan:
         self._stream()
         _check(lib().g3pcf_backward(self._h, _ptr(dz), _ptr(dpos), _ptr(dw)))
         return dpos, dw
+
+    def autotune(self, pos, w) -> dict:
+        """Pick cells-per-rmax and flush size for this data (see g3pcf_autotune)."""
+        import torch
+        pos = pos.contiguous()
+        w = w.contiguous()
+        flags = F_POS_F64 if pos.dtype == torch.float64 else 0
+        out = np.zeros(3, dtype=np.int64)
+        self._stream()
+        _check(lib().g3pcf_autotune(self._h, _ptr(pos), _ptr(w), pos.shape[0], flags,
+                                    out.ctypes.data_as(ctypes.c_void_p)))
+        return {"cells_per_rmax": int(out[0]), "kflush": int(out[1]), "pair_us": int(out[2])}
 
     def set_option(self, option: int, value: int):
         """Tuning knob (OPT_CHUNK_ROWS, OPT_CELLS_PER_RMAX, OPT_KFLUSH; 0 = automatic)."""

@@ -91,6 +91,17 @@ struct g3pcf_plan_s {
     DevBuf counts, A, partials, d_tiles, d_segs, d_segfirst, d_colmap, d_colscale, d_catoff;
     DevBuf d_ranges, d_tiles_tc, ops, d_cats, d_mreal, d_V, d_bintab, wrow;
     int64_t opt_chunk = 0;   // G3PCF_OPT_CHUNK_ROWS
+    // pinned staging for host -> device tables (capturable copies); offset
+    // restarts at every forward
+    unsigned char* h_stage = nullptr;
+    size_t stage_cap = 0, stage_off = 0;
+    bool capturing = false;
+    int64_t fixed_chunk = -1;  // chunk size frozen for a captured graph
+    // CUDA graph of the last G3PCF_F_GRAPH call
+    cudaStream_t gstream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<long long> gkey;
+    cudaEvent_t gev[2] = {};
     int opt_cells = 0;       // G3PCF_OPT_CELLS_PER_RMAX
     bool last_chunked = false;
     std::vector<unsigned char> bintab;  // r^2 -> bin lookup (see compute_bins)
@@ -115,6 +126,40 @@ struct g3pcf_plan_s {
 };
 
 namespace {
+
+// Copy a host table to the device through the plan's pinned staging buffer
+// so that the copy can be captured into a CUDA graph (replays read the same
+// staging bytes, which the capturing call has filled).
+int upload(g3pcf_plan_t P, void* dev, const void* host, size_t bytes, cudaStream_t st) {
+    if (bytes == 0) return 0;
+    const size_t off = (P->stage_off + 255) & ~(size_t)255;
+    if (off + bytes > P->stage_cap) {
+        if (P->capturing)
+            return fail(G3PCF_ERR_CUDA, "staging buffer too small during graph capture");
+        // a fresh buffer: the old one may still be read by copies in flight
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail(G3PCF_ERR_CUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e));
+        if (P->h_stage) cudaFreeHost(P->h_stage);
+        P->h_stage = nullptr;
+        size_t cap = (off + bytes) * 2 + 65536;
+        if (cudaHostAlloc(reinterpret_cast<void**>(&P->h_stage), cap, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            P->stage_cap = 0;
+            return fail(G3PCF_ERR_ALLOC, "pinned staging allocation failed");
+        }
+        P->stage_cap = cap;
+    }
+    std::memcpy(P->h_stage + off, host, bytes);
+    P->stage_off = off + bytes;
+    cudaError_t e = cudaMemcpyAsync(dev, P->h_stage + off, bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail(G3PCF_ERR_CUDA, "cudaMemcpyAsync: %s", cudaGetErrorString(e));
+    return 0;
+}
+
+#define UP(dev, host, bytes)                                     \
+    do {                                                         \
+        if (int r_ = upload(P, (dev), (host), (bytes), st)) return r_; \
+    } while (0)
 
 int setup_device(g3pcf_plan_t P) {
     if (P->device >= 0) return 0;
@@ -311,6 +356,7 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
     P->have_forward = false;
     P->have_alm = false;
     P->launches = 0;
+    P->stage_off = 0;
     CK(cudaEventRecord(P->ev[0], st));
     // zero outputs and counters
     if (ensure(P->small, 256, "status")) return G3PCF_ERR_ALLOC;
@@ -372,7 +418,7 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
         const PrimRanges* prp = nullptr;
         if (c.ncat > 1) {
             if (ensure(P->d_catoff, 8 * (c.ncat + 1), "offsets")) return G3PCF_ERR_ALLOC;
-            CK(cudaMemcpyAsync(P->d_catoff.p, c.offs.data(), 8 * (c.ncat + 1), cudaMemcpyHostToDevice, st));
+            UP(P->d_catoff.p, c.offs.data(), 8 * (c.ncat + 1));
             d_catoff = P->d_catoff.as<int64_t>();
             // processing order: catalogs by decreasing size (heaviest first)
             std::vector<int> order(c.ncat);
@@ -390,7 +436,7 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
                 o += rs[c.ncat + k];
             }
             if (ensure(P->d_ranges, 4 * rs.size(), "ranges")) return G3PCF_ERR_ALLOC;
-            CK(cudaMemcpyAsync(P->d_ranges.p, rs.data(), 4 * rs.size(), cudaMemcpyHostToDevice, st));
+            UP(P->d_ranges.p, rs.data(), 4 * rs.size());
             pr.start = P->d_ranges.as<int>();
             pr.len = pr.start + c.ncat;
             pr.out = pr.start + 2 * c.ncat;
@@ -415,6 +461,8 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
         if (c.ncat == 1) {
             if (P->opt_chunk > 0) {
                 C = P->opt_chunk;
+            } else if (P->capturing && P->fixed_chunk > 0) {
+                C = P->fixed_chunk;
             } else {
                 size_t fr = 0, tot = 0;
                 CK(cudaMemGetInfo(&fr, &tot));
@@ -427,6 +475,7 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
             if (C > rows_all) C = rows_all;
         }
         const bool chunked = (c.ncat == 1) && C < rows_all;
+        P->fixed_chunk = C;
         const int64_t nchunks = chunked ? (rows_all + C - 1) / C : 1;
         const int64_t rows_cap = chunked ? C : rows_all;
         if (ensure(P->A, sizeof(float) * (size_t)P->RLP * (rows_cap > 0 ? rows_cap : 1), "multipoles") ||
@@ -496,7 +545,7 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
                            ensure(P->ops, (size_t)4 * P->RL * (max_pad > 0 ? max_pad : 1) * 2,
                                   "tensor-core operands")))
                 return G3PCF_ERR_ALLOC;
-            CK(cudaMemcpyAsync(P->d_segfirst.p, segfirst.data(), 4 * (c.ncat + 1), cudaMemcpyHostToDevice, st));
+            UP(P->d_segfirst.p, segfirst.data(), 4 * (c.ncat + 1));
         }
         float pair_ms_acc = 0.f;
         (void)pair_ms_acc;
@@ -539,9 +588,9 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
             const int nsegs = (int)segs.size();
             if (nsegs > 0) {
                 double* part = P->partials.as<double>() + (size_t)seg_base * part_stride;
-                CK(cudaMemcpyAsync(P->d_segs.p, segs.data(), sizeof(Segment) * nsegs, cudaMemcpyHostToDevice, st));
+                UP(P->d_segs.p, segs.data(), sizeof(Segment) * nsegs);
                 if (use_tc) {
-                    CK(cudaMemcpyAsync(P->d_cats.p, ccats[ch].data(), 4 * ccats[ch].size(), cudaMemcpyHostToDevice, st));
+                    UP(P->d_cats.p, ccats[ch].data(), 4 * ccats[ch].size());
                     P->launches += 2;
                     if (launch_split(P->A.as<float>(), P->RLP, P->RL, P->wrow.as<float>(), P->d_cats.as<int4>(),
                                      (int)(ccats[ch].size() / 4), cpad[ch], P->ops.p, st) != 0)
@@ -590,6 +639,74 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
     P->stats[6] = (double)nprim;
     if (c.flags & G3PCF_F_NO_SYNC) return G3PCF_OK;
     CK(cudaStreamSynchronize(st));
+    return read_status(P);
+}
+
+// G3PCF_F_GRAPH: the first call with a new signature runs once normally (all
+// allocations, staging sizes and the chunk size settle), then captures the
+// same device work into a CUDA graph on an internal stream; calls with the
+// same signature replay the graph, ordered after the plan's stream.
+int forward_entry(g3pcf_plan_t P, CallSpec& c) {
+    if (!(c.flags & G3PCF_F_GRAPH)) {
+        if (P->gexec) {  // a plain forward reuses the staging buffer: drop the graph
+            cudaGraphExecDestroy(P->gexec);
+            P->gexec = nullptr;
+        }
+        return run_forward(P, c);
+    }
+    if (int r = setup_device(P)) return r;
+    std::vector<long long> key = {(long long)(intptr_t)c.pos, (long long)(intptr_t)c.w,
+                                  (long long)(intptr_t)c.zeta, (long long)(intptr_t)c.counts,
+                                  (long long)c.n, (long long)c.n_primary, (long long)c.ncat,
+                                  (long long)c.pos_f64,
+                                  (long long)(c.flags & ~(G3PCF_F_NO_SYNC | G3PCF_F_GRAPH)),
+                                  (long long)P->opt_chunk, (long long)P->opt_cells, (long long)P->kflush};
+    key.insert(key.end(), c.offs.begin(), c.offs.end());
+    if (!P->gstream) {
+        CK(cudaStreamCreateWithFlags(&P->gstream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&P->gev[0], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&P->gev[1], cudaEventDisableTiming));
+    }
+    cudaStream_t user = P->stream;
+    if (!(P->gexec && key == P->gkey)) {
+        if (P->gexec) {
+            cudaGraphExecDestroy(P->gexec);
+            P->gexec = nullptr;
+        }
+        CallSpec warm = c;
+        warm.flags &= ~(G3PCF_F_GRAPH | G3PCF_F_NO_SYNC);
+        if (int r = run_forward(P, warm)) return r;
+        CallSpec cap = c;
+        cap.flags = (c.flags & ~G3PCF_F_GRAPH) | G3PCF_F_NO_SYNC;
+        P->stream = P->gstream;
+        P->capturing = true;
+        cudaError_t e = cudaStreamBeginCapture(P->gstream, cudaStreamCaptureModeThreadLocal);
+        int r = (e == cudaSuccess) ? run_forward(P, cap)
+                                   : fail(G3PCF_ERR_CUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(P->gstream, &graph);
+        P->stream = user;
+        P->capturing = false;
+        if (r != 0 || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return r != 0 ? r : fail(G3PCF_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e2));
+        }
+        e = cudaGraphInstantiate(&P->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            P->gexec = nullptr;
+            return fail(G3PCF_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        }
+        P->gkey = key;
+    }
+    CK(cudaEventRecord(P->gev[0], user));
+    CK(cudaStreamWaitEvent(P->gstream, P->gev[0], 0));
+    CK(cudaGraphLaunch(P->gexec, P->gstream));
+    CK(cudaEventRecord(P->gev[1], P->gstream));
+    CK(cudaStreamWaitEvent(user, P->gev[1], 0));
+    if (c.flags & G3PCF_F_NO_SYNC) return G3PCF_OK;
+    CK(cudaStreamSynchronize(user));
     return read_status(P);
 }
 
@@ -675,7 +792,8 @@ int g3pcf_compute_ex(g3pcf_plan_t P, const void* pos, const float* w, int64_t n,
     if (n >= G3PCF_MAX_POINTS) return fail(G3PCF_ERR_ARG, "n must be < 2^27");
     if (!zeta) return fail(G3PCF_ERR_ARG, "zeta is NULL");
     if (n > 0 && (!pos || !w)) return fail(G3PCF_ERR_ARG, "pos or w is NULL");
-    if (flags & ~(G3PCF_F_POS_F64 | G3PCF_F_CONTRACT_FP32 | G3PCF_F_NO_SYNC | G3PCF_F_KEEP_ALM))
+    if (flags & ~(G3PCF_F_POS_F64 | G3PCF_F_CONTRACT_FP32 | G3PCF_F_NO_SYNC | G3PCF_F_KEEP_ALM |
+                  G3PCF_F_GRAPH))
         return fail(G3PCF_ERR_ARG, "unknown flags 0x%x", flags);
     if (n_primary < 0 || n_primary > n) n_primary = n;
     CallSpec c;
@@ -689,7 +807,7 @@ int g3pcf_compute_ex(g3pcf_plan_t P, const void* pos, const float* w, int64_t n,
     c.zeta = zeta;
     c.counts = counts;
     c.flags = flags;
-    return run_forward(P, c);
+    return forward_entry(P, c);
 }
 
 int g3pcf_compute(g3pcf_plan_t P, const float* pos, const float* w, int64_t n, double* zeta) {
@@ -702,7 +820,7 @@ int g3pcf_compute_batch(g3pcf_plan_t P, const float* pos, const float* w, const 
     if (int r = check_plan(P)) return r;
     if (!offsets || ncat < 1) return fail(G3PCF_ERR_ARG, "need ncat >= 1 and offsets");
     if (!zeta) return fail(G3PCF_ERR_ARG, "zeta is NULL");
-    if (flags & ~(G3PCF_F_CONTRACT_FP32 | G3PCF_F_NO_SYNC | G3PCF_F_KEEP_ALM))
+    if (flags & ~(G3PCF_F_CONTRACT_FP32 | G3PCF_F_NO_SYNC | G3PCF_F_KEEP_ALM | G3PCF_F_GRAPH))
         return fail(G3PCF_ERR_ARG, "unsupported flags 0x%x for batch", flags);
     if (offsets[0] != 0) return fail(G3PCF_ERR_ARG, "offsets[0] must be 0");
     for (int k = 0; k < ncat; ++k)
@@ -721,7 +839,7 @@ int g3pcf_compute_batch(g3pcf_plan_t P, const float* pos, const float* w, const 
     c.zeta = zeta;
     c.counts = counts;
     c.flags = flags;
-    return run_forward(P, c);
+    return forward_entry(P, c);
 }
 
 int g3pcf_alm(g3pcf_plan_t P, const int64_t* primaries, int64_t np, double* out) {
@@ -840,6 +958,87 @@ int g3pcf_set_option(g3pcf_plan_t P, int option, int64_t value) {
     }
 }
 
+int g3pcf_autotune(g3pcf_plan_t P, const void* pos, const float* w, int64_t n, int flags,
+                   int64_t* chosen) {
+    g_err.clear();
+    if (int r = check_plan(P)) return r;
+    if (n <= 0 || !pos || !w) return fail(G3PCF_ERR_ARG, "autotune needs n > 0 points");
+    if (n >= G3PCF_MAX_POINTS) return fail(G3PCF_ERR_ARG, "n must be < 2^27");
+    if (flags & ~G3PCF_F_POS_F64) return fail(G3PCF_ERR_ARG, "autotune accepts G3PCF_F_POS_F64 only");
+    if (int r = setup_device(P)) return r;
+    const int64_t zs = zsize_of(P->nbins, P->lmax);
+    double* ztmp = nullptr;
+    if (cudaMalloc(&ztmp, sizeof(double) * 2 * zs) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(G3PCF_ERR_ALLOC, "autotune scratch allocation failed");
+    }
+    // heuristic resolution and the largest flush size that fits
+    const double density = (double)n / (P->box * P->box * P->box);
+    int s0 = (int)std::floor(P->rmax / std::cbrt(48.0 / density));
+    s0 = s0 < 1 ? 1 : (s0 > 8 ? 8 : s0);
+    int kmax = 2;
+    for (int kf = 16; kf >= 2; --kf)
+        if ((pair_smem_per_warp(P->lmax, P->nbins, kf) * 4 + 4096) * 2 <= 227 * 1024) {
+            kmax = kf;
+            break;
+        }
+    const int64_t saved_cells = P->opt_cells, saved_chunk = P->opt_chunk;
+    const int saved_kf = P->kflush;
+    double best = 1e300;
+    int best_s = s0, best_kf = kmax;
+    int rc = G3PCF_OK;
+    for (int s = s0 - 1; s <= s0 + 2 && rc == G3PCF_OK; ++s) {
+        if (s < 1 || s > 8) continue;
+        for (int kf : {kmax, kmax > 6 ? kmax - 4 : kmax}) {
+            P->opt_cells = s;
+            P->kflush = kf;
+            CallSpec c;
+            c.pos = pos;
+            c.w = w;
+            c.n = n;
+            c.n_primary = n < 8192 ? n : 8192;  // a bounded sample of primaries
+            c.pos_f64 = (flags & G3PCF_F_POS_F64) ? 1 : 0;
+            c.ncat = 1;
+            c.offs = {0, n};
+            c.zeta = ztmp;
+            c.counts = nullptr;
+            c.flags = G3PCF_F_CONTRACT_FP32;
+            double t = 0;
+            for (int rep = 0; rep < 2 && rc == G3PCF_OK; ++rep) {
+                rc = run_forward(P, c);
+                if (rc == G3PCF_OK && rep == 1) {
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, P->ev[1], P->ev[2]);
+                    t = ms;
+                }
+            }
+            if (rc == G3PCF_OK && t < best) {
+                best = t;
+                best_s = s;
+                best_kf = kf;
+            }
+            if (kf == (kmax > 6 ? kmax - 4 : kmax)) break;
+        }
+    }
+    cudaFree(ztmp);
+    P->have_forward = false;
+    P->have_alm = false;
+    P->opt_chunk = saved_chunk;
+    if (rc != G3PCF_OK) {
+        P->opt_cells = (int)saved_cells;
+        P->kflush = saved_kf;
+        return rc;
+    }
+    P->opt_cells = best_s;
+    P->kflush = best_kf;
+    if (chosen) {
+        chosen[0] = best_s;
+        chosen[1] = best_kf;
+        chosen[2] = (int64_t)(best * 1000.0);
+    }
+    return G3PCF_OK;
+}
+
 int g3pcf_status(g3pcf_plan_t P) {
     g_err.clear();
     if (int r = check_plan(P)) return r;
@@ -888,6 +1087,11 @@ int g3pcf_destroy(g3pcf_plan_t P) {
                       &P->wrow};
     for (DevBuf* b : bufs) b->release();
     if (P->h_status) cudaFreeHost(P->h_status);
+    if (P->h_stage) cudaFreeHost(P->h_stage);
+    if (P->gexec) cudaGraphExecDestroy(P->gexec);
+    if (P->gstream) cudaStreamDestroy(P->gstream);
+    for (auto& e : P->gev)
+        if (e) cudaEventDestroy(e);
     for (auto& e : P->ev)
         if (e) cudaEventDestroy(e);
     delete P;

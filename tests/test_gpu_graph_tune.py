@@ -1,0 +1,84 @@
+"""CUDA-graph replay of the batched forward and the autotuner.
+
+A captured graph must reproduce the plain call bit for bit (same kernels and
+inputs; every reduction has a fixed order), and a replay after the input
+buffers were overwritten in place must compute the new data.  The autotuner
+must return settings inside their ranges and leave the plan producing the
+oracle's counts and zeta.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1709_00086_gb300 as g3  # noqa: E402
+from paper_1709_00086_gb300 import catalogs  # noqa: E402
+
+from gpu_util import maxrel, oracle_zeta, to_dev  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(seed):
+    cats = catalogs.batched(ncat=5, seed=seed, sizes=[900, 3000, 50, 1800, 400], box=400.0)
+    pos = np.concatenate([c.pos for c in cats])
+    w = np.concatenate([c.w for c in cats])
+    offs = np.cumsum([0] + [c.n for c in cats])
+    return cats, pos, w, offs
+
+
+@pytest.mark.parametrize("tc", [False, True])
+def test_graph_replay_matches_plain_and_follows_new_data(tc):
+    cats, pos, w, offs = _batch(9)
+    plan = g3.Plan(**cats[0].params())
+    dpos = torch.from_numpy(pos).cuda()
+    dw = torch.from_numpy(w).cuda()
+    z0, c0 = plan.compute_batch(dpos, dw, offs, fp32_contraction=not tc)
+    zbuf = torch.empty((len(cats), plan.zsize, 2), dtype=torch.float64, device="cuda")
+    cbuf = torch.empty((len(cats), plan.nbins), dtype=torch.int64, device="cuda")
+    for _ in range(3):  # capture, then two replays
+        z1, c1 = plan.compute_batch(dpos, dw, offs, fp32_contraction=not tc, graph=True,
+                                    out=zbuf, counts_out=cbuf)
+        assert torch.equal(z1, z0) and torch.equal(c1, c0)
+    # new data in the same buffers: the replay computes it
+    cats2, pos2, w2, _ = _batch(10)
+    dpos.copy_(torch.from_numpy(pos2))
+    dw.copy_(torch.from_numpy(w2))
+    z2, c2 = plan.compute_batch(dpos, dw, offs, fp32_contraction=not tc, graph=True,
+                                out=zbuf, counts_out=cbuf)
+    for k, cat in enumerate(cats2):
+        zo, co = oracle_zeta(cat)
+        np.testing.assert_array_equal(c2[k].cpu().numpy(), co)
+        if np.abs(zo).max() > 0:
+            assert maxrel(z2[k].cpu().numpy(), zo) < (1e-4 if tc else 1e-5)
+
+
+def test_graph_single_catalog_and_plain_call_drops_graph():
+    cat = catalogs.small_case("clustered", 5000, seed=3, box=300.0, nbins=6, rmin=0.0, rmax=60.0,
+                              lmax=6)
+    plan = g3.Plan(**cat.params())
+    pos, w = to_dev(cat, torch)
+    zb = torch.empty((plan.zsize, 2), dtype=torch.float64, device="cuda")
+    cb = torch.empty(plan.nbins, dtype=torch.int64, device="cuda")
+    za, ca = plan.compute(pos, w, n_primary=700, graph=True, out=zb, counts_out=cb)
+    za = za.clone()
+    zp, cp = plan.compute(pos, w, n_primary=300)  # a plain call in between
+    zc, cc = plan.compute(pos, w, n_primary=700, graph=True, out=zb, counts_out=cb)
+    assert torch.equal(za, zc)
+    zo, co = oracle_zeta(cat, n_primary=700)
+    np.testing.assert_array_equal(cc.cpu().numpy(), co)
+    assert maxrel(zc.cpu().numpy(), zo) < 1e-4
+
+
+def test_autotune_choices_and_result():
+    cat = catalogs.clustered_2m(n=60000, seed=21, box=700.0)
+    plan = g3.Plan(**cat.params())
+    pos, w = to_dev(cat, torch)
+    best = plan.autotune(pos, w)
+    assert 1 <= best["cells_per_rmax"] <= 8 and 2 <= best["kflush"] <= 16 and best["pair_us"] > 0
+    z, c = plan.compute(pos, w, n_primary=300)
+    zo, co = oracle_zeta(cat, n_primary=300)
+    np.testing.assert_array_equal(c.cpu().numpy(), co)
+    assert maxrel(z.cpu().numpy(), zo) < 1e-4
