@@ -209,9 +209,25 @@ int g3pcf_zeta_from_alm_noalloc(int nbins, int lmax, const float* alm, int64_t l
  *                             after a chunked forward g3pcf_alm and g3pcf_backward
  *                             return G3PCF_ERR_STATE
  *   G3PCF_OPT_CELLS_PER_RMAX  cell-list resolution s (cell side >= rmax / s, 1..8)
- *   G3PCF_OPT_KFLUSH          pairs per lane per bucket flush (2..16)
+ *   G3PCF_OPT_KFLUSH          pairs per lane per bucket flush of the fused pair
+ *                             kernel (2..16)
+ *   G3PCF_OPT_PAIR_KERNELS    forward pair stage: 1 = the fused kernel (bucket and
+ *                             accumulate in one pass), 2 = pair lists (count, scan
+ *                             into per-bin lists of 32 pairs, accumulate; one host
+ *                             synchronisation per chunk of primaries), 0 = lists
+ *                             except inside a captured graph (G3PCF_F_GRAPH), which
+ *                             always uses the fused kernel
+ *   G3PCF_OPT_LIST_BYTES      device bytes for the pair lists (0: up to 40% of free
+ *                             memory, at most 32 GB); more pairs than fit are
+ *                             processed in several passes
  * Returns G3PCF_ERR_ARG for unknown options or values out of range. */
-enum { G3PCF_OPT_CHUNK_ROWS = 1, G3PCF_OPT_CELLS_PER_RMAX = 2, G3PCF_OPT_KFLUSH = 3 };
+enum {
+    G3PCF_OPT_CHUNK_ROWS = 1,
+    G3PCF_OPT_CELLS_PER_RMAX = 2,
+    G3PCF_OPT_KFLUSH = 3,
+    G3PCF_OPT_PAIR_KERNELS = 4,
+    G3PCF_OPT_LIST_BYTES = 5
+};
 int g3pcf_set_option(g3pcf_plan_t plan, int option, int64_t value);
 
 /* Destroy a plan and free its workspace (synchronises its stream). */

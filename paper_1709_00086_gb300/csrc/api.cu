@@ -103,6 +103,15 @@ struct g3pcf_plan_s {
     std::vector<long long> gkey;
     cudaEvent_t gev[2] = {};
     int opt_cells = 0;       // G3PCF_OPT_CELLS_PER_RMAX
+    int opt_pair = 0;        // G3PCF_OPT_PAIR_KERNELS
+    int64_t opt_list_bytes = 0;  // G3PCF_OPT_LIST_BYTES
+    // pair lists (forward, pairlist.cu): per-primary need / base / nchunks,
+    // the chunk pool and its bin tags; pinned host copies of need and base
+    DevBuf l_need, l_base, l_nch, l_pool, l_dir;
+    int* h_need = nullptr;
+    int* h_base = nullptr;
+    size_t h_list_cap = 0;
+    int stats_passes = 0;
     bool last_chunked = false;
     std::vector<unsigned char> bintab;  // r^2 -> bin lookup (see compute_bins)
     float bin_tscale = 0.f;
@@ -346,6 +355,114 @@ int read_status(g3pcf_plan_t P) {
     return G3PCF_OK;
 }
 
+// Forward pair stage through pair lists for the primaries [pa.q0, pa.nprim):
+// count candidates, bring the per-primary chunk bounds to the host, split the
+// range into passes whose lists fit the pool, then scan + accumulate each pass.
+int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st) {
+    const int qa = pa.q0, qb = pa.nprim;
+    const int64_t nq = (int64_t)qb - qa;
+    if (nq <= 0) return G3PCF_OK;
+    if (ensure(P->l_need, 4 * (size_t)qb, "pair-list bounds") ||
+        ensure(P->l_base, 4 * (size_t)qb, "pair-list bounds") ||
+        ensure(P->l_nch, 4 * (size_t)qb, "pair-list bounds"))
+        return G3PCF_ERR_ALLOC;
+    if ((size_t)nq > P->h_list_cap) {
+        if (P->h_need) cudaFreeHost(P->h_need);
+        if (P->h_base) cudaFreeHost(P->h_base);
+        P->h_need = P->h_base = nullptr;
+        P->h_list_cap = 0;
+        if (cudaHostAlloc(reinterpret_cast<void**>(&P->h_need), 4 * nq, cudaHostAllocDefault) != cudaSuccess ||
+            cudaHostAlloc(reinterpret_cast<void**>(&P->h_base), 4 * nq, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(G3PCF_ERR_ALLOC, "pinned host allocation of %lld bytes failed", (long long)(8 * nq));
+        }
+        P->h_list_cap = (size_t)nq;
+    }
+    ListArgs la{};
+    la.pts = pa.pts;
+    la.pts64 = pa.pts64;
+    la.orig = pa.orig;
+    la.cstart = pa.cstart;
+    la.plist = pa.plist;
+    la.key = pa.key;
+    la.q0 = pa.q0;
+    la.chunked = pa.chunked;
+    la.wrow = pa.wrow;
+    la.A = pa.A;
+    la.RLP = pa.RLP;
+    la.colmap = pa.colmap;
+    la.colscale = pa.colscale;
+    la.RL = pa.RL;
+    la.counts = pa.counts;
+    la.queue = pa.queue;
+    la.status = pa.status;
+    la.bintab = pa.bintab;
+    la.bin_tscale = pa.bin_tscale;
+    la.g = pa.g;
+    la.bins = pa.bins;
+    la.need = P->l_need.as<int>();
+    la.base = P->l_base.as<int>();
+    la.nchunks = P->l_nch.as<int>();
+    la.qa = qa;
+    la.qb = qb;
+    ++P->launches;
+    if (launch_count(la, P->nsm, st) != 0)
+        return fail(G3PCF_ERR_CUDA, "pair count launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    CK(cudaMemcpyAsync(P->h_need, la.need + qa, 4 * nq, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    // pool capacity (chunks of 128 bytes + one bin byte)
+    int64_t total = 0, most = 0;
+    for (int64_t k = 0; k < nq; ++k) {
+        total += P->h_need[k];
+        most = std::max<int64_t>(most, P->h_need[k]);
+    }
+    double budget = (double)P->opt_list_bytes;
+    if (budget <= 0) {
+        size_t fr = 0, tot = 0;
+        CK(cudaMemGetInfo(&fr, &tot));
+        budget = 0.4 * (double)(fr + P->l_pool.bytes + P->l_dir.bytes);
+        if (budget > 32e9) budget = 32e9;
+    }
+    int64_t cap = (int64_t)(budget / 129.0);
+    if (cap > ((int64_t)1 << 30)) cap = (int64_t)1 << 30;
+    if (cap > total) cap = total;
+    if (cap < most)
+        return fail(G3PCF_ERR_ALLOC, "pair lists of one primary (%lld chunks) exceed the list budget (%lld)",
+                    (long long)most, (long long)cap);
+    if (cap > 0 && (ensure(P->l_pool, 128 * (size_t)cap, "pair lists") ||
+                    ensure(P->l_dir, (size_t)cap, "pair lists")))
+        return G3PCF_ERR_ALLOC;
+    la.chunks = P->l_pool.as<int>();
+    la.dir = P->l_dir.as<unsigned char>();
+    std::vector<int> cuts{qa};
+    int64_t acc = 0;
+    for (int64_t k = 0; k < nq; ++k) {
+        if (acc + P->h_need[k] > cap) {
+            cuts.push_back(qa + (int)k);
+            acc = 0;
+        }
+        P->h_base[k] = (int)acc;
+        acc += P->h_need[k];
+    }
+    cuts.push_back(qb);
+    CK(cudaMemcpyAsync(P->l_base.as<int>() + qa, P->h_base, 4 * nq, cudaMemcpyHostToDevice, st));
+    for (size_t k = 0; k + 1 < cuts.size(); ++k) {
+        la.qa = cuts[k];
+        la.qb = cuts[k + 1];
+        if (la.qb <= la.qa) continue;
+        CK(cudaMemsetAsync(la.queue, 0, sizeof(int), st));
+        ++P->launches;
+        if (launch_scan(la, P->nsm, st) != 0)
+            return fail(G3PCF_ERR_CUDA, "pair scan launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        CK(cudaMemsetAsync(la.queue, 0, sizeof(int), st));
+        ++P->launches;
+        if (launch_accum(P->lmax, la, P->nsm, st) != 0)
+            return fail(G3PCF_ERR_CUDA, "pair accumulate launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    P->stats_passes = (int)cuts.size() - 1;
+    return G3PCF_OK;
+}
+
 int run_forward(g3pcf_plan_t P, CallSpec& c) {
     if (int r = setup_device(P)) return r;
     if (int r = upload_consts(P)) return r;
@@ -579,9 +696,14 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
                 pa.bins = P->bins;
                 pa.bintab = P->d_bintab.as<unsigned char>();
                 pa.bin_tscale = P->bin_tscale;
-                ++P->launches;
-                if (launch_pair(P->lmax, pa, P->nsm, st) != 0)
-                    return fail(G3PCF_ERR_CUDA, "pair kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+                const bool use_list = P->opt_pair == 2 || (P->opt_pair == 0 && !P->capturing);
+                if (use_list) {
+                    if (int r = run_pair_lists(P, pa, st)) return r;
+                } else {
+                    ++P->launches;
+                    if (launch_pair(P->lmax, pa, P->nsm, st) != 0)
+                        return fail(G3PCF_ERR_CUDA, "pair kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+                }
             }
             if (ch == 0) CK(cudaEventRecord(P->ev[2], st));
             const std::vector<Segment>& segs = csegs[ch];
@@ -953,6 +1075,15 @@ int g3pcf_set_option(g3pcf_plan_t P, int option, int64_t value) {
             P->kflush = (int)value;
             return G3PCF_OK;
         }
+        case G3PCF_OPT_PAIR_KERNELS:
+            if (value < 0 || value > 2) return fail(G3PCF_ERR_ARG, "pair kernels must be 0, 1 or 2");
+            P->opt_pair = (int)value;
+            return G3PCF_OK;
+        case G3PCF_OPT_LIST_BYTES:
+            if (value < 0) return fail(G3PCF_ERR_ARG, "list bytes must be >= 0");
+            if (value > 0 && value < (int64_t)1 << 20) return fail(G3PCF_ERR_ARG, "list bytes must be >= 1 MiB");
+            P->opt_list_bytes = value;
+            return G3PCF_OK;
         default:
             return fail(G3PCF_ERR_ARG, "unknown option %d", option);
     }
@@ -1084,8 +1215,10 @@ int g3pcf_destroy(g3pcf_plan_t P) {
                       &P->small, &P->counts, &P->A, &P->partials, &P->d_tiles, &P->d_segs,
                       &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_catoff, &P->d_ranges,
                       &P->d_tiles_tc, &P->ops, &P->d_cats, &P->d_mreal, &P->d_V, &P->d_bintab,
-                      &P->wrow};
+                      &P->wrow, &P->l_need, &P->l_base, &P->l_nch, &P->l_pool, &P->l_dir};
     for (DevBuf* b : bufs) b->release();
+    if (P->h_need) cudaFreeHost(P->h_need);
+    if (P->h_base) cudaFreeHost(P->h_base);
     if (P->h_status) cudaFreeHost(P->h_status);
     if (P->h_stage) cudaFreeHost(P->h_stage);
     if (P->gexec) cudaGraphExecDestroy(P->gexec);

@@ -137,6 +137,46 @@ struct PairArgs {
 int launch_pair(int lmax, const PairArgs& a, int nsm, cudaStream_t st, int mode = 0);
 size_t pair_smem_per_warp(int lmax, int nbins, int kflush);
 
+// ---- pairlist.cu -----------------------------------------------------------
+// Forward pair stage as three kernels over the primaries [qa, qb) (processing
+// order): k_count writes need[q] = ceil(candidates / 32) + nbins (an upper
+// bound of the list chunks of q); the host sets base[q] (first chunk of q in
+// the pool, relative to the pass) so that a pass fits the pool; k_scan writes
+// the chunks (32 entries j | code << 27, padding 0xffffffff), their bins
+// (dir) and nchunks[q]; k_accum turns them into A rows.
+struct ListArgs {
+    const float4* pts;
+    const double* pts64;
+    const int* orig;
+    const int* cstart;
+    const int* plist;
+    const unsigned* key;
+    int qa, qb;              // primaries of this launch (processing order)
+    int q0;                  // first primary of the A chunk (row = q - q0 when chunked)
+    int chunked;
+    float* wrow;
+    float* A;
+    int RLP;
+    const int* colmap;
+    const float* colscale;
+    int RL;
+    unsigned long long* counts;
+    int* queue;
+    int* status;
+    const unsigned char* bintab;
+    float bin_tscale;
+    int* need;               // [q] (global processing-order index)
+    const int* base;         // [q] first chunk of q, relative to chunks/dir
+    int* nchunks;            // [q]
+    int* chunks;             // pool: 32 ints per chunk
+    unsigned char* dir;      // pool: bin of each chunk
+    Grid g;
+    Bins bins;
+};
+int launch_count(const ListArgs& a, int nsm, cudaStream_t st);
+int launch_scan(const ListArgs& a, int nsm, cudaStream_t st);
+int launch_accum(int lmax, const ListArgs& a, int nsm, cudaStream_t st);
+
 // ---- contract.cu -----------------------------------------------------------
 struct Tile {          // one output tile of one m block of C_m = sum_i w_i v_i v_i^T
     int m, r0, c0, rows, cols, col0;  // col0: first column of block m inside an A row

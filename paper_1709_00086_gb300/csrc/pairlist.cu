@@ -1,0 +1,448 @@
+// Pair stage split in three kernels (forward): count, scan, accumulate.
+//
+// Paper: Algorithm 1 and Sec. 3.1 (neighbours within rmax, radial bin,
+// rotation, harmonics, multipoles per shell), Sec. 3.3.1 (pre-binning: pairs
+// of one primary collected per radial bin before their multipoles are
+// computed) and Sec. 3.3.2 (one reduction of the per-lane partials per
+// primary and bin instead of one per pair group).
+//
+//   k_count  -- per primary, the number of candidate secondaries in the
+//               sphere's cell rows; the host turns ceil(candidates/32) + B
+//               into exact, non-overlapping list offsets and into passes that
+//               fit the list pool.
+//   k_scan   -- per primary (one warp), streams the candidates, decides each
+//               pair's bin exactly and appends accepted pairs to a per-bin
+//               staging ring in shared memory; every 32 pairs of a bin leave
+//               as one 128-byte chunk, tagged with its bin, for this primary.
+//               Few registers: many warps hide the candidate loads.
+//   k_accum  -- per primary (one warp), walks its chunks bin by bin: each
+//               lane takes one pair of a chunk, evaluates Y_lm (FP32
+//               recurrence, pair_common.cuh) into (lmax+1)^2 register
+//               partials, and one warp butterfly per (primary, bin) reduces
+//               them; the normalised row of multipoles goes to A.
+//
+// Compared with the fused kernel (pair.cu, kept for graph-captured calls and
+// for the adjoint), the accumulation runs without the scan's state in
+// registers and reduces across lanes once per bin instead of once per bucket.
+#include "pair_common.cuh"
+
+namespace g3 {
+
+namespace {
+
+constexpr int kLWarps = 4;
+constexpr int kLThreads = kLWarps * 32;
+constexpr int kChunk = 32;      // pairs per list chunk
+constexpr int kRing = 64;       // per-bin staging ring in k_scan (entries)
+constexpr int kScanSlots = 4;   // candidate iterations in flight in k_scan
+constexpr unsigned kNoPair = 0xffffffffu;  // padding entry of a list chunk (image code 31 is unused)
+
+// Per-warp shared memory of k_scan: img[27] float4, pd[4] double,
+// pcs[kMaxPieces] int4, head[32] int, cnt[32] int, ring[B][kRing] int.
+struct ScanSmem {
+    float4* img;
+    double* pd;
+    int4* pcs;
+    int* head;
+    int* cnt;
+    int* ring;
+};
+__host__ __device__ constexpr size_t scan_smem_per_warp(int B) {
+    return 27 * 16 + 4 * 8 + kMaxPieces * 16 + 2 * 32 * 4 + (size_t)B * kRing * 4;
+}
+__device__ __forceinline__ ScanSmem scan_smem(unsigned char* raw, int wid, int B) {
+    unsigned char* b = raw + (size_t)wid * scan_smem_per_warp(B);
+    ScanSmem S;
+    S.img = reinterpret_cast<float4*>(b);
+    S.pd = reinterpret_cast<double*>(b + 27 * 16);
+    S.pcs = reinterpret_cast<int4*>(b + 27 * 16 + 32);
+    S.head = reinterpret_cast<int*>(b + 27 * 16 + 32 + kMaxPieces * 16);
+    S.cnt = S.head + 32;
+    S.ring = S.cnt + 32;
+    return S;
+}
+
+__global__ void __launch_bounds__(kLThreads) k_count(ListArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const Grid& g = a.g;
+    const int K = g.reach, W = 2 * K + 1, nrows = W * W;
+    for (int q = a.qa + gw; q < a.qb; q += nw) {
+        const int p = a.plist ? a.plist[q] : q;
+        const float4 P0 = a.pts[p];
+        const long long cat = (long long)(a.key[p] / (unsigned long long)g.cells_per_cat);
+        const long long kbase = cat * g.cells_per_cat;
+        const int cy = cell_of(P0.y, g), cz = cell_of(P0.z, g);
+        long long sum = 0;
+        for (int r = lane; r < nrows; r += 32) {
+            int4 pm, p0, pp;
+            row_pieces(r, W, K, cy, cz, P0, g, a.bins.slack, a.bins.rmax2f, kbase, a.cstart, pm, p0,
+                       pp);
+            sum += max(pm.y - pm.x, 0) + max(p0.y - p0.x, 0) + max(pp.y - pp.x, 0);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+        if (lane == 0) a.need[q] = (int)((sum + kChunk - 1) / kChunk) + a.bins.nbins;
+    }
+}
+
+__global__ void __launch_bounds__(kLThreads) k_scan(ListArgs a) {
+    extern __shared__ __align__(16) unsigned char ls_raw[];
+    __shared__ double s_e2[kMaxBins + 1];
+    __shared__ float2 s_dec[kMaxBins];
+    __shared__ unsigned char s_tab[kBinTable + 2];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int B = a.bins.nbins;
+    for (int k = threadIdx.x; k <= B; k += blockDim.x) {
+        s_e2[k] = a.bins.e2[k];
+        if (k < B)
+            s_dec[k] = make_float2(a.bins.e2f[k] + a.bins.guard[k], a.bins.e2f[k + 1] - a.bins.guard[k + 1]);
+    }
+    for (int k = threadIdx.x; k < kBinTable + 2; k += blockDim.x) s_tab[k] = a.bintab[k];
+    __syncthreads();
+    const ScanSmem S = scan_smem(ls_raw, wid, B);
+    const unsigned lt = lanemask_lt();
+    const Grid& g = a.g;
+    const float Lb = g.box;
+    const bool exact_inputs = (a.pts64 == nullptr);
+    const float hi_rej = a.bins.hi_rej, lo_rej = a.bins.lo_rej, guard0 = a.bins.guard[0];
+    const float rminf = a.bins.rmin, invw = a.bins.invw, tscale = a.bin_tscale;
+    const float slack = a.bins.slack, rmax2 = a.bins.rmax2f;
+    const int K = g.reach, W = 2 * K + 1, nrows = W * W;
+    unsigned long long my_total = 0;
+    long long cur_cat = -1;
+
+    for (;;) {
+        int q = 0;
+        if (lane == 0) q = a.qa + atomicAdd(a.queue, 1);
+        q = __shfl_sync(kFull, q, 0);
+        if (q >= a.qb) break;
+        const int p = a.plist ? a.plist[q] : q;
+        const long long cat = (long long)(a.key[p] / (unsigned long long)g.cells_per_cat);
+        if (cat != cur_cat) {
+            if (cur_cat >= 0 && lane < B && my_total) atomicAdd(&a.counts[cur_cat * B + lane], my_total);
+            my_total = 0;
+            cur_cat = cat;
+        }
+        const long long kbase = cat * g.cells_per_cat;
+        const float4 P0 = a.pts[p];
+        if (lane < 27) {
+            const int sx = lane % 3 - 1, sy = (lane / 3) % 3 - 1, sz = lane / 9 - 1;
+            S.img[lane] = make_float4(P0.x - sx * Lb, P0.y - sy * Lb, P0.z - sz * Lb, 0.f);
+        }
+        if (lane < 3) {
+            const float pv = lane == 0 ? P0.x : (lane == 1 ? P0.y : P0.z);
+            S.pd[lane] = a.pts64 ? a.pts64[3 * (int64_t)p + lane] : (double)pv;
+        }
+        for (int k = lane; k < B; k += 32) {
+            S.head[k] = 0;
+            S.cnt[k] = 0;
+        }
+        __syncwarp();
+        const int cy = cell_of(P0.y, g), cz = cell_of(P0.z, g);
+        const int cb = a.base[q];       // first chunk of this primary in the pool
+        const int cap_ch = a.need[q];   // chunks reserved for it
+        int nch = 0;
+
+        auto emit = [&](int b, int n) {  // one chunk of bin b from the ring head
+            if (nch < cap_ch) {
+                const int h = S.head[b];
+                const int e = lane < n ? S.ring[b * kRing + ((h + lane) & (kRing - 1))] : (int)kNoPair;
+                a.chunks[((int64_t)cb + nch) * kChunk + lane] = e;
+                if (lane == 0) a.dir[(int64_t)cb + nch] = (unsigned char)b;
+            } else if (lane == 0) {
+                atomicOr(a.status, kStatusOverflow);
+            }
+            ++nch;
+            __syncwarp();
+            if (lane == 0) {
+                S.head[b] = (S.head[b] + n) & (kRing - 1);
+                S.cnt[b] -= n;
+            }
+            if (lane == b) my_total += (unsigned long long)n;
+            __syncwarp();
+        };
+
+        // candidate stream (as in the fused kernel): batches of 32 rows ->
+        // pieces -> iterations of up to 32 consecutive slots of one piece
+        int rb = 0, npcs = 0, pi = 0, poff = 0;
+        auto build_batch = [&]() {
+            int4 pm = make_int4(0, 0, 0, 0), p0 = pm, pp = pm;
+            const int r = rb + lane;
+            if (r < nrows) row_pieces(r, W, K, cy, cz, P0, g, slack, rmax2, kbase, a.cstart, pm, p0, pp);
+            const int npc = (pm.y > pm.x) + (p0.y > p0.x) + (pp.y > pp.x);
+            int incl = npc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += y;
+            }
+            npcs = __shfl_sync(kFull, incl, 31);
+            __syncwarp();
+            int k = incl - npc;
+            if (pm.y > pm.x) S.pcs[k++] = pm;
+            if (p0.y > p0.x) S.pcs[k++] = p0;
+            if (pp.y > pp.x) S.pcs[k++] = pp;
+            __syncwarp();
+            pi = 0;
+            poff = 0;
+            rb += 32;
+        };
+        auto issue = [&](float4& qv, int& jv, int& codev) -> bool {
+            while (pi >= npcs && rb < nrows) build_batch();
+            if (pi >= npcs) {
+                jv = -1;
+                codev = 13;
+                return false;
+            }
+            const int4 pc = S.pcs[pi];
+            const int jj = pc.x + poff + lane;
+            codev = pc.z;
+            jv = jj < pc.y ? jj : -1;
+            if (jv >= 0) qv = __ldg(a.pts + jv);
+            poff += 32;
+            if (pc.x + poff >= pc.y) {
+                ++pi;
+                poff = 0;
+            }
+            return true;
+        };
+        float4 sq[kScanSlots];
+        int sj[kScanSlots], sc[kScanSlots];
+        unsigned live = 0;
+#pragma unroll
+        for (int s = 0; s < kScanSlots; ++s) {
+            sq[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (issue(sq[s], sj[s], sc[s])) live |= 1u << s;
+        }
+        while (live) {
+#pragma unroll
+            for (int s = 0; s < kScanSlots; ++s) {
+                const int j = sj[s];
+                const int code = sc[s];
+                const float4 qq = sq[s];
+                const bool on = (live >> s) & 1u;
+                if (on && !issue(sq[s], sj[s], sc[s])) live &= ~(1u << s);
+                int bin = -1;
+                if (on && j >= 0) {
+                    const float4 o = S.img[code];
+                    const float dx = qq.x - o.x, dy = qq.y - o.y, dz = qq.z - o.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    bin = decide_bin(r2, hi_rej, lo_rej, tscale, s_tab, guard0, s_dec, rminf, invw, B,
+                                     exact_inputs, code, a.pts, a.pts64, j, S.pd, g.boxd, g.periodic,
+                                     s_e2);
+                }
+                // append to the bin's staging ring (warp-aggregated per bin)
+                const unsigned peers = __match_any_sync(kFull, bin);
+                const int leader = __ffs(peers) - 1;
+                int pos = 0;
+                if (lane == leader && bin >= 0) {
+                    const int c = S.cnt[bin];
+                    pos = S.head[bin] + c;
+                    S.cnt[bin] = c + __popc(peers);
+                }
+                pos = __shfl_sync(kFull, pos, leader);
+                if (bin >= 0)
+                    S.ring[bin * kRing + ((pos + __popc(peers & lt)) & (kRing - 1))] =
+                        (int)((unsigned)j | ((unsigned)code << kIdxBits));
+                __syncwarp();
+                // full chunks leave at once (a ring holds < 64 after every append)
+                unsigned fm = __ballot_sync(kFull, lane < B && S.cnt[lane] >= kChunk);
+                while (fm) {
+                    const int b = __ffs(fm) - 1;
+                    fm &= fm - 1;
+                    emit(b, kChunk);
+                }
+            }
+        }
+        {  // the rest of every bin, padded with -1
+            unsigned nz = __ballot_sync(kFull, lane < B && S.cnt[lane] > 0);
+            while (nz) {
+                const int b = __ffs(nz) - 1;
+                nz &= nz - 1;
+                emit(b, S.cnt[b]);
+            }
+        }
+        if (lane == 0) a.nchunks[q] = nch < cap_ch ? nch : cap_ch;
+        __syncwarp();
+    }
+    if (cur_cat >= 0 && lane < B && my_total) atomicAdd(&a.counts[cur_cat * B + lane], my_total);
+}
+
+template <int L>
+__device__ __forceinline__ void pair_term(float (&acc)[Shape<L>::NR], const float4& q, unsigned e,
+                                          const float4* img, const float* R, int radial) {
+    const bool valid = e != kNoPair;
+    float w = 0.f, dx = 1.f, dy = 0.f, dz = 0.f;
+    if (valid) {
+        const float4 o = img[e >> kIdxBits];
+        dx = q.x - o.x;
+        dy = q.y - o.y;
+        dz = q.z - o.z;
+        w = q.w;
+        if (radial) {
+            const float rx = fmaf(R[0], dx, fmaf(R[1], dy, R[2] * dz));
+            const float ry = fmaf(R[3], dx, fmaf(R[4], dy, R[5] * dz));
+            const float rz = fmaf(R[6], dx, fmaf(R[7], dy, R[8] * dz));
+            dx = rx;
+            dy = ry;
+            dz = rz;
+        }
+    }
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float rinv = rsqrtf(r2);
+    accum_pair<L>(acc, dz * rinv, dx * rinv, dy * rinv, w);
+}
+
+template <int L>
+__global__ void __launch_bounds__(kLThreads, 3) k_accum(ListArgs a) {
+    constexpr int NR = Shape<L>::NR, NRP = Shape<L>::NRP;
+    extern __shared__ __align__(16) unsigned char la_raw[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int B = a.bins.nbins;
+    unsigned char* base = la_raw + (size_t)wid * (B * NRP * 4 + 27 * 16 + 64);
+    float* res = reinterpret_cast<float*>(base);
+    float4* img = reinterpret_cast<float4*>(base + B * NRP * 4);
+    float* Rs = reinterpret_cast<float*>(base + B * NRP * 4 + 27 * 16);
+    const Grid& g = a.g;
+    const float Lb = g.box;
+    for (;;) {
+        int q = 0;
+        if (lane == 0) q = a.qa + atomicAdd(a.queue, 1);
+        q = __shfl_sync(kFull, q, 0);
+        if (q >= a.qb) break;
+        const int p = a.plist ? a.plist[q] : q;
+        const float4 P0 = a.pts[p];
+        if (lane < 27) {
+            const int sx = lane % 3 - 1, sy = (lane / 3) % 3 - 1, sz = lane / 9 - 1;
+            img[lane] = make_float4(P0.x - sx * Lb, P0.y - sy * Lb, P0.z - sz * Lb, 0.f);
+        }
+        if (lane < 9) {
+            double x0 = P0.x, x1 = P0.y, x2 = P0.z;
+            if (a.pts64) {
+                x0 = a.pts64[3 * (int64_t)p];
+                x1 = a.pts64[3 * (int64_t)p + 1];
+                x2 = a.pts64[3 * (int64_t)p + 2];
+            }
+            Rs[lane] = g.radial ? los_rotation_entry(lane, x0, x1, x2, g.boxd)
+                                : ((lane % 4 == 0) ? 1.f : 0.f);
+        }
+        __syncwarp();
+        const int cb = a.base[q];
+        const int nch = a.nchunks[q];
+        const int* chunks = a.chunks + (int64_t)cb * kChunk;
+        const unsigned char* dir = a.dir + cb;
+        for (int b = 0; b < B; ++b) {
+            float acc[NR];
+            static_for<0, NR>([&](auto ic) { acc[decltype(ic)::value] = 0.f; });
+            bool any = false;
+            for (int c0 = 0; c0 < nch; c0 += 32) {
+                unsigned m = __ballot_sync(kFull, c0 + lane < nch && dir[c0 + lane] == b);
+                if (!m) continue;
+                any = true;
+                // one chunk (32 pairs, one per lane) per step, the next one in flight
+                int c = c0 + __ffs(m) - 1;
+                m &= m - 1;
+                unsigned e = (unsigned)__ldg(chunks + (int64_t)c * kChunk + lane);
+                float4 qv = make_float4(1.f, 0.f, 0.f, 0.f);
+                if (e != kNoPair) qv = __ldg(a.pts + (e & kIdxMask));
+                for (;;) {
+                    const unsigned ecur = e;
+                    const float4 qcur = qv;
+                    const bool more = m != 0;
+                    if (more) {
+                        c = c0 + __ffs(m) - 1;
+                        m &= m - 1;
+                        e = (unsigned)__ldg(chunks + (int64_t)c * kChunk + lane);
+                        qv = make_float4(1.f, 0.f, 0.f, 0.f);
+                        if (e != kNoPair) qv = __ldg(a.pts + (e & kIdxMask));
+                    }
+                    pair_term<L>(acc, qcur, ecur, img, Rs, g.radial);
+                    if (!more) break;
+                }
+            }
+            if (any) {
+                float* rb = res + b * NRP;
+                for (int k = lane; k < NR; k += 32) rb[k] = 0.f;
+                __syncwarp();
+                butterfly_add<L>(acc, lane, rb);
+            } else {
+                for (int k = lane; k < NR; k += 32) res[b * NRP + k] = 0.f;
+            }
+        }
+        __syncwarp();
+        const int row = a.chunked ? q - a.q0 : a.orig[p];
+        float* Arow = a.A + (int64_t)row * a.RLP;
+        for (int col = lane; col < a.RL; col += 32) Arow[col] = res[a.colmap[col]] * a.colscale[col];
+        if (lane == 0) a.wrow[row] = P0.w;
+        __syncwarp();
+    }
+}
+
+template <int L>
+int launch_accum_t(const ListArgs& a, int nsm, cudaStream_t st) {
+    constexpr int NRP = Shape<L>::NRP;
+    const size_t per_warp = (size_t)a.bins.nbins * NRP * 4 + 27 * 16 + 64;
+    const size_t smem = per_warp * kLWarps;
+    if (cudaFuncSetAttribute(k_accum<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return -1;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_accum<L>, kLThreads, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        return -1;
+    int blocks = per_sm * nsm;
+    const int need = (a.qb - a.qa + kLWarps - 1) / kLWarps;
+    if (blocks > need) blocks = need > 0 ? need : 1;
+    k_accum<L><<<blocks, kLThreads, smem, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace
+
+int launch_count(const ListArgs& a, int nsm, cudaStream_t st) {
+    if (a.qb <= a.qa) return 0;
+    const int warps = a.qb - a.qa;
+    int blocks = (warps + kLWarps - 1) / kLWarps;
+    if (blocks > nsm * 16) blocks = nsm * 16;
+    k_count<<<blocks, kLThreads, 0, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_scan(const ListArgs& a, int nsm, cudaStream_t st) {
+    if (a.qb <= a.qa) return 0;
+    const size_t smem = scan_smem_per_warp(a.bins.nbins) * kLWarps;
+    if (cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return -1;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan, kLThreads, smem) != cudaSuccess ||
+        per_sm < 1)
+        return -1;
+    int blocks = per_sm * nsm;
+    const int need = (a.qb - a.qa + kLWarps - 1) / kLWarps;
+    if (blocks > need) blocks = need;
+    k_scan<<<blocks, kLThreads, smem, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_accum(int lmax, const ListArgs& a, int nsm, cudaStream_t st) {
+    if (a.qb <= a.qa) return 0;
+    switch (lmax) {
+        case 0: return launch_accum_t<0>(a, nsm, st);
+        case 1: return launch_accum_t<1>(a, nsm, st);
+        case 2: return launch_accum_t<2>(a, nsm, st);
+        case 3: return launch_accum_t<3>(a, nsm, st);
+        case 4: return launch_accum_t<4>(a, nsm, st);
+        case 5: return launch_accum_t<5>(a, nsm, st);
+        case 6: return launch_accum_t<6>(a, nsm, st);
+        case 7: return launch_accum_t<7>(a, nsm, st);
+        case 8: return launch_accum_t<8>(a, nsm, st);
+        case 9: return launch_accum_t<9>(a, nsm, st);
+        case 10: return launch_accum_t<10>(a, nsm, st);
+        default: return -1;
+    }
+}
+
+}  // namespace g3
