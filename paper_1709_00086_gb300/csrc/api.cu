@@ -107,7 +107,7 @@ struct g3pcf_plan_s {
     int64_t opt_list_bytes = 0;  // G3PCF_OPT_LIST_BYTES
     // pair lists (forward, pairlist.cu): per-primary need / base / nchunks,
     // the chunk pool and its bin tags; pinned host copies of need and base
-    DevBuf l_need, l_base, l_nch, l_pool, l_dir;
+    DevBuf l_need, l_base, l_nch, l_pool, l_tag, l_ord, l_dir;
     int* h_need = nullptr;
     int* h_base = nullptr;
     size_t h_list_cap = 0;
@@ -410,7 +410,7 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st) {
         return fail(G3PCF_ERR_CUDA, "pair count launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     CK(cudaMemcpyAsync(P->h_need, la.need + qa, 4 * nq, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    // pool capacity (chunks of 128 bytes + one bin byte)
+    // pool capacity (per chunk: 128 bytes of entries, tag and list ints, a bin byte)
     int64_t total = 0, most = 0;
     for (int64_t k = 0; k < nq; ++k) {
         total += P->h_need[k];
@@ -420,19 +420,23 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st) {
     if (budget <= 0) {
         size_t fr = 0, tot = 0;
         CK(cudaMemGetInfo(&fr, &tot));
-        budget = 0.4 * (double)(fr + P->l_pool.bytes + P->l_dir.bytes);
+        budget = 0.4 * (double)(fr + P->l_pool.bytes + P->l_tag.bytes + P->l_ord.bytes + P->l_dir.bytes);
         if (budget > 32e9) budget = 32e9;
     }
-    int64_t cap = (int64_t)(budget / 129.0);
+    int64_t cap = (int64_t)(budget / 137.0);
     if (cap > ((int64_t)1 << 30)) cap = (int64_t)1 << 30;
     if (cap > total) cap = total;
     if (cap < most)
         return fail(G3PCF_ERR_ALLOC, "pair lists of one primary (%lld chunks) exceed the list budget (%lld)",
                     (long long)most, (long long)cap);
     if (cap > 0 && (ensure(P->l_pool, 128 * (size_t)cap, "pair lists") ||
+                    ensure(P->l_tag, 4 * (size_t)cap, "pair lists") ||
+                    ensure(P->l_ord, 4 * (size_t)cap, "pair lists") ||
                     ensure(P->l_dir, (size_t)cap, "pair lists")))
         return G3PCF_ERR_ALLOC;
     la.chunks = P->l_pool.as<int>();
+    la.tag = P->l_tag.as<int>();
+    la.ord = P->l_ord.as<int>();
     la.dir = P->l_dir.as<unsigned char>();
     std::vector<int> cuts{qa};
     int64_t acc = 0;
@@ -1215,7 +1219,7 @@ int g3pcf_destroy(g3pcf_plan_t P) {
                       &P->small, &P->counts, &P->A, &P->partials, &P->d_tiles, &P->d_segs,
                       &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_catoff, &P->d_ranges,
                       &P->d_tiles_tc, &P->ops, &P->d_cats, &P->d_mreal, &P->d_V, &P->d_bintab,
-                      &P->wrow, &P->l_need, &P->l_base, &P->l_nch, &P->l_pool, &P->l_dir};
+                      &P->wrow, &P->l_need, &P->l_base, &P->l_nch, &P->l_pool, &P->l_tag, &P->l_ord, &P->l_dir};
     for (DevBuf* b : bufs) b->release();
     if (P->h_need) cudaFreeHost(P->h_need);
     if (P->h_base) cudaFreeHost(P->h_base);

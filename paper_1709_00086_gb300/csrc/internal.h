@@ -142,8 +142,9 @@ size_t pair_smem_per_warp(int lmax, int nbins, int kflush);
 // order): k_count writes need[q] = ceil(candidates / 32) + nbins (an upper
 // bound of the list chunks of q); the host sets base[q] (first chunk of q in
 // the pool, relative to the pass) so that a pass fits the pool; k_scan writes
-// the chunks (32 entries j | code << 27, padding 0xffffffff), their bins
-// (dir) and nchunks[q]; k_accum turns them into A rows.
+// the chunks (32 entries j | code << 27, padding 0xffffffff), the list of them
+// ordered by bin (ord, with the bins in dir) and nchunks[q]; k_accum walks that
+// list and writes A rows.
 struct ListArgs {
     const float4* pts;
     const double* pts64;
@@ -169,7 +170,9 @@ struct ListArgs {
     const int* base;         // [q] first chunk of q, relative to chunks/dir
     int* nchunks;            // [q]
     int* chunks;             // pool: 32 ints per chunk
-    unsigned char* dir;      // pool: bin of each chunk
+    int* tag;                // pool: (rank among its bin's chunks) << 5 | bin, per chunk
+    int* ord;                // pool: the primary's chunks listed by bin (stable)
+    unsigned char* dir;      // pool: bin of each ord entry
     Grid g;
     Bins bins;
 };

@@ -33,22 +33,19 @@ namespace {
 constexpr int kLWarps = 4;
 constexpr int kLThreads = kLWarps * 32;
 constexpr int kChunk = 32;      // pairs per list chunk
-constexpr int kRing = 64;       // per-bin staging ring in k_scan (entries)
-constexpr int kScanSlots = 4;   // candidate iterations in flight in k_scan
+constexpr int kRing = 64;       // compaction stage of k_scan (entries)
 constexpr unsigned kNoPair = 0xffffffffu;  // padding entry of a list chunk (image code 31 is unused)
 
 // Per-warp shared memory of k_scan: img[27] float4, pd[4] double,
-// pcs[kMaxPieces] int4, head[32] int, cnt[32] int, ring[B][kRing] int.
+// pcs[kMaxPieces] int4, stage[kRing] int2 (accepted pairs: entry, bin).
 struct ScanSmem {
     float4* img;
     double* pd;
     int4* pcs;
-    int* head;
-    int* cnt;
-    int* ring;
+    int2* stage;
 };
-__host__ __device__ constexpr size_t scan_smem_per_warp(int B) {
-    return 27 * 16 + 4 * 8 + kMaxPieces * 16 + 2 * 32 * 4 + (size_t)B * kRing * 4;
+__host__ __device__ constexpr size_t scan_smem_per_warp(int) {
+    return 27 * 16 + 4 * 8 + kMaxPieces * 16 + kRing * 8;
 }
 __device__ __forceinline__ ScanSmem scan_smem(unsigned char* raw, int wid, int B) {
     unsigned char* b = raw + (size_t)wid * scan_smem_per_warp(B);
@@ -56,9 +53,7 @@ __device__ __forceinline__ ScanSmem scan_smem(unsigned char* raw, int wid, int B
     S.img = reinterpret_cast<float4*>(b);
     S.pd = reinterpret_cast<double*>(b + 27 * 16);
     S.pcs = reinterpret_cast<int4*>(b + 27 * 16 + 32);
-    S.head = reinterpret_cast<int*>(b + 27 * 16 + 32 + kMaxPieces * 16);
-    S.cnt = S.head + 32;
-    S.ring = S.cnt + 32;
+    S.stage = reinterpret_cast<int2*>(b + 27 * 16 + 32 + kMaxPieces * 16);
     return S;
 }
 
@@ -87,11 +82,15 @@ __global__ void __launch_bounds__(kLThreads) k_count(ListArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(kLThreads) k_scan(ListArgs a) {
+// NB: bits of the multisplit key (5 when nbins <= 31, key 31 = no pair; 6 for
+// nbins = 32, key 63 = no pair).
+template <int NB>
+__global__ void __launch_bounds__(kLThreads, 6) k_scan(ListArgs a) {
     extern __shared__ __align__(16) unsigned char ls_raw[];
     __shared__ double s_e2[kMaxBins + 1];
     __shared__ float2 s_dec[kMaxBins];
     __shared__ unsigned char s_tab[kBinTable + 2];
+    constexpr int kNone = (1 << NB) - 1;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int B = a.bins.nbins;
     for (int k = threadIdx.x; k <= B; k += blockDim.x) {
@@ -103,6 +102,9 @@ __global__ void __launch_bounds__(kLThreads) k_scan(ListArgs a) {
     __syncthreads();
     const ScanSmem S = scan_smem(ls_raw, wid, B);
     const unsigned lt = lanemask_lt();
+    unsigned lrep[NB];  // all ones where bit k of lane is 0
+#pragma unroll
+    for (int k = 0; k < NB; ++k) lrep[k] = ((lane >> k) & 1) ? 0u : ~0u;
     const Grid& g = a.g;
     const float Lb = g.box;
     const bool exact_inputs = (a.pts64 == nullptr);
@@ -135,39 +137,86 @@ __global__ void __launch_bounds__(kLThreads) k_scan(ListArgs a) {
             const float pv = lane == 0 ? P0.x : (lane == 1 ? P0.y : P0.z);
             S.pd[lane] = a.pts64 ? a.pts64[3 * (int64_t)p + lane] : (double)pv;
         }
-        for (int k = lane; k < B; k += 32) {
-            S.head[k] = 0;
-            S.cnt[k] = 0;
-        }
         __syncwarp();
         const int cy = cell_of(P0.y, g), cz = cell_of(P0.z, g);
-        const int cb = a.base[q];       // first chunk of this primary in the pool
-        const int cap_ch = a.need[q];   // chunks reserved for it
-        int nch = 0;
+        int* const pool = a.chunks + (int64_t)a.base[q] * kChunk;  // this primary's chunks
+        int* const ptag = a.tag + a.base[q];
+        int* const pord = a.ord + a.base[q];
+        unsigned char* const pdir = a.dir + a.base[q];
+        const int cap_ch = a.need[q];  // chunks reserved for it
+        int nch = 0;                   // chunks opened so far (warp-uniform)
+        // the open chunk of bin b lives in lane b: its index and fill (kChunk: none open)
+        int ccur = 0, cfill = kChunk;
+        int nbc = 0;                   // chunks of bin lane opened so far
+        unsigned padd = 0;             // pairs of bin lane for this primary
 
-        auto emit = [&](int b, int n) {  // one chunk of bin b from the ring head
-            if (nch < cap_ch) {
-                const int h = S.head[b];
-                const int e = lane < n ? S.ring[b * kRing + ((h + lane) & (kRing - 1))] : (int)kNoPair;
-                a.chunks[((int64_t)cb + nch) * kChunk + lane] = e;
-                if (lane == 0) a.dir[(int64_t)cb + nch] = (unsigned char)b;
-            } else if (lane == 0) {
-                atomicOr(a.status, kStatusOverflow);
+        // Place one accepted pair per lane (bin < 0: none) into the open chunk of
+        // its bin, opening a new chunk where a bin's chunk fills.  NB ballots over
+        // the key bits give lane b the lanes whose key is b; a shuffle from lane
+        // key hands every lane its peers (rank = peers below it).
+        auto place = [&](int entry, int bin) {
+            const int key = bin >= 0 ? bin : kNone;
+            unsigned ofme = kFull;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) ofme &= __ballot_sync(kFull, (key >> k) & 1) ^ lrep[k];
+            const int add = lane < B ? __popc(ofme) : 0;
+            const bool grow = cfill + add > kChunk;  // at most one new chunk per call
+            const unsigned gm = __ballot_sync(kFull, grow);
+            const int nnew = nch + __popc(gm & lt);
+            nch += __popc(gm);
+            const int src = key & 31;
+            const unsigned mine = __shfl_sync(kFull, ofme, src);
+            const int cur = __shfl_sync(kFull, ccur, src);
+            const int fill = __shfl_sync(kFull, cfill, src);
+            const int nxt = __shfl_sync(kFull, nnew, src);
+            if (bin >= 0) {
+                const int pos = fill + __popc(mine & lt);
+                const int c = pos < kChunk ? cur : nxt;
+                if (c < cap_ch) pool[(int64_t)c * kChunk + (pos & (kChunk - 1))] = entry;
             }
-            ++nch;
-            __syncwarp();
-            if (lane == 0) {
-                S.head[b] = (S.head[b] + n) & (kRing - 1);
-                S.cnt[b] -= n;
+            if (grow) {
+                if (nnew < cap_ch)
+                    ptag[nnew] = (nbc << 5) | lane;  // (rank among the bin's chunks, bin)
+                else
+                    atomicOr(a.status, kStatusOverflow);
+                ++nbc;
+                ccur = nnew;
+                cfill = cfill + add - kChunk;
+            } else {
+                cfill += add;
             }
-            if (lane == b) my_total += (unsigned long long)n;
-            __syncwarp();
+            padd += add;
+        };
+        // accepted pairs are first compacted into stage (warp-uniform head/count)
+        int shead = 0, scnt = 0;
+        auto candidate = [&](const float4& qq, int j, int end, int code, const float4& o) {
+            int bin = -1;
+            if (j < end) {
+                const float dx = qq.x - o.x, dy = qq.y - o.y, dz = qq.z - o.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                bin = decide_bin(r2, hi_rej, lo_rej, tscale, s_tab, guard0, s_dec, rminf, invw, B,
+                                 exact_inputs, code, a.pts, a.pts64, j, S.pd, g.boxd, g.periodic, s_e2);
+            }
+            const unsigned vm = __ballot_sync(kFull, bin >= 0);
+            if (vm) {
+                if (bin >= 0)
+                    S.stage[(shead + scnt + __popc(vm & lt)) & (kRing - 1)] =
+                        make_int2((int)((unsigned)j | ((unsigned)code << kIdxBits)), bin);
+                scnt += __popc(vm);
+                if (scnt >= kChunk) {
+                    __syncwarp();
+                    const int2 v = S.stage[(shead + lane) & (kRing - 1)];
+                    shead = (shead + kChunk) & (kRing - 1);
+                    scnt -= kChunk;
+                    __syncwarp();
+                    place(v.x, v.y);
+                }
+            }
         };
 
-        // candidate stream (as in the fused kernel): batches of 32 rows ->
-        // pieces -> iterations of up to 32 consecutive slots of one piece
-        int rb = 0, npcs = 0, pi = 0, poff = 0;
-        auto build_batch = [&]() {
+        // candidates: batches of 32 cell rows -> slot ranges (pieces) -> 64 slots
+        // per trip, two loads in flight per lane
+        for (int rb = 0; rb < nrows; rb += 32) {
             int4 pm = make_int4(0, 0, 0, 0), p0 = pm, pp = pm;
             const int r = rb + lane;
             if (r < nrows) row_pieces(r, W, K, cy, cz, P0, g, slack, rmax2, kbase, a.cstart, pm, p0, pp);
@@ -178,93 +227,68 @@ __global__ void __launch_bounds__(kLThreads) k_scan(ListArgs a) {
                 const int y = __shfl_up_sync(kFull, incl, o);
                 if (lane >= o) incl += y;
             }
-            npcs = __shfl_sync(kFull, incl, 31);
+            const int npcs = __shfl_sync(kFull, incl, 31);
             __syncwarp();
-            int k = incl - npc;
-            if (pm.y > pm.x) S.pcs[k++] = pm;
-            if (p0.y > p0.x) S.pcs[k++] = p0;
-            if (pp.y > pp.x) S.pcs[k++] = pp;
+            {
+                int k = incl - npc;
+                if (pm.y > pm.x) S.pcs[k++] = pm;
+                if (p0.y > p0.x) S.pcs[k++] = p0;
+                if (pp.y > pp.x) S.pcs[k++] = pp;
+            }
             __syncwarp();
-            pi = 0;
-            poff = 0;
-            rb += 32;
-        };
-        auto issue = [&](float4& qv, int& jv, int& codev) -> bool {
-            while (pi >= npcs && rb < nrows) build_batch();
-            if (pi >= npcs) {
-                jv = -1;
-                codev = 13;
-                return false;
+            for (int pi = 0; pi < npcs; ++pi) {
+                const int4 pc = S.pcs[pi];
+                const float4 o = S.img[pc.z];
+                for (int j0 = pc.x; j0 < pc.y; j0 += 2 * kChunk) {
+                    const int ja = j0 + lane, jb = ja + kChunk;
+                    float4 qa = o, qb = o;
+                    if (ja < pc.y) qa = __ldg(a.pts + ja);
+                    if (jb < pc.y) qb = __ldg(a.pts + jb);
+                    candidate(qa, ja, pc.y, pc.z, o);
+                    if (j0 + kChunk < pc.y) candidate(qb, jb, pc.y, pc.z, o);
+                }
             }
-            const int4 pc = S.pcs[pi];
-            const int jj = pc.x + poff + lane;
-            codev = pc.z;
-            jv = jj < pc.y ? jj : -1;
-            if (jv >= 0) qv = __ldg(a.pts + jv);
-            poff += 32;
-            if (pc.x + poff >= pc.y) {
-                ++pi;
-                poff = 0;
-            }
-            return true;
-        };
-        float4 sq[kScanSlots];
-        int sj[kScanSlots], sc[kScanSlots];
-        unsigned live = 0;
-#pragma unroll
-        for (int s = 0; s < kScanSlots; ++s) {
-            sq[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (issue(sq[s], sj[s], sc[s])) live |= 1u << s;
+            __syncwarp();
         }
-        while (live) {
-#pragma unroll
-            for (int s = 0; s < kScanSlots; ++s) {
-                const int j = sj[s];
-                const int code = sc[s];
-                const float4 qq = sq[s];
-                const bool on = (live >> s) & 1u;
-                if (on && !issue(sq[s], sj[s], sc[s])) live &= ~(1u << s);
-                int bin = -1;
-                if (on && j >= 0) {
-                    const float4 o = S.img[code];
-                    const float dx = qq.x - o.x, dy = qq.y - o.y, dz = qq.z - o.z;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    bin = decide_bin(r2, hi_rej, lo_rej, tscale, s_tab, guard0, s_dec, rminf, invw, B,
-                                     exact_inputs, code, a.pts, a.pts64, j, S.pd, g.boxd, g.periodic,
-                                     s_e2);
-                }
-                // append to the bin's staging ring (warp-aggregated per bin)
-                const unsigned peers = __match_any_sync(kFull, bin);
-                const int leader = __ffs(peers) - 1;
-                int pos = 0;
-                if (lane == leader && bin >= 0) {
-                    const int c = S.cnt[bin];
-                    pos = S.head[bin] + c;
-                    S.cnt[bin] = c + __popc(peers);
-                }
-                pos = __shfl_sync(kFull, pos, leader);
-                if (bin >= 0)
-                    S.ring[bin * kRing + ((pos + __popc(peers & lt)) & (kRing - 1))] =
-                        (int)((unsigned)j | ((unsigned)code << kIdxBits));
-                __syncwarp();
-                // full chunks leave at once (a ring holds < 64 after every append)
-                unsigned fm = __ballot_sync(kFull, lane < B && S.cnt[lane] >= kChunk);
-                while (fm) {
-                    const int b = __ffs(fm) - 1;
-                    fm &= fm - 1;
-                    emit(b, kChunk);
-                }
-            }
+        if (scnt > 0) {  // the last accepted pairs (fewer than 32)
+            __syncwarp();
+            const int2 v = lane < scnt ? S.stage[(shead + lane) & (kRing - 1)] : make_int2(0, -1);
+            __syncwarp();
+            place(v.x, v.y);
         }
-        {  // the rest of every bin, padded with -1
-            unsigned nz = __ballot_sync(kFull, lane < B && S.cnt[lane] > 0);
-            while (nz) {
-                const int b = __ffs(nz) - 1;
-                nz &= nz - 1;
-                emit(b, S.cnt[b]);
+        // pad the open chunks behind their last entry
+        unsigned pmask = __ballot_sync(kFull, lane < B && cfill < kChunk);
+        while (pmask) {
+            const int b = __ffs(pmask) - 1;
+            pmask &= pmask - 1;
+            const int c = __shfl_sync(kFull, ccur, b);
+            const int f = __shfl_sync(kFull, cfill, b);
+            if (lane >= f && c < cap_ch) pool[(int64_t)c * kChunk + lane] = (int)kNoPair;
+        }
+        // list the chunks grouped by bin (stable): position = chunks of the
+        // lower bins + rank inside the bin
+        {
+            int off = nbc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, off, o);
+                if (lane >= o) off += y;
+            }
+            off -= nbc;
+            const int nlist = nch < cap_ch ? nch : cap_ch;
+            for (int c0 = 0; c0 < nlist; c0 += 32) {
+                const int c = c0 + lane;
+                const int t = c < nlist ? ptag[c] : 0;
+                const int b = t & 31;
+                const int pos = __shfl_sync(kFull, off, b) + (t >> 5);
+                if (c < nlist && pos < cap_ch) {
+                    pord[pos] = c;
+                    pdir[pos] = (unsigned char)b;
+                }
             }
         }
         if (lane == 0) a.nchunks[q] = nch < cap_ch ? nch : cap_ch;
+        my_total += padd;
         __syncwarp();
     }
     if (cur_cat >= 0 && lane < B && my_total) atomicAdd(&a.counts[cur_cat * B + lane], my_total);
@@ -332,44 +356,55 @@ __global__ void __launch_bounds__(kLThreads, 3) k_accum(ListArgs a) {
         const int cb = a.base[q];
         const int nch = a.nchunks[q];
         const int* chunks = a.chunks + (int64_t)cb * kChunk;
-        const unsigned char* dir = a.dir + cb;
-        for (int b = 0; b < B; ++b) {
+        const int* ordp = a.ord + cb;
+        const unsigned char* dirp = a.dir + cb;
+        for (int k = lane; k < B * NRP; k += 32) res[k] = 0.f;
+        __syncwarp();
+        if (nch > 0) {
+            auto entry = [&](int c) -> unsigned { return (unsigned)__ldg(chunks + (int64_t)c * kChunk + lane); };
+            auto point = [&](unsigned e) -> float4 {
+                return e != kNoPair ? __ldg(a.pts + (e & kIdxMask)) : make_float4(1.f, 0.f, 0.f, 0.f);
+            };
             float acc[NR];
             static_for<0, NR>([&](auto ic) { acc[decltype(ic)::value] = 0.f; });
-            bool any = false;
-            for (int c0 = 0; c0 < nch; c0 += 32) {
-                unsigned m = __ballot_sync(kFull, c0 + lane < nch && dir[c0 + lane] == b);
-                if (!m) continue;
-                any = true;
-                // one chunk (32 pairs, one per lane) per step, the next one in flight
-                int c = c0 + __ffs(m) - 1;
-                m &= m - 1;
-                unsigned e = (unsigned)__ldg(chunks + (int64_t)c * kChunk + lane);
-                float4 qv = make_float4(1.f, 0.f, 0.f, 0.f);
-                if (e != kNoPair) qv = __ldg(a.pts + (e & kIdxMask));
-                for (;;) {
-                    const unsigned ecur = e;
-                    const float4 qcur = qv;
-                    const bool more = m != 0;
-                    if (more) {
-                        c = c0 + __ffs(m) - 1;
-                        m &= m - 1;
-                        e = (unsigned)__ldg(chunks + (int64_t)c * kChunk + lane);
-                        qv = make_float4(1.f, 0.f, 0.f, 0.f);
-                        if (e != kNoPair) qv = __ldg(a.pts + (e & kIdxMask));
-                    }
-                    pair_term<L>(acc, qcur, ecur, img, Rs, g.radial);
-                    if (!more) break;
+            // chunks in bin order; in flight: list slot i+3, entries of i+2, points of i+1
+            unsigned eA = entry(__ldg(ordp));
+            int bA = dirp[0];
+            float4 qA = point(eA);
+            unsigned eB = kNoPair;
+            int bB = -1, cC = 0, bC = -1;
+            if (nch > 1) {
+                eB = entry(__ldg(ordp + 1));
+                bB = dirp[1];
+            }
+            if (nch > 2) {
+                cC = __ldg(ordp + 2);
+                bC = dirp[2];
+            }
+            int curb = bA;
+            for (int i = 0; i < nch; ++i) {
+                int cD = 0, bD = -1;
+                if (i + 3 < nch) {
+                    cD = __ldg(ordp + i + 3);
+                    bD = dirp[i + 3];
                 }
+                const unsigned eC = (i + 2 < nch) ? entry(cC) : kNoPair;
+                const float4 qB = point(eB);
+                if (bA != curb) {  // the bin changes: reduce the partials of the last one
+                    butterfly_add<L>(acc, lane, res + curb * NRP);
+                    static_for<0, NR>([&](auto ic) { acc[decltype(ic)::value] = 0.f; });
+                    curb = bA;
+                }
+                pair_term<L>(acc, qA, eA, img, Rs, g.radial);
+                eA = eB;
+                qA = qB;
+                bA = bB;
+                eB = eC;
+                bB = bC;
+                cC = cD;
+                bC = bD;
             }
-            if (any) {
-                float* rb = res + b * NRP;
-                for (int k = lane; k < NR; k += 32) rb[k] = 0.f;
-                __syncwarp();
-                butterfly_add<L>(acc, lane, rb);
-            } else {
-                for (int k = lane; k < NR; k += 32) res[b * NRP + k] = 0.f;
-            }
+            butterfly_add<L>(acc, lane, res + curb * NRP);
         }
         __syncwarp();
         const int row = a.chunked ? q - a.q0 : a.orig[p];
@@ -400,6 +435,23 @@ int launch_accum_t(const ListArgs& a, int nsm, cudaStream_t st) {
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+template <int NB>
+int launch_scan_t(const ListArgs& a, int nsm, cudaStream_t st) {
+    const size_t smem = scan_smem_per_warp(a.bins.nbins) * kLWarps;
+    if (cudaFuncSetAttribute(k_scan<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return -1;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan<NB>, kLThreads, smem) != cudaSuccess ||
+        per_sm < 1)
+        return -1;
+    int blocks = per_sm * nsm;
+    const int need = (a.qb - a.qa + kLWarps - 1) / kLWarps;
+    if (blocks > need) blocks = need;
+    k_scan<NB><<<blocks, kLThreads, smem, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 }  // namespace
 
 int launch_count(const ListArgs& a, int nsm, cudaStream_t st) {
@@ -413,18 +465,7 @@ int launch_count(const ListArgs& a, int nsm, cudaStream_t st) {
 
 int launch_scan(const ListArgs& a, int nsm, cudaStream_t st) {
     if (a.qb <= a.qa) return 0;
-    const size_t smem = scan_smem_per_warp(a.bins.nbins) * kLWarps;
-    if (cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return -1;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan, kLThreads, smem) != cudaSuccess ||
-        per_sm < 1)
-        return -1;
-    int blocks = per_sm * nsm;
-    const int need = (a.qb - a.qa + kLWarps - 1) / kLWarps;
-    if (blocks > need) blocks = need;
-    k_scan<<<blocks, kLThreads, smem, st>>>(a);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return a.bins.nbins < 32 ? launch_scan_t<5>(a, nsm, st) : launch_scan_t<6>(a, nsm, st);
 }
 
 int launch_accum(int lmax, const ListArgs& a, int nsm, cudaStream_t st) {
