@@ -81,6 +81,8 @@ struct g3pcf_plan_s {
     int RL = 0, RLP = 0, nrp = 0;
     std::vector<int> colmap;
     std::vector<float> colscale;
+    std::vector<int4> colconv;     // Chebyshev-form columns (pair-list path)
+    std::vector<float> colcoef;
     std::vector<Tile> tiles;      // FP32 contraction tiles (edge T)
     std::vector<Tile> tiles_tc;   // tensor-core contraction tiles (edge T_tc)
     int T = 0, T_tc = 0;
@@ -89,6 +91,7 @@ struct g3pcf_plan_s {
     DevBuf key_a, key_b, val_a, val_b, hist, hist_off, scan_tmp, pts, pts64, orig, cstart, plist;
     DevBuf small;       // status, queue
     DevBuf counts, A, partials, d_tiles, d_segs, d_segfirst, d_colmap, d_colscale, d_catoff;
+    DevBuf d_colconv, d_colcoef;
     DevBuf d_ranges, d_tiles_tc, ops, d_cats, d_mreal, d_V, d_bintab, wrow;
     int64_t opt_chunk = 0;   // G3PCF_OPT_CHUNK_ROWS
     // pinned staging for host -> device tables (capturable copies); offset
@@ -107,7 +110,7 @@ struct g3pcf_plan_s {
     int64_t opt_list_bytes = 0;  // G3PCF_OPT_LIST_BYTES
     // pair lists (forward, pairlist.cu): per-primary need / base / nchunks,
     // the chunk pool and its bin tags; pinned host copies of need and base
-    DevBuf l_need, l_base, l_nch, l_pool, l_tag, l_ord, l_dir;
+    DevBuf l_need, l_base, l_nch, l_pool, l_tag, l_ord;
     int* h_need = nullptr;
     int* h_base = nullptr;
     size_t h_list_cap = 0;
@@ -195,6 +198,11 @@ int upload_consts(g3pcf_plan_t P) {
     CK(cudaMemcpy(P->d_bintab.p, P->bintab.data(), P->bintab.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->d_colmap.p, P->colmap.data(), P->RL * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->d_colscale.p, P->colscale.data(), P->RL * sizeof(float), cudaMemcpyHostToDevice));
+    if (P->d_colconv.ensure(P->colconv.size() * sizeof(int4)) ||
+        P->d_colcoef.ensure(P->colcoef.size() * sizeof(float)))
+        return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (constants)");
+    CK(cudaMemcpy(P->d_colconv.p, P->colconv.data(), P->colconv.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->d_colcoef.p, P->colcoef.data(), P->colcoef.size() * sizeof(float), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->d_tiles.p, P->tiles.data(), P->tiles.size() * sizeof(Tile),
                   cudaMemcpyHostToDevice));
     P->consts_uploaded = true;
@@ -292,6 +300,37 @@ void compute_bins(g3pcf_plan_t P) {
 
 // Column map of an A row: block m (m = 0: K_0 reals; m >= 1: Re and Im halves)
 // and the normalisation K_lm of Y_lm.
+// Coefficients c_k of the monic D_{m+n,m}(z) = sum_k c_k T_k(z) (Chebyshev
+// polynomials of the first kind), k = 0..n.  D follows the monic recurrence
+// D_{l+1} = z D_l - (l^2 - m^2)/(4 l^2 - 1) D_{l-1}; both sides are expanded in
+// powers of z (FP64) and the T_k are peeled off from the top degree down.
+std::vector<double> cheb_coeffs(int m, int n) {
+    std::vector<std::vector<double>> T(n + 1, std::vector<double>(n + 1, 0.0));
+    T[0][0] = 1.0;
+    if (n >= 1) T[1][1] = 1.0;
+    for (int k = 1; k < n; ++k)
+        for (int d = 0; d <= n; ++d)
+            T[k + 1][d] = (d > 0 ? 2.0 * T[k][d - 1] : 0.0) - T[k - 1][d];
+    std::vector<double> d0(n + 1, 0.0), d1(n + 1, 0.0);
+    d0[0] = 1.0;
+    if (n >= 1) d1[1] = 1.0;
+    std::vector<double> D = n == 0 ? d0 : d1;
+    for (int l = m + 1; l < m + n; ++l) {
+        const double beta = double(l * l - m * m) / double(4 * l * l - 1);
+        std::vector<double> d2(n + 1, 0.0);
+        for (int d = 0; d <= n; ++d) d2[d] = (d > 0 ? d1[d - 1] : 0.0) - beta * d0[d];
+        d0 = d1;
+        d1 = d2;
+        D = d2;
+    }
+    std::vector<double> c(n + 1, 0.0);
+    for (int k = n; k >= 0; --k) {
+        c[k] = D[k] / T[k][k];
+        for (int d = 0; d <= k; ++d) D[d] -= c[k] * T[k][d];
+    }
+    return c;
+}
+
 void compute_columns(g3pcf_plan_t P) {
     const int B = P->nbins, L = P->lmax;
     P->nrp = pair_nrp(L);
@@ -299,6 +338,19 @@ void compute_columns(g3pcf_plan_t P) {
     P->RLP = (P->RL + 7) & ~7;
     P->colmap.assign(P->RL, 0);
     P->colscale.assign(P->RL, 0.f);
+    P->colconv.assign(P->RL, int4{0, 0, 0, 0});
+    P->colcoef.clear();
+    // coefficient rows (times K_lm) per (l, m), shared by the bins and parts
+    std::vector<int> coef_off((L + 1) * (L + 1), 0);
+    for (int m = 0; m <= L; ++m)
+        for (int l = m; l <= L; ++l) {
+            const double lnN = 0.5 * (std::log((2.0 * l + 1.0) / (4.0 * M_PI)) + lfact(l - m) - lfact(l + m));
+            const double lnLead = lfact(2 * l) - l * std::log(2.0) - lfact(l) - lfact(l - m);
+            double kl = std::exp(lnN + lnLead);
+            if (m & 1) kl = -kl;
+            coef_off[l * (L + 1) + m] = (int)P->colcoef.size();
+            for (double ck : cheb_coeffs(m, l - m)) P->colcoef.push_back((float)(ck * kl));
+        }
     int col = 0;
     for (int m = 0; m <= L; ++m) {
         const int K = B * (L + 1 - m);
@@ -314,6 +366,8 @@ void compute_columns(g3pcf_plan_t P) {
                 if (m & 1) kl = -kl;
                 P->colmap[col] = b * P->nrp + slot;
                 P->colscale[col] = (float)kl;
+                const int slot0 = (m == 0) ? 0 : acc_base(L, m) + part;
+                P->colconv[col] = int4{b * P->nrp + slot0, m == 0 ? 1 : 2, l - m + 1, coef_off[l * (L + 1) + m]};
                 ++col;
             }
     }
@@ -390,8 +444,8 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st) {
     la.wrow = pa.wrow;
     la.A = pa.A;
     la.RLP = pa.RLP;
-    la.colmap = pa.colmap;
-    la.colscale = pa.colscale;
+    la.colconv = P->d_colconv.as<int4>();
+    la.colcoef = P->d_colcoef.as<float>();
     la.RL = pa.RL;
     la.counts = pa.counts;
     la.queue = pa.queue;
@@ -410,7 +464,7 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st) {
         return fail(G3PCF_ERR_CUDA, "pair count launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     CK(cudaMemcpyAsync(P->h_need, la.need + qa, 4 * nq, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    // pool capacity (per chunk: 128 bytes of entries, tag and list ints, a bin byte)
+    // pool capacity (per chunk: 128 bytes of entries, a tag and a list int)
     int64_t total = 0, most = 0;
     for (int64_t k = 0; k < nq; ++k) {
         total += P->h_need[k];
@@ -420,10 +474,10 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st) {
     if (budget <= 0) {
         size_t fr = 0, tot = 0;
         CK(cudaMemGetInfo(&fr, &tot));
-        budget = 0.4 * (double)(fr + P->l_pool.bytes + P->l_tag.bytes + P->l_ord.bytes + P->l_dir.bytes);
+        budget = 0.4 * (double)(fr + P->l_pool.bytes + P->l_tag.bytes + P->l_ord.bytes);
         if (budget > 32e9) budget = 32e9;
     }
-    int64_t cap = (int64_t)(budget / 137.0);
+    int64_t cap = (int64_t)(budget / 136.0);
     if (cap > ((int64_t)1 << 30)) cap = (int64_t)1 << 30;
     if (cap > total) cap = total;
     if (cap < most)
@@ -431,13 +485,11 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st) {
                     (long long)most, (long long)cap);
     if (cap > 0 && (ensure(P->l_pool, 128 * (size_t)cap, "pair lists") ||
                     ensure(P->l_tag, 4 * (size_t)cap, "pair lists") ||
-                    ensure(P->l_ord, 4 * (size_t)cap, "pair lists") ||
-                    ensure(P->l_dir, (size_t)cap, "pair lists")))
+                    ensure(P->l_ord, 4 * (size_t)cap, "pair lists")))
         return G3PCF_ERR_ALLOC;
     la.chunks = P->l_pool.as<int>();
     la.tag = P->l_tag.as<int>();
     la.ord = P->l_ord.as<int>();
-    la.dir = P->l_dir.as<unsigned char>();
     std::vector<int> cuts{qa};
     int64_t acc = 0;
     for (int64_t k = 0; k < nq; ++k) {
@@ -1217,9 +1269,9 @@ int g3pcf_destroy(g3pcf_plan_t P) {
     DevBuf* bufs[] = {&P->key_a, &P->key_b, &P->val_a, &P->val_b, &P->hist, &P->hist_off,
                       &P->scan_tmp, &P->pts, &P->pts64, &P->orig, &P->cstart, &P->plist,
                       &P->small, &P->counts, &P->A, &P->partials, &P->d_tiles, &P->d_segs,
-                      &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_catoff, &P->d_ranges,
+                      &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_colconv, &P->d_colcoef, &P->d_catoff, &P->d_ranges,
                       &P->d_tiles_tc, &P->ops, &P->d_cats, &P->d_mreal, &P->d_V, &P->d_bintab,
-                      &P->wrow, &P->l_need, &P->l_base, &P->l_nch, &P->l_pool, &P->l_tag, &P->l_ord, &P->l_dir};
+                      &P->wrow, &P->l_need, &P->l_base, &P->l_nch, &P->l_pool, &P->l_tag, &P->l_ord};
     for (DevBuf* b : bufs) b->release();
     if (P->h_need) cudaFreeHost(P->h_need);
     if (P->h_base) cudaFreeHost(P->h_base);

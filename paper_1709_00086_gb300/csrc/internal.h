@@ -143,7 +143,7 @@ size_t pair_smem_per_warp(int lmax, int nbins, int kflush);
 // bound of the list chunks of q); the host sets base[q] (first chunk of q in
 // the pool, relative to the pass) so that a pass fits the pool; k_scan writes
 // the chunks (32 entries j | code << 27, padding 0xffffffff), the list of them
-// ordered by bin (ord, with the bins in dir) and nchunks[q]; k_accum walks that
+// ordered by bin (ord: chunk | bin << 26) and nchunks[q]; k_accum walks that
 // list and writes A rows.
 struct ListArgs {
     const float4* pts;
@@ -158,8 +158,8 @@ struct ListArgs {
     float* wrow;
     float* A;
     int RLP;
-    const int* colmap;
-    const float* colscale;
+    const int4* colconv;     // RL entries: {first res slot, slot stride, terms, coefficient offset}
+    const float* colcoef;    // Chebyshev -> Legendre-form coefficients (times K_lm)
     int RL;
     unsigned long long* counts;
     int* queue;
@@ -167,12 +167,11 @@ struct ListArgs {
     const unsigned char* bintab;
     float bin_tscale;
     int* need;               // [q] (global processing-order index)
-    const int* base;         // [q] first chunk of q, relative to chunks/dir
+    const int* base;         // [q] first chunk of q, relative to the pool arrays
     int* nchunks;            // [q]
     int* chunks;             // pool: 32 ints per chunk
     int* tag;                // pool: (rank among its bin's chunks) << 5 | bin, per chunk
-    int* ord;                // pool: the primary's chunks listed by bin (stable)
-    unsigned char* dir;      // pool: bin of each ord entry
+    int* ord;                // pool: the primary's chunks listed by bin (stable), chunk | bin << 26
     Grid g;
     Bins bins;
 };

@@ -92,6 +92,54 @@ __device__ __forceinline__ void accum_pair(float (&acc)[Shape<L>::NR], float z, 
     });
 }
 
+// Accumulators of the Chebyshev form (pair-list path): for m = 0, acc0[k] +=
+// w T_k(z); for m >= 1, accc[cidx(m) + k] += T_k(z) w (x + iy)^m as (Re, Im),
+// k = 0..L-m.  The T_k (first kind, T_{k+1} = 2z T_k - T_{k-1}) do not depend
+// on m, so one recurrence of L-1 steps serves every m, and each complex term
+// costs one packed FMA.  The monic D_lm(z) of the Legendre form are
+// non-negative combinations of the T_k (Gegenbauer-to-Chebyshev connection
+// coefficients), applied per primary when its row of multipoles is written.
+template <int L>
+struct Cheb {
+    static constexpr int NC = L * (L + 1) / 2;  // (l, m >= 1) terms
+    __host__ __device__ static constexpr int cidx(int m) { return (m - 1) * (L + 1) - (m - 1) * m / 2; }
+};
+
+template <int L>
+__device__ __forceinline__ void accum_pair_cheb(float (&acc0)[L + 1], float2 (&accc)[Cheb<L>::NC > 0 ? Cheb<L>::NC : 1],
+                                                float z, float ux, float uy, float w) {
+    float T[L + 1];
+    T[0] = 1.f;
+    acc0[0] += w;
+    if constexpr (L >= 1) {
+        T[1] = z;
+        const float z2 = z + z;
+        static_for<2, L + 1>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            T[k] = fmaf(z2, T[k - 1], -T[k - 2]);
+        });
+        static_for<1, L + 1>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            acc0[k] = fmaf(w, T[k], acc0[k]);
+        });
+        float2 c = make_float2(w * ux, w * uy);  // w (x + iy)^m, m = 1
+        static_for<1, L + 1>([&](auto mc) {
+            constexpr int m = decltype(mc)::value;
+            constexpr int b = Cheb<L>::cidx(m);
+            accc[b] = __fadd2_rn(accc[b], c);
+            static_for<1, L - m + 1>([&](auto kc) {
+                constexpr int k = decltype(kc)::value;
+                accc[b + k] = __ffma2_rn(make_float2(T[k], T[k]), c, accc[b + k]);
+            });
+            if constexpr (m < L) {
+                const float t = fmaf(c.x, ux, -c.y * uy);
+                c.y = fmaf(c.x, uy, c.y * ux);
+                c.x = t;
+            }
+        });
+    }
+}
+
 __host__ __device__ constexpr int bf_size(int n, int r) { return r == 0 ? n : (bf_size(n, r - 1) + 1) / 2; }
 
 // Sum acc over the 32 lanes by recursive halving (5 rounds of shuffles; the

@@ -142,7 +142,6 @@ __global__ void __launch_bounds__(kLThreads, 6) k_scan(ListArgs a) {
         int* const pool = a.chunks + (int64_t)a.base[q] * kChunk;  // this primary's chunks
         int* const ptag = a.tag + a.base[q];
         int* const pord = a.ord + a.base[q];
-        unsigned char* const pdir = a.dir + a.base[q];
         const int cap_ch = a.need[q];  // chunks reserved for it
         int nch = 0;                   // chunks opened so far (warp-uniform)
         // the open chunk of bin b lives in lane b: its index and fill (kChunk: none open)
@@ -281,10 +280,7 @@ __global__ void __launch_bounds__(kLThreads, 6) k_scan(ListArgs a) {
                 const int t = c < nlist ? ptag[c] : 0;
                 const int b = t & 31;
                 const int pos = __shfl_sync(kFull, off, b) + (t >> 5);
-                if (c < nlist && pos < cap_ch) {
-                    pord[pos] = c;
-                    pdir[pos] = (unsigned char)b;
-                }
+                if (c < nlist && pos < cap_ch) pord[pos] = c | (b << 26);
             }
         }
         if (lane == 0) a.nchunks[q] = nch < cap_ch ? nch : cap_ch;
@@ -294,12 +290,28 @@ __global__ void __launch_bounds__(kLThreads, 6) k_scan(ListArgs a) {
     if (cur_cat >= 0 && lane < B && my_total) atomicAdd(&a.counts[cur_cat * B + lane], my_total);
 }
 
-template <int L>
-__device__ __forceinline__ void pair_term(float (&acc)[Shape<L>::NR], const float4& q, unsigned e,
-                                          const float4* img, const float* R, int radial) {
-    const bool valid = e != kNoPair;
-    float w = 0.f, dx = 1.f, dy = 0.f, dz = 0.f;
-    if (valid) {
+// Asynchronous global -> shared copies (one per lane) and their groups.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+// 16 bytes, or zeros without reading when !valid
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Separation of one list entry from the primary (image img[code]), rotated
+// to the primary's line of sight in radial mode, as a unit vector and weight.
+__device__ __forceinline__ void pair_dir(const float4& q, unsigned e, const float4* img, const float* R,
+                                         int radial, float& z, float& ux, float& uy, float& w) {
+    float dx = 1.f, dy = 0.f, dz = 0.f;
+    w = 0.f;
+    if (e != kNoPair) {
         const float4 o = img[e >> kIdxBits];
         dx = q.x - o.x;
         dy = q.y - o.y;
@@ -314,21 +326,48 @@ __device__ __forceinline__ void pair_term(float (&acc)[Shape<L>::NR], const floa
             dz = rz;
         }
     }
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float rinv = rsqrtf(r2);
-    accum_pair<L>(acc, dz * rinv, dx * rinv, dy * rinv, w);
+    const float rinv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    z = dz * rinv;
+    ux = dx * rinv;
+    uy = dy * rinv;
+}
+
+// Reduce the Chebyshev-form partials over the warp into res_b (accumulator
+// slot layout: m = 0 slot k; m >= 1 slot acc_base(m) + 2k + part).
+template <int L>
+__device__ __forceinline__ void reduce_cheb(float (&acc0)[L + 1], float2 (&accc)[Cheb<L>::NC > 0 ? Cheb<L>::NC : 1],
+                                            int lane, float* res_b) {
+    constexpr int NR = Shape<L>::NR;
+    float acc[NR];
+    static_for<0, L + 1>([&](auto kc) { acc[decltype(kc)::value] = acc0[decltype(kc)::value]; });
+    static_for<0, Cheb<L>::NC>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        acc[L + 1 + 2 * i] = accc[i].x;
+        acc[L + 2 + 2 * i] = accc[i].y;
+    });
+    butterfly_add<L>(acc, lane, res_b);
+}
+
+// Per-warp shared memory of k_accum: res[B][NRP] float, img[27] float4, R[16]
+// float, entry ring [kEntRing][32] uint, point ring [kPtRing][32] float4.
+constexpr int kEntRing = 8;
+constexpr int kPtRing = 4;
+__host__ __device__ constexpr size_t accum_smem_per_warp(int B, int NRP) {
+    return (size_t)B * NRP * 4 + 27 * 16 + 64 + kEntRing * 32 * 4 + kPtRing * 32 * 16;
 }
 
 template <int L>
 __global__ void __launch_bounds__(kLThreads, 3) k_accum(ListArgs a) {
-    constexpr int NR = Shape<L>::NR, NRP = Shape<L>::NRP;
+    constexpr int NRP = Shape<L>::NRP;
     extern __shared__ __align__(16) unsigned char la_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int B = a.bins.nbins;
-    unsigned char* base = la_raw + (size_t)wid * (B * NRP * 4 + 27 * 16 + 64);
-    float* res = reinterpret_cast<float*>(base);
-    float4* img = reinterpret_cast<float4*>(base + B * NRP * 4);
-    float* Rs = reinterpret_cast<float*>(base + B * NRP * 4 + 27 * 16);
+    unsigned char* base = la_raw + (size_t)wid * accum_smem_per_warp(B, NRP);
+    float4* img = reinterpret_cast<float4*>(base);
+    float* Rs = reinterpret_cast<float*>(base + 27 * 16);
+    float4* pring = reinterpret_cast<float4*>(base + 27 * 16 + 64);
+    unsigned* ering = reinterpret_cast<unsigned*>(base + 27 * 16 + 64 + kPtRing * 32 * 16);
+    float* res = reinterpret_cast<float*>(base + 27 * 16 + 64 + kPtRing * 32 * 16 + kEntRing * 32 * 4);
     const Grid& g = a.g;
     const float Lb = g.box;
     for (;;) {
@@ -352,64 +391,90 @@ __global__ void __launch_bounds__(kLThreads, 3) k_accum(ListArgs a) {
             Rs[lane] = g.radial ? los_rotation_entry(lane, x0, x1, x2, g.boxd)
                                 : ((lane % 4 == 0) ? 1.f : 0.f);
         }
-        __syncwarp();
         const int cb = a.base[q];
         const int nch = a.nchunks[q];
         const int* chunks = a.chunks + (int64_t)cb * kChunk;
         const int* ordp = a.ord + cb;
-        const unsigned char* dirp = a.dir + cb;
         for (int k = lane; k < B * NRP; k += 32) res[k] = 0.f;
         __syncwarp();
         if (nch > 0) {
-            auto entry = [&](int c) -> unsigned { return (unsigned)__ldg(chunks + (int64_t)c * kChunk + lane); };
-            auto point = [&](unsigned e) -> float4 {
-                return e != kNoPair ? __ldg(a.pts + (e & kIdxMask)) : make_float4(1.f, 0.f, 0.f, 0.f);
+            // List slot i = chunk (low 26 bits) | bin << 26.  Copies in flight
+            // (cp.async groups): entries up to slot i+4, points up to slot i+2.
+            auto ent_async = [&](int i, unsigned o) {
+                cp_async4(ering + (i & (kEntRing - 1)) * 32 + lane,
+                          chunks + (int64_t)(o & 0x3ffffffu) * kChunk + lane);
             };
-            float acc[NR];
-            static_for<0, NR>([&](auto ic) { acc[decltype(ic)::value] = 0.f; });
-            // chunks in bin order; in flight: list slot i+3, entries of i+2, points of i+1
-            unsigned eA = entry(__ldg(ordp));
-            int bA = dirp[0];
-            float4 qA = point(eA);
-            unsigned eB = kNoPair;
-            int bB = -1, cC = 0, bC = -1;
-            if (nch > 1) {
-                eB = entry(__ldg(ordp + 1));
-                bB = dirp[1];
-            }
-            if (nch > 2) {
-                cC = __ldg(ordp + 2);
-                bC = dirp[2];
-            }
-            int curb = bA;
+            auto pt_async = [&](int i) {
+                const unsigned e = ering[(i & (kEntRing - 1)) * 32 + lane];
+                const bool v = e != kNoPair;
+                cp_async16(pring + (i & (kPtRing - 1)) * 32 + lane, a.pts + (v ? (e & kIdxMask) : 0u), v);
+            };
+            auto slot = [&](int i) -> unsigned { return i < nch ? (unsigned)__ldg(ordp + i) : 0u; };
+            unsigned o0 = slot(0), o1 = slot(1), o2 = slot(2), o3 = slot(3);
+            ent_async(0, o0);
+            if (nch > 1) ent_async(1, o1);
+            cp_async_commit();
+            cp_async_wait<0>();
+            pt_async(0);
+            if (nch > 2) ent_async(2, o2);
+            cp_async_commit();
+            if (nch > 1) pt_async(1);
+            if (nch > 3) ent_async(3, o3);
+            cp_async_commit();
+            // slot words of i .. i+3 in registers, i+4 .. i+6 loading
+            unsigned s4 = slot(4), s5 = slot(5), s6 = slot(6);
+            unsigned sA = o0, sB = o1, sC = o2, sD = o3;
+            constexpr int NC = Cheb<L>::NC > 0 ? Cheb<L>::NC : 1;
+            float acc0[L + 1];
+            float2 accc[NC];
+            auto clear = [&]() {
+                static_for<0, L + 1>([&](auto kc) { acc0[decltype(kc)::value] = 0.f; });
+                static_for<0, NC>([&](auto ic) { accc[decltype(ic)::value] = make_float2(0.f, 0.f); });
+            };
+            clear();
+            int curb = (int)(sA >> 26);
             for (int i = 0; i < nch; ++i) {
-                int cD = 0, bD = -1;
-                if (i + 3 < nch) {
-                    cD = __ldg(ordp + i + 3);
-                    bD = dirp[i + 3];
-                }
-                const unsigned eC = (i + 2 < nch) ? entry(cC) : kNoPair;
-                const float4 qB = point(eB);
+                cp_async_wait<1>();  // entries of i+2 and points of i have landed
+                if (i + 2 < nch) pt_async(i + 2);
+                if (i + 4 < nch) ent_async(i + 4, s4);
+                cp_async_commit();
+                const unsigned s7 = slot(i + 7);
+                const int bA = (int)(sA >> 26);
                 if (bA != curb) {  // the bin changes: reduce the partials of the last one
-                    butterfly_add<L>(acc, lane, res + curb * NRP);
-                    static_for<0, NR>([&](auto ic) { acc[decltype(ic)::value] = 0.f; });
+                    reduce_cheb<L>(acc0, accc, lane, res + curb * NRP);
+                    clear();
                     curb = bA;
                 }
-                pair_term<L>(acc, qA, eA, img, Rs, g.radial);
-                eA = eB;
-                qA = qB;
-                bA = bB;
-                eB = eC;
-                bB = bC;
-                cC = cD;
-                bC = bD;
+                {
+                    const unsigned e = ering[(i & (kEntRing - 1)) * 32 + lane];
+                    const float4 qv = pring[(i & (kPtRing - 1)) * 32 + lane];
+                    float z, ux, uy, w;
+                    pair_dir(qv, e, img, Rs, g.radial, z, ux, uy, w);
+                    accum_pair_cheb<L>(acc0, accc, z, ux, uy, w);
+                }
+                sA = sB;
+                sB = sC;
+                sC = sD;
+                sD = s4;
+                s4 = s5;
+                s5 = s6;
+                s6 = s7;
             }
-            butterfly_add<L>(acc, lane, res + curb * NRP);
+            cp_async_wait<0>();
+            reduce_cheb<L>(acc0, accc, lane, res + curb * NRP);
         }
         __syncwarp();
         const int row = a.chunked ? q - a.q0 : a.orig[p];
         float* Arow = a.A + (int64_t)row * a.RLP;
-        for (int col = lane; col < a.RL; col += 32) Arow[col] = res[a.colmap[col]] * a.colscale[col];
+        // Legendre form: column (l, m, part, b) = sum_k coef_k res[slot0 + stride k]
+        // (the Chebyshev-to-D_lm connection coefficients times K_lm)
+        for (int col = lane; col < a.RL; col += 32) {
+            const int4 cv = __ldg(a.colconv + col);
+            const float* cf = a.colcoef + cv.w;
+            float v = 0.f;
+            for (int k = 0; k < cv.z; ++k) v = fmaf(__ldg(cf + k), res[cv.x + cv.y * k], v);
+            Arow[col] = v;
+        }
         if (lane == 0) a.wrow[row] = P0.w;
         __syncwarp();
     }
@@ -417,9 +482,7 @@ __global__ void __launch_bounds__(kLThreads, 3) k_accum(ListArgs a) {
 
 template <int L>
 int launch_accum_t(const ListArgs& a, int nsm, cudaStream_t st) {
-    constexpr int NRP = Shape<L>::NRP;
-    const size_t per_warp = (size_t)a.bins.nbins * NRP * 4 + 27 * 16 + 64;
-    const size_t smem = per_warp * kLWarps;
+    const size_t smem = accum_smem_per_warp(a.bins.nbins, Shape<L>::NRP) * kLWarps;
     if (cudaFuncSetAttribute(k_accum<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return -1;
