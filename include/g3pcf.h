@@ -172,8 +172,9 @@ int g3pcf_status(g3pcf_plan_t plan);
 /* Per-stage device times (milliseconds, CUDA events) and counters of the last
  * compute call: [0] index build, [1] pair stage, [2] contraction, [3] reduction,
  * [4] total, [5] accepted pairs (as a double), [6] primaries, [7] cells per
- * Rmax used, [8] kernels launched by the call.  Synchronises the stream.
- * At most min(nvals, 9) values are written. */
+ * Rmax used, [8] kernels launched by the call, [9] candidate secondaries
+ * visited (pair-list path; 0 for the fused kernel), [10] passes of the pair
+ * lists.  Synchronises the stream.  At most min(nvals, 11) values are written. */
 int g3pcf_stats(g3pcf_plan_t plan, double* vals, int nvals);
 
 /* zeta from multipoles the caller already holds, without allocating any

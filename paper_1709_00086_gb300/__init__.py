@@ -228,10 +228,10 @@ class Plan:
         _check(lib().g3pcf_status(self._h))
 
     def stats(self) -> dict:
-        v = np.zeros(9)
-        _check(lib().g3pcf_stats(self._h, v.ctypes.data_as(ctypes.c_void_p), 9))
+        v = np.zeros(11)
+        _check(lib().g3pcf_stats(self._h, v.ctypes.data_as(ctypes.c_void_p), 11))
         keys = ["index_ms", "pair_ms", "contract_ms", "reduce_ms", "total_ms", "pairs", "primaries",
-                "cells_per_rmax", "launches"]
+                "cells_per_rmax", "launches", "candidates", "list_passes"]
         return dict(zip(keys, v.tolist()))
 
 

@@ -91,7 +91,7 @@ struct g3pcf_plan_s {
     DevBuf key_a, key_b, val_a, val_b, hist, hist_off, scan_tmp, pts, pts64, orig, cstart, plist;
     DevBuf small;       // status, queue
     DevBuf counts, A, partials, d_tiles, d_segs, d_segfirst, d_colmap, d_colscale, d_catoff;
-    DevBuf d_colconv, d_colcoef;
+    DevBuf d_colconv, d_colcoef, d_bintab_s;
     DevBuf d_ranges, d_tiles_tc, ops, d_cats, d_mreal, d_V, d_bintab, wrow;
     int64_t opt_chunk = 0;   // G3PCF_OPT_CHUNK_ROWS
     // pinned staging for host -> device tables (capturable copies); offset
@@ -114,9 +114,9 @@ struct g3pcf_plan_s {
     int* h_need = nullptr;
     int* h_base = nullptr;
     size_t h_list_cap = 0;
-    int stats_passes = 0;
     bool last_chunked = false;
     std::vector<unsigned char> bintab;  // r^2 -> bin lookup (see compute_bins)
+    std::vector<signed char> bintab_s;  // signed form (pair-list scan)
     float bin_tscale = 0.f;
     // index state of the last forward (for the adjoint pair pass)
     bool last_plist = false;
@@ -133,7 +133,7 @@ struct g3pcf_plan_s {
     int last_pos_f64 = 0;
     Grid last_grid{};
     unsigned* key_sorted = nullptr;
-    double stats[10] = {};
+    double stats[11] = {};
     int launches = 0;
 };
 
@@ -194,8 +194,10 @@ int upload_consts(g3pcf_plan_t P) {
         return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (constants)");
     CK(cudaMemcpy(P->d_tiles_tc.p, P->tiles_tc.data(), P->tiles_tc.size() * sizeof(Tile),
                   cudaMemcpyHostToDevice));
-    if (P->d_bintab.ensure(P->bintab.size())) return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (bin table)");
+    if (P->d_bintab.ensure(P->bintab.size()) || P->d_bintab_s.ensure(P->bintab_s.size()))
+        return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (bin table)");
     CK(cudaMemcpy(P->d_bintab.p, P->bintab.data(), P->bintab.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->d_bintab_s.p, P->bintab_s.data(), P->bintab_s.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->d_colmap.p, P->colmap.data(), P->RL * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->d_colscale.p, P->colscale.data(), P->RL * sizeof(float), cudaMemcpyHostToDevice));
     if (P->d_colconv.ensure(P->colconv.size() * sizeof(int4)) ||
@@ -295,6 +297,17 @@ void compute_bins(g3pcf_plan_t P) {
                 P->bintab[t] = (unsigned char)k;
                 break;
             }
+    }
+    // Signed form for the pair-list scan: bin, -1 surely outside (also every
+    // cell from e_B^2 + g_B up, so the last entry takes all larger r^2), -3 check.
+    P->bintab_s.assign(T + 2, -3);
+    for (int t = 0; t < T + 2; ++t) {
+        const double lo = (t - 0.01) * D, hi = (t + 1.01) * D;
+        const unsigned char v = P->bintab[t];
+        if (v == 254 || lo > b.e2[B] + b.guard[B])
+            P->bintab_s[t] = -1;
+        else if (v < 254)
+            P->bintab_s[t] = (signed char)v;
     }
 }
 
@@ -450,7 +463,7 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st) {
     la.counts = pa.counts;
     la.queue = pa.queue;
     la.status = pa.status;
-    la.bintab = pa.bintab;
+    la.bintab = P->d_bintab_s.as<signed char>();
     la.bin_tscale = pa.bin_tscale;
     la.g = pa.g;
     la.bins = pa.bins;
@@ -459,11 +472,14 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st) {
     la.nchunks = P->l_nch.as<int>();
     la.qa = qa;
     la.qb = qb;
+    la.ncand = reinterpret_cast<unsigned long long*>(pa.status + 24);  // zeroed with the status word
     ++P->launches;
     if (launch_count(la, P->nsm, st) != 0)
         return fail(G3PCF_ERR_CUDA, "pair count launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     CK(cudaMemcpyAsync(P->h_need, la.need + qa, 4 * nq, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(P->h_status + 8, la.ncand, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    P->stats[9] = (double)*reinterpret_cast<unsigned long long*>(P->h_status + 8);
     // pool capacity (per chunk: 128 bytes of entries, a tag and a list int)
     int64_t total = 0, most = 0;
     for (int64_t k = 0; k < nq; ++k) {
@@ -515,7 +531,7 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st) {
         if (launch_accum(P->lmax, la, P->nsm, st) != 0)
             return fail(G3PCF_ERR_CUDA, "pair accumulate launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     }
-    P->stats_passes = (int)cuts.size() - 1;
+    P->stats[10] += (double)(cuts.size() - 1);
     return G3PCF_OK;
 }
 
@@ -529,6 +545,7 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
     P->have_forward = false;
     P->have_alm = false;
     P->launches = 0;
+    P->stats[9] = P->stats[10] = 0.0;
     P->stage_off = 0;
     CK(cudaEventRecord(P->ev[0], st));
     // zero outputs and counters
@@ -1258,7 +1275,7 @@ int g3pcf_stats(g3pcf_plan_t P, double* vals, int nvals) {
         P->stats[5] = tot;
     }
     P->stats[8] = (double)P->launches;
-    for (int k = 0; k < nvals && k < 9; ++k) vals[k] = P->stats[k];
+    for (int k = 0; k < nvals && k < 11; ++k) vals[k] = P->stats[k];
     return G3PCF_OK;
 }
 
@@ -1269,7 +1286,7 @@ int g3pcf_destroy(g3pcf_plan_t P) {
     DevBuf* bufs[] = {&P->key_a, &P->key_b, &P->val_a, &P->val_b, &P->hist, &P->hist_off,
                       &P->scan_tmp, &P->pts, &P->pts64, &P->orig, &P->cstart, &P->plist,
                       &P->small, &P->counts, &P->A, &P->partials, &P->d_tiles, &P->d_segs,
-                      &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_colconv, &P->d_colcoef, &P->d_catoff, &P->d_ranges,
+                      &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_colconv, &P->d_colcoef, &P->d_bintab_s, &P->d_catoff, &P->d_ranges,
                       &P->d_tiles_tc, &P->ops, &P->d_cats, &P->d_mreal, &P->d_V, &P->d_bintab,
                       &P->wrow, &P->l_need, &P->l_base, &P->l_nch, &P->l_pool, &P->l_tag, &P->l_ord};
     for (DevBuf* b : bufs) b->release();

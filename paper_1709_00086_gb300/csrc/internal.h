@@ -164,9 +164,10 @@ struct ListArgs {
     unsigned long long* counts;
     int* queue;
     int* status;
-    const unsigned char* bintab;
+    const signed char* bintab;  // G3_BIN_TABLE + 2: bin, -1 no pair, -3 decide per pair
     float bin_tscale;
     int* need;               // [q] (global processing-order index)
+    unsigned long long* ncand;  // candidates visited (k_count adds)
     const int* base;         // [q] first chunk of q, relative to the pool arrays
     int* nchunks;            // [q]
     int* chunks;             // pool: 32 ints per chunk

@@ -358,5 +358,35 @@ __device__ __forceinline__ int decide_bin(float r2, float hi_rej, float lo_rej, 
     return bin;
 }
 
+// decide_bin split for warp-wide use: bin_fast settles almost every
+// candidate with one lookup in the signed r^2 table (bin, -1 = no pair, -3 =
+// in a guard band or an ambiguous cell; indices past the table clamp to its
+// last entry, which is -1); bin_slow finishes the -3 cases.
+__device__ __forceinline__ int bin_fast(float r2, float tscale, const signed char* tab) {
+    int ti = (int)(r2 * tscale);
+    ti = ti > kBinTable + 1 ? kBinTable + 1 : ti;
+    return tab[ti];
+}
+__device__ __noinline__ int bin_slow(float r2, float lo_rej, float hi_rej, float guard0, const float2* dec,
+                                     float rminf, float invw, int B, bool exact_inputs, int code,
+                                     const float4* __restrict__ pts, const double* pts64, int j,
+                                     const double* pd, double boxd, int periodic, const double* e2) {
+    if (r2 < lo_rej || !(r2 < hi_rej)) return -1;
+    int bin;
+    if (!(r2 > guard0)) {
+        bin = (exact_inputs && code == 13 && r2 == 0.f) ? -1 : -2;
+    } else {
+        const float rr = r2 * rsqrtf(r2);
+        int bb = (int)((rr - rminf) * invw);
+        bb = bb < 0 ? 0 : (bb >= B ? B - 1 : bb);
+        const float2 iv = dec[bb];
+        bin = (r2 > iv.x && r2 < iv.y) ? bb : -2;
+    }
+    if (bin == -2)
+        bin = exact_bin(pts, pts64, j, pd[0], pd[1], pd[2], code % 3 - 1, (code / 3) % 3 - 1,
+                        code / 9 - 1, boxd, periodic, e2, B);
+    return bin;
+}
+
 }  // namespace
 }  // namespace g3

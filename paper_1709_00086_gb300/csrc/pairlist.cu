@@ -33,19 +33,24 @@ namespace {
 constexpr int kLWarps = 4;
 constexpr int kLThreads = kLWarps * 32;
 constexpr int kChunk = 32;      // pairs per list chunk
-constexpr int kRing = 64;       // compaction stage of k_scan (entries)
+constexpr int kStage = 256;     // compaction stage of k_scan (entries)
+constexpr int kTrip = 4;        // candidate sub-iterations per trip in k_scan
 constexpr unsigned kNoPair = 0xffffffffu;  // padding entry of a list chunk (image code 31 is unused)
 
 // Per-warp shared memory of k_scan: img[27] float4, pd[4] double,
-// pcs[kMaxPieces] int4, stage[kRing] int2 (accepted pairs: entry, bin).
+// pcs[kMaxPieces] int4, stage[kStage + 32] int2 (accepted pairs: entry, bin;
+// the last 32 are scratch), per-bin fill / open chunk / chunk count.
 struct ScanSmem {
     float4* img;
     double* pd;
     int4* pcs;
     int2* stage;
+    int* bfill;
+    int* bcur;
+    int* bnbc;
 };
 __host__ __device__ constexpr size_t scan_smem_per_warp(int) {
-    return 27 * 16 + 4 * 8 + kMaxPieces * 16 + kRing * 8;
+    return 27 * 16 + 4 * 8 + kMaxPieces * 16 + (kStage + 32) * 8 + 3 * 32 * 4;
 }
 __device__ __forceinline__ ScanSmem scan_smem(unsigned char* raw, int wid, int B) {
     unsigned char* b = raw + (size_t)wid * scan_smem_per_warp(B);
@@ -54,6 +59,9 @@ __device__ __forceinline__ ScanSmem scan_smem(unsigned char* raw, int wid, int B
     S.pd = reinterpret_cast<double*>(b + 27 * 16);
     S.pcs = reinterpret_cast<int4*>(b + 27 * 16 + 32);
     S.stage = reinterpret_cast<int2*>(b + 27 * 16 + 32 + kMaxPieces * 16);
+    S.bfill = reinterpret_cast<int*>(b + 27 * 16 + 32 + kMaxPieces * 16 + (kStage + 32) * 8);
+    S.bcur = S.bfill + 32;
+    S.bnbc = S.bcur + 32;
     return S;
 }
 
@@ -78,19 +86,18 @@ __global__ void __launch_bounds__(kLThreads) k_count(ListArgs a) {
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
-        if (lane == 0) a.need[q] = (int)((sum + kChunk - 1) / kChunk) + a.bins.nbins;
+        if (lane == 0) {
+            a.need[q] = (int)((sum + kChunk - 1) / kChunk) + a.bins.nbins;
+            atomicAdd(a.ncand, (unsigned long long)sum);
+        }
     }
 }
 
-// NB: bits of the multisplit key (5 when nbins <= 31, key 31 = no pair; 6 for
-// nbins = 32, key 63 = no pair).
-template <int NB>
 __global__ void __launch_bounds__(kLThreads, 6) k_scan(ListArgs a) {
     extern __shared__ __align__(16) unsigned char ls_raw[];
     __shared__ double s_e2[kMaxBins + 1];
     __shared__ float2 s_dec[kMaxBins];
-    __shared__ unsigned char s_tab[kBinTable + 2];
-    constexpr int kNone = (1 << NB) - 1;
+    __shared__ signed char s_tab[kBinTable + 2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int B = a.bins.nbins;
     for (int k = threadIdx.x; k <= B; k += blockDim.x) {
@@ -102,9 +109,6 @@ __global__ void __launch_bounds__(kLThreads, 6) k_scan(ListArgs a) {
     __syncthreads();
     const ScanSmem S = scan_smem(ls_raw, wid, B);
     const unsigned lt = lanemask_lt();
-    unsigned lrep[NB];  // all ones where bit k of lane is 0
-#pragma unroll
-    for (int k = 0; k < NB; ++k) lrep[k] = ((lane >> k) & 1) ? 0u : ~0u;
     const Grid& g = a.g;
     const float Lb = g.box;
     const bool exact_inputs = (a.pts64 == nullptr);
@@ -144,77 +148,64 @@ __global__ void __launch_bounds__(kLThreads, 6) k_scan(ListArgs a) {
         int* const pord = a.ord + a.base[q];
         const int cap_ch = a.need[q];  // chunks reserved for it
         int nch = 0;                   // chunks opened so far (warp-uniform)
-        // the open chunk of bin b lives in lane b: its index and fill (kChunk: none open)
-        int ccur = 0, cfill = kChunk;
-        int nbc = 0;                   // chunks of bin lane opened so far
-        unsigned padd = 0;             // pairs of bin lane for this primary
+        // per-bin state in shared memory: fill of the open chunk (kChunk: none
+        // open), its index, chunks opened so far
+        if (lane < B) {
+            S.bfill[lane] = kChunk;
+            S.bcur[lane] = 0;
+            S.bnbc[lane] = 0;
+        }
+        __syncwarp();
 
         // Place one accepted pair per lane (bin < 0: none) into the open chunk of
-        // its bin, opening a new chunk where a bin's chunk fills.  NB ballots over
-        // the key bits give lane b the lanes whose key is b; a shuffle from lane
-        // key hands every lane its peers (rank = peers below it).
+        // its bin, opening a new chunk where a bin's chunk fills.  Lanes with the
+        // same bin form a group (match); its lowest lane updates the bin state.
         auto place = [&](int entry, int bin) {
-            const int key = bin >= 0 ? bin : kNone;
-            unsigned ofme = kFull;
-#pragma unroll
-            for (int k = 0; k < NB; ++k) ofme &= __ballot_sync(kFull, (key >> k) & 1) ^ lrep[k];
-            const int add = lane < B ? __popc(ofme) : 0;
-            const bool grow = cfill + add > kChunk;  // at most one new chunk per call
-            const unsigned gm = __ballot_sync(kFull, grow);
-            const int nnew = nch + __popc(gm & lt);
+            const bool v = bin >= 0;
+            const unsigned mine = __match_any_sync(kFull, v ? bin : 63);
+            const int rank = __popc(mine & lt);
+            const int cnt = __popc(mine);
+            const int bs = v ? bin : 0;
+            const int fill = S.bfill[bs], cur = S.bcur[bs];
+            const bool grow = v && fill + cnt > kChunk;  // at most one new chunk per call
+            const bool lead = v && rank == 0;
+            const unsigned gm = __ballot_sync(kFull, grow && rank == 0);
+            const unsigned below_leader = mine & (0u - mine);  // lowest lane of the group
+            const int nnew = nch + __popc(gm & (below_leader - 1u));
             nch += __popc(gm);
-            const int src = key & 31;
-            const unsigned mine = __shfl_sync(kFull, ofme, src);
-            const int cur = __shfl_sync(kFull, ccur, src);
-            const int fill = __shfl_sync(kFull, cfill, src);
-            const int nxt = __shfl_sync(kFull, nnew, src);
-            if (bin >= 0) {
-                const int pos = fill + __popc(mine & lt);
-                const int c = pos < kChunk ? cur : nxt;
-                if (c < cap_ch) pool[(int64_t)c * kChunk + (pos & (kChunk - 1))] = entry;
+            const int pos = fill + rank;
+            const int c = pos < kChunk ? cur : nnew;
+            if (v && c < cap_ch) pool[(int64_t)c * kChunk + (pos & (kChunk - 1))] = entry;
+            __syncwarp();
+            if (lead) {
+                S.bfill[bin] = grow ? fill + cnt - kChunk : fill + cnt;
+                if (grow) {
+                    const int nb = S.bnbc[bin];
+                    if (nnew < cap_ch)
+                        ptag[nnew] = (nb << 5) | bin;  // (rank among the bin's chunks, bin)
+                    else
+                        atomicOr(a.status, kStatusOverflow);
+                    S.bnbc[bin] = nb + 1;
+                    S.bcur[bin] = nnew;
+                }
             }
-            if (grow) {
-                if (nnew < cap_ch)
-                    ptag[nnew] = (nbc << 5) | lane;  // (rank among the bin's chunks, bin)
-                else
-                    atomicOr(a.status, kStatusOverflow);
-                ++nbc;
-                ccur = nnew;
-                cfill = cfill + add - kChunk;
-            } else {
-                cfill += add;
-            }
-            padd += add;
+            __syncwarp();
         };
         // accepted pairs are first compacted into stage (warp-uniform head/count)
         int shead = 0, scnt = 0;
-        auto candidate = [&](const float4& qq, int j, int end, int code, const float4& o) {
-            int bin = -1;
-            if (j < end) {
-                const float dx = qq.x - o.x, dy = qq.y - o.y, dz = qq.z - o.z;
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                bin = decide_bin(r2, hi_rej, lo_rej, tscale, s_tab, guard0, s_dec, rminf, invw, B,
-                                 exact_inputs, code, a.pts, a.pts64, j, S.pd, g.boxd, g.periodic, s_e2);
-            }
-            const unsigned vm = __ballot_sync(kFull, bin >= 0);
-            if (vm) {
-                if (bin >= 0)
-                    S.stage[(shead + scnt + __popc(vm & lt)) & (kRing - 1)] =
-                        make_int2((int)((unsigned)j | ((unsigned)code << kIdxBits)), bin);
-                scnt += __popc(vm);
-                if (scnt >= kChunk) {
-                    __syncwarp();
-                    const int2 v = S.stage[(shead + lane) & (kRing - 1)];
-                    shead = (shead + kChunk) & (kRing - 1);
-                    scnt -= kChunk;
-                    __syncwarp();
-                    place(v.x, v.y);
-                }
+        auto drain = [&]() {
+            while (scnt >= kChunk) {
+                __syncwarp();
+                const int2 v = S.stage[(shead + lane) & (kStage - 1)];
+                shead = (shead + kChunk) & (kStage - 1);
+                scnt -= kChunk;
+                __syncwarp();
+                place(v.x, v.y);
             }
         };
 
-        // candidates: batches of 32 cell rows -> slot ranges (pieces) -> 64 slots
-        // per trip, two loads in flight per lane
+        // candidates: batches of 32 cell rows -> slot ranges (pieces) -> up to
+        // kTrip x 32 slots per trip, all loads of a trip in flight together
         for (int rb = 0; rb < nrows; rb += 32) {
             int4 pm = make_int4(0, 0, 0, 0), p0 = pm, pp = pm;
             const int r = rb + lane;
@@ -238,23 +229,68 @@ __global__ void __launch_bounds__(kLThreads, 6) k_scan(ListArgs a) {
             for (int pi = 0; pi < npcs; ++pi) {
                 const int4 pc = S.pcs[pi];
                 const float4 o = S.img[pc.z];
-                for (int j0 = pc.x; j0 < pc.y; j0 += 2 * kChunk) {
-                    const int ja = j0 + lane, jb = ja + kChunk;
-                    float4 qa = o, qb = o;
-                    if (ja < pc.y) qa = __ldg(a.pts + ja);
-                    if (jb < pc.y) qb = __ldg(a.pts + jb);
-                    candidate(qa, ja, pc.y, pc.z, o);
-                    if (j0 + kChunk < pc.y) candidate(qb, jb, pc.y, pc.z, o);
+                const unsigned codebits = (unsigned)pc.z << kIdxBits;
+                for (int j0 = pc.x; j0 < pc.y; j0 += kTrip * kChunk) {
+                    const int nu = (pc.y - j0 + kChunk - 1) / kChunk;  // sub-iterations with slots
+                    // slots past the piece read as a far point (r^2 ~ 1e36: no pair)
+                    float4 qv[kTrip];
+#pragma unroll
+                    for (int u = 0; u < kTrip; ++u) {
+                        const int j = j0 + u * kChunk + lane;
+                        qv[u] = make_float4(o.x + 1e18f, o.y, o.z, 0.f);
+                        if (j < pc.y) qv[u] = __ldg(a.pts + j);
+                    }
+                    int bn[kTrip];
+                    bool chk = false;
+#pragma unroll
+                    for (int u = 0; u < kTrip; ++u) {
+                        const float dx = qv[u].x - o.x, dy = qv[u].y - o.y, dz = qv[u].z - o.z;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        bn[u] = bin_fast(r2, tscale, s_tab);
+                        chk |= bn[u] < -1;
+                    }
+                    if (__any_sync(kFull, chk)) {
+#pragma unroll
+                        for (int u = 0; u < kTrip; ++u) {
+                            if (bn[u] == -3) {
+                                const int j = j0 + u * kChunk + lane;
+                                const float dx = qv[u].x - o.x, dy = qv[u].y - o.y, dz = qv[u].z - o.z;
+                                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                                bn[u] = bin_slow(r2, lo_rej, hi_rej, guard0, s_dec, rminf, invw, B, exact_inputs,
+                                                 pc.z, a.pts, a.pts64, j, S.pd, g.boxd, g.periodic, s_e2);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kTrip; ++u) {
+                        if (u < nu) {
+                            // accepted lanes append in lane order; the others write a scratch slot
+                            const bool acc = bn[u] >= 0;
+                            const unsigned vm = __ballot_sync(kFull, acc);
+                            const int at = acc ? ((shead + scnt + __popc(vm & lt)) & (kStage - 1)) : kStage + lane;
+                            S.stage[at] = make_int2((int)((unsigned)(j0 + u * kChunk + lane) | codebits), bn[u]);
+                            scnt += __popc(vm);
+                        }
+                    }
+                    drain();
                 }
             }
             __syncwarp();
         }
         if (scnt > 0) {  // the last accepted pairs (fewer than 32)
             __syncwarp();
-            const int2 v = lane < scnt ? S.stage[(shead + lane) & (kRing - 1)] : make_int2(0, -1);
+            const int2 v = lane < scnt ? S.stage[(shead + lane) & (kStage - 1)] : make_int2(0, -1);
             __syncwarp();
             place(v.x, v.y);
         }
+        // the bin state back in lane b
+        int cfill = kChunk, ccur = 0, nbc = 0;
+        if (lane < B) {
+            cfill = S.bfill[lane];
+            ccur = S.bcur[lane];
+            nbc = S.bnbc[lane];
+        }
+        const unsigned padd = nbc > 0 ? (unsigned)((nbc - 1) * kChunk + cfill) : 0u;  // pairs of bin lane
         // pad the open chunks behind their last entry
         unsigned pmask = __ballot_sync(kFull, lane < B && cfill < kChunk);
         while (pmask) {
@@ -498,20 +534,18 @@ int launch_accum_t(const ListArgs& a, int nsm, cudaStream_t st) {
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-template <int NB>
-int launch_scan_t(const ListArgs& a, int nsm, cudaStream_t st) {
+int launch_scan_k(const ListArgs& a, int nsm, cudaStream_t st) {
     const size_t smem = scan_smem_per_warp(a.bins.nbins) * kLWarps;
-    if (cudaFuncSetAttribute(k_scan<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return -1;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan<NB>, kLThreads, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan, kLThreads, smem) != cudaSuccess ||
         per_sm < 1)
         return -1;
     int blocks = per_sm * nsm;
     const int need = (a.qb - a.qa + kLWarps - 1) / kLWarps;
     if (blocks > need) blocks = need;
-    k_scan<NB><<<blocks, kLThreads, smem, st>>>(a);
+    k_scan<<<blocks, kLThreads, smem, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -528,7 +562,7 @@ int launch_count(const ListArgs& a, int nsm, cudaStream_t st) {
 
 int launch_scan(const ListArgs& a, int nsm, cudaStream_t st) {
     if (a.qb <= a.qa) return 0;
-    return a.bins.nbins < 32 ? launch_scan_t<5>(a, nsm, st) : launch_scan_t<6>(a, nsm, st);
+    return launch_scan_k(a, nsm, st);
 }
 
 int launch_accum(int lmax, const ListArgs& a, int nsm, cudaStream_t st) {
