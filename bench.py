@@ -50,10 +50,19 @@ def zeta_flops_per_primary(nbins: int, L: int) -> int:
     return sum(4 * (nbins * (L + 1 - m)) * (nbins * (L + 1 - m) + 1) for m in range(L + 1))
 
 
-# DRAM bytes of one pair-stage launch per primary, from the ncu capture
-# summarised in profiles/k_pair_clustered_203k_L700.md (0.972 GB for 203,000
-# primaries: one 4.86 KB multipole row each); traffic grows with primaries.
-PAIR_DRAM_BYTES_PER_PRIMARY = 0.972e9 / 203000
+# Executed FP32 flops per pair of the accumulate kernel (Chebyshev form, FMA = 2):
+# T_k recurrence 2(L-1), m = 0 sums 2L + 1, m >= 1 terms 2 L + 4 L (L - 1) / 2 x 2,
+# (x + iy)^m 6 (L - 1) + 2, separation and unit vector 12.
+def accum_exec_flops(L: int) -> int:
+    if L == 0:
+        return 13
+    return 2 * (L - 1) + (2 * L + 1) + 2 * L + 4 * (L * (L + 1) // 2 - L) + 6 * (L - 1) + 2 + 12
+
+
+# DRAM bytes of one k_accum launch per primary, from the ncu capture summarised
+# in profiles/k_accum_clustered_200k_L696.md (17.59 GB for 200,000 primaries,
+# Lambda = 10); a full-size launch is scaled by its primaries.
+ACCUM_DRAM_BYTES_PER_PRIMARY = 17.59e9 / 200000
 
 
 def peaks():
@@ -262,27 +271,39 @@ def run_ours(args):
     pk = peaks()
     clk_max = float(pk.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp32_peak = 2.0 * 128 * n_sm * clk_max * 1e6 / 1e12  # TFLOP/s, FMA = 2 flop
-    achieved = pairs * pair_flops(L) / (pair_ms / 1e3) / 1e12
+    nominal = 2.0 * 128 * n_sm * clk_max * 1e6 / 1e12  # TFLOP/s, FMA = 2 flop
+    fp32_peak = g3.fp32_peak_tflops()
+    accum_ms = float(np.mean([s["accum_ms"] for s in st_tc]))
+    scan_ms = float(np.mean([s["scan_ms"] for s in st_tc]))
+    n_acc = int(st_tc[-1]["accum_launches"]) or 1
+    achieved = pairs * pair_flops(L) / (accum_ms / 1e3) / 1e12
+    executed = pairs * accum_exec_flops(L) / (accum_ms / 1e3) / 1e12
     out = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "form": "split-BF16 tensor-core contraction",
                    "pairs_per_step": pairs, "primaries": nprim,
+                   "candidates_per_step": st_tc[-1]["candidates"],
                    "l2": "256 MB buffer written between timed steps; per-step working set > L2",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "zeta_tflops": zf / (con_tc / 1e3) / 1e12,
         "stage_ms": {"index": float(np.mean([s["index_ms"] for s in st_tc])), "pair": pair_ms,
+                     "pair_scan": scan_ms, "pair_accum": accum_ms,
                      "contract": con_tc, "reduce": float(np.mean([s["reduce_ms"] for s in st_tc]))},
         "fp32_form": {"ms_per_step": float(np.mean(ms_32)), "value": pairs / (np.mean(ms_32) / 1e3),
                       "contract_ms": con_32, "zeta_tflops": zf / (con_32 / 1e3) / 1e12,
                       "max_rel_diff_vs_tc": diff},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak,
-                     "traffic": PAIR_DRAM_BYTES_PER_PRIMARY * nprim if L == 10 else None,
-                     "kernel": "k_pair (FP32 FMA pipe; peak = 2 x 128 FP32 lanes x %d SMs x %.0f MHz)" % (n_sm, clk_max),
-                     "flops_per_pair": pair_flops(L)},
+                     "traffic": ACCUM_DRAM_BYTES_PER_PRIMARY * nprim / n_acc if L == 10 else None,
+                     "kernel": "k_accum<%d> (FP32 FMA pipe), %d launches per step, %.2f ms per launch"
+                               % (L, n_acc, accum_ms / n_acc),
+                     "peak_source": "measured: g3pcf_fp32_peak FMA-chain probe on this GPU "
+                                    "(nominal 2 x 128 lanes x %d SMs x %.0f MHz = %.1f)" % (n_sm, clk_max, nominal),
+                     "flops_per_pair": pair_flops(L),
+                     "executed_flops_per_pair": accum_exec_flops(L),
+                     "executed_tflops": executed},
         "e2e": {"value": e2e_val, "unit": "pairs/s",
                 "h2d_bytes_per_step": int(hpos.numel() * 4 + hw.numel() * 4),
                 "d2h_bytes_per_step": int(hz.numel() * 8)},

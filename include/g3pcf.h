@@ -157,8 +157,9 @@ int g3pcf_alm(g3pcf_plan_t plan, const int64_t* primaries, int64_t np, double* o
 
 /* Autotuner (a project-written search, not in the paper): times the pair stage
  * on a bounded sample (the first min(n, 8192) points as primaries, all n as
- * secondaries) for cell resolutions around the density heuristic and two flush
- * sizes, and keeps the fastest on the plan (as if set with g3pcf_set_option).
+ * secondaries) for cell resolutions around the density heuristic (and, when
+ * the plan uses the fused pair kernel, two flush sizes), and keeps the fastest
+ * on the plan (as if set with g3pcf_set_option).
  * pos/w as for g3pcf_compute_ex (flags: G3PCF_F_POS_F64 only).  chosen (HOST,
  * may be NULL) receives {cells per rmax, kflush, pair-stage microseconds}.
  * Allocates a temporary zeta buffer; synchronises the plan's stream. */
@@ -174,7 +175,9 @@ int g3pcf_status(g3pcf_plan_t plan);
  * [4] total, [5] accepted pairs (as a double), [6] primaries, [7] cells per
  * Rmax used, [8] kernels launched by the call, [9] candidate secondaries
  * visited (pair-list path; 0 for the fused kernel), [10] passes of the pair
- * lists.  Synchronises the stream.  At most min(nvals, 11) values are written. */
+ * lists, [11] and [12] summed device times (ms) of the list scan and
+ * accumulate kernels, [13] accumulate launches.  Synchronises the stream.
+ * At most min(nvals, 14) values are written. */
 int g3pcf_stats(g3pcf_plan_t plan, double* vals, int nvals);
 
 /* zeta from multipoles the caller already holds, without allocating any
@@ -201,6 +204,12 @@ int g3pcf_stats(g3pcf_plan_t plan, double* vals, int nvals);
  * segment of partials would not fit return G3PCF_ERR_ARG. */
 int g3pcf_zeta_from_alm_noalloc(int nbins, int lmax, const float* alm, int64_t ld,
                                 const float* w, int64_t np, double* zeta, void* stream);
+
+/* Diagnostic: measured FP32 FMA throughput of the current device (TFLOP/s,
+ * one FMA = 2 flop), best of 5 timed launches of an FMA-chain kernel that fills
+ * every SM.  The denominator of the pair stage's roofline.  stream may be NULL.
+ * Allocates and frees a small device buffer; synchronises the stream. */
+int g3pcf_fp32_peak(double* tflops, void* stream);
 
 /* Tuning knobs of a plan (0 = automatic, the default for each):
  *   G3PCF_OPT_CHUNK_ROWS      primaries per pass of the pair stage + contraction;

@@ -61,6 +61,8 @@ def lib():
         L.g3pcf_destroy.argtypes = [P]
         L.g3pcf_autotune.argtypes = [P, P, P, I64, I, P]
         L.g3pcf_autotune.restype = I
+        L.g3pcf_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), P]
+        L.g3pcf_fp32_peak.restype = I
         L.g3pcf_set_option.argtypes = [P, I, I64]
         L.g3pcf_set_option.restype = I
         L.g3pcf_zeta_from_alm_noalloc.argtypes = [I, I, P, I64, P, I64, P, P]
@@ -76,6 +78,13 @@ def lib():
 def _check(rc: int):
     if rc != 0:
         raise G3PCFError(rc, lib().g3pcf_last_error().decode())
+
+
+def fp32_peak_tflops(stream=None) -> float:
+    """Measured FP32 FMA throughput of the current device (TFLOP/s)."""
+    v = ctypes.c_double(0.0)
+    _check(lib().g3pcf_fp32_peak(ctypes.byref(v), stream))
+    return v.value
 
 
 def zeta_size(nbins: int, lmax: int) -> int:
@@ -228,10 +237,11 @@ class Plan:
         _check(lib().g3pcf_status(self._h))
 
     def stats(self) -> dict:
-        v = np.zeros(11)
-        _check(lib().g3pcf_stats(self._h, v.ctypes.data_as(ctypes.c_void_p), 11))
+        v = np.zeros(14)
+        _check(lib().g3pcf_stats(self._h, v.ctypes.data_as(ctypes.c_void_p), 14))
         keys = ["index_ms", "pair_ms", "contract_ms", "reduce_ms", "total_ms", "pairs", "primaries",
-                "cells_per_rmax", "launches", "candidates", "list_passes"]
+                "cells_per_rmax", "launches", "candidates", "list_passes", "scan_ms", "accum_ms",
+                "accum_launches"]
         return dict(zip(keys, v.tolist()))
 
 

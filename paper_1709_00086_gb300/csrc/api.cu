@@ -114,6 +114,9 @@ struct g3pcf_plan_s {
     int* h_need = nullptr;
     int* h_base = nullptr;
     size_t h_list_cap = 0;
+    // events around every k_scan / k_accum launch of the last forward (4 per pass)
+    std::vector<cudaEvent_t> lev;
+    int lev_used = 0;
     bool last_chunked = false;
     std::vector<unsigned char> bintab;  // r^2 -> bin lookup (see compute_bins)
     std::vector<signed char> bintab_s;  // signed form (pair-list scan)
@@ -133,7 +136,7 @@ struct g3pcf_plan_s {
     int last_pos_f64 = 0;
     Grid last_grid{};
     unsigned* key_sorted = nullptr;
-    double stats[11] = {};
+    double stats[14] = {};
     int launches = 0;
 };
 
@@ -522,14 +525,25 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st) {
         la.qa = cuts[k];
         la.qb = cuts[k + 1];
         if (la.qb <= la.qa) continue;
+        while ((int)P->lev.size() < P->lev_used + 4) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            P->lev.push_back(e);
+        }
+        cudaEvent_t* ev = P->lev.data() + P->lev_used;
+        P->lev_used += 4;
         CK(cudaMemsetAsync(la.queue, 0, sizeof(int), st));
         ++P->launches;
+        CK(cudaEventRecord(ev[0], st));
         if (launch_scan(la, P->nsm, st) != 0)
             return fail(G3PCF_ERR_CUDA, "pair scan launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        CK(cudaEventRecord(ev[1], st));
         CK(cudaMemsetAsync(la.queue, 0, sizeof(int), st));
         ++P->launches;
+        CK(cudaEventRecord(ev[2], st));
         if (launch_accum(P->lmax, la, P->nsm, st) != 0)
             return fail(G3PCF_ERR_CUDA, "pair accumulate launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        CK(cudaEventRecord(ev[3], st));
     }
     P->stats[10] += (double)(cuts.size() - 1);
     return G3PCF_OK;
@@ -546,6 +560,7 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
     P->have_alm = false;
     P->launches = 0;
     P->stats[9] = P->stats[10] = 0.0;
+    P->lev_used = 0;
     P->stage_off = 0;
     CK(cudaEventRecord(P->ev[0], st));
     // zero outputs and counters
@@ -1191,9 +1206,12 @@ int g3pcf_autotune(g3pcf_plan_t P, const void* pos, const float* w, int64_t n, i
     double best = 1e300;
     int best_s = s0, best_kf = kmax;
     int rc = G3PCF_OK;
+    // the flush size matters to the fused kernel only (G3PCF_OPT_PAIR_KERNELS = 1)
+    const bool fused = P->opt_pair == 1;
+    const int kf_alt = fused ? (kmax > 6 ? kmax - 4 : kmax) : saved_kf;
     for (int s = s0 - 1; s <= s0 + 2 && rc == G3PCF_OK; ++s) {
         if (s < 1 || s > 8) continue;
-        for (int kf : {kmax, kmax > 6 ? kmax - 4 : kmax}) {
+        for (int kf : {fused ? kmax : saved_kf, kf_alt}) {
             P->opt_cells = s;
             P->kflush = kf;
             CallSpec c;
@@ -1221,7 +1239,7 @@ int g3pcf_autotune(g3pcf_plan_t P, const void* pos, const float* w, int64_t n, i
                 best_s = s;
                 best_kf = kf;
             }
-            if (kf == (kmax > 6 ? kmax - 4 : kmax)) break;
+            if (kf == kf_alt) break;
         }
     }
     cudaFree(ztmp);
@@ -1275,7 +1293,18 @@ int g3pcf_stats(g3pcf_plan_t P, double* vals, int nvals) {
         P->stats[5] = tot;
     }
     P->stats[8] = (double)P->launches;
-    for (int k = 0; k < nvals && k < 11; ++k) vals[k] = P->stats[k];
+    double scan_ms = 0.0, accum_ms = 0.0;
+    for (int k = 0; k + 3 < P->lev_used; k += 4) {
+        float a = 0.f, b = 0.f;
+        CK(cudaEventElapsedTime(&a, P->lev[k], P->lev[k + 1]));
+        CK(cudaEventElapsedTime(&b, P->lev[k + 2], P->lev[k + 3]));
+        scan_ms += a;
+        accum_ms += b;
+    }
+    P->stats[11] = scan_ms;
+    P->stats[12] = accum_ms;
+    P->stats[13] = (double)(P->lev_used / 4);
+    for (int k = 0; k < nvals && k < 14; ++k) vals[k] = P->stats[k];
     return G3PCF_OK;
 }
 
@@ -1300,6 +1329,7 @@ int g3pcf_destroy(g3pcf_plan_t P) {
         if (e) cudaEventDestroy(e);
     for (auto& e : P->ev)
         if (e) cudaEventDestroy(e);
+    for (auto& e : P->lev) cudaEventDestroy(e);
     delete P;
     return G3PCF_OK;
 }

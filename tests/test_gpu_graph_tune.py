@@ -1,10 +1,11 @@
 """CUDA-graph replay of the batched forward and the autotuner.
 
-A captured graph must reproduce the plain call bit for bit (same kernels and
-inputs; every reduction has a fixed order), and a replay after the input
-buffers were overwritten in place must compute the new data.  The autotuner
-must return settings inside their ranges and leave the plan producing the
-oracle's counts and zeta.
+A captured graph runs the fused pair kernel, so it must reproduce a plain call
+made with the fused kernel bit for bit (same kernels and inputs; every
+reduction has a fixed order) and the default pair-list call within tolerance;
+a replay after the input buffers were overwritten in place must compute the
+new data.  The autotuner must return settings inside their ranges and leave
+the plan producing the oracle's counts and zeta.
 """
 import numpy as np
 import pytest
@@ -35,7 +36,12 @@ def test_graph_replay_matches_plain_and_follows_new_data(tc):
     plan = g3.Plan(**cats[0].params())
     dpos = torch.from_numpy(pos).cuda()
     dw = torch.from_numpy(w).cuda()
-    z0, c0 = plan.compute_batch(dpos, dw, offs, fp32_contraction=not tc)
+    zl, cl = plan.compute_batch(dpos, dw, offs, fp32_contraction=not tc)  # pair lists
+    plan.set_option(g3.OPT_PAIR_KERNELS, 1)
+    z0, c0 = plan.compute_batch(dpos, dw, offs, fp32_contraction=not tc)  # fused kernel
+    plan.set_option(g3.OPT_PAIR_KERNELS, 0)
+    assert torch.equal(cl, c0)
+    assert maxrel(zl.cpu().numpy(), z0.cpu().numpy()) < (1e-4 if tc else 1e-5)
     zbuf = torch.empty((len(cats), plan.zsize, 2), dtype=torch.float64, device="cuda")
     cbuf = torch.empty((len(cats), plan.nbins), dtype=torch.int64, device="cuda")
     for _ in range(3):  # capture, then two replays
