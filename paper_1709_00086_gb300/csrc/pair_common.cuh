@@ -122,18 +122,23 @@ __device__ __forceinline__ void accum_pair_cheb(float (&acc0)[L + 1], float2 (&a
             constexpr int k = decltype(kc)::value;
             acc0[k] = fmaf(w, T[k], acc0[k]);
         });
-        float2 c = make_float2(w * ux, w * uy);  // w (x + iy)^m, m = 1
+        // w (x + iy)^m as two interleaved chains (odd m from m = 1, even m
+        // from m = 2, each stepping by (x + iy)^2) to halve the dependency depth
+        const float u2x = fmaf(ux, ux, -uy * uy), u2y = 2.f * ux * uy;
+        float2 co = make_float2(w * ux, w * uy);                      // m = 1
+        float2 ce = make_float2(fmaf(co.x, ux, -co.y * uy), fmaf(co.x, uy, co.y * ux));  // m = 2
         static_for<1, L + 1>([&](auto mc) {
             constexpr int m = decltype(mc)::value;
             constexpr int b = Cheb<L>::cidx(m);
+            float2& c = (m & 1) ? co : ce;
             accc[b] = __fadd2_rn(accc[b], c);
             static_for<1, L - m + 1>([&](auto kc) {
                 constexpr int k = decltype(kc)::value;
                 accc[b + k] = __ffma2_rn(make_float2(T[k], T[k]), c, accc[b + k]);
             });
-            if constexpr (m < L) {
-                const float t = fmaf(c.x, ux, -c.y * uy);
-                c.y = fmaf(c.x, uy, c.y * ux);
+            if constexpr (m + 2 <= L) {
+                const float t = fmaf(c.x, u2x, -c.y * u2y);
+                c.y = fmaf(c.x, u2y, c.y * u2x);
                 c.x = t;
             }
         });

@@ -5,7 +5,7 @@ and positions, with the pair set and bins held fixed; the oracle's reference
 gradient is itself pinned to finite differences in test_oracle_grad.py.  The
 target zeta comes from the oracle on a second catalog, so no expected value
 comes from the CUDA path.  Tolerance: max |g - g_ref| / max |g_ref| per
-quantity.
+quantity, 1e-6 (FP32 pair arithmetic, FP64 accumulation of the gradients).
 """
 import numpy as np
 import pytest
@@ -21,7 +21,7 @@ from paper_1709_00086_gb300 import catalogs  # noqa: E402
 from gpu_util import maxrel, oracle_zeta, to_dev  # noqa: E402
 
 pytestmark = pytest.mark.gpu
-TOL_GRAD = 1e-5
+TOL_GRAD = 1e-6
 
 
 def _case(seed, n=2500, box=300.0, los_mode=0):
