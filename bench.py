@@ -230,6 +230,17 @@ def run_ours(args):
     sampler = ClockSampler(local) if rank == 0 else None
     z_tc, ms_tc, st_tc, clocks = timed(False, args.steps, args.warmup, sampler)
     z_32, ms_32, st_32, _ = timed(True, max(2, args.steps // 2), 1)
+    # isotropic Legendre 3PCF epilogue (g3pcf_isotropic) on the step's zeta
+    iso_ms = []
+    for k in range(4):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g3.isotropic(z_tc, B, L)
+        e1.record(stream)
+        e1.synchronize()
+        if k > 0:
+            iso_ms.append(e0.elapsed_time(e1))
     pairs = st_tc[-1]["pairs"]
     nprim = st_tc[-1]["primaries"]
     t_step = float(np.mean(ms_tc)) / 1e3
@@ -290,7 +301,8 @@ def run_ours(args):
         "zeta_tflops": zf / (con_tc / 1e3) / 1e12,
         "stage_ms": {"index": float(np.mean([s["index_ms"] for s in st_tc])), "pair": pair_ms,
                      "pair_scan": scan_ms, "pair_accum": accum_ms,
-                     "contract": con_tc, "reduce": float(np.mean([s["reduce_ms"] for s in st_tc]))},
+                     "contract": con_tc, "reduce": float(np.mean([s["reduce_ms"] for s in st_tc])),
+                     "isotropic_epilogue": float(np.mean(iso_ms))},
         "fp32_form": {"ms_per_step": float(np.mean(ms_32)), "value": pairs / (np.mean(ms_32) / 1e3),
                       "contract_ms": con_32, "zeta_tflops": zf / (con_32 / 1e3) / 1e12,
                       "max_rel_diff_vs_tc": diff},

@@ -205,6 +205,22 @@ int g3pcf_stats(g3pcf_plan_t plan, double* vals, int nvals);
 int g3pcf_zeta_from_alm_noalloc(int nbins, int lmax, const float* alm, int64_t ld,
                                 const float* w, int64_t np, double* zeta, void* stream);
 
+/* Isotropic (Legendre) 3PCF from zeta.  The paper's Sec. 2.2 expands the
+ * isotropic 3PCF in Legendre polynomials of rhat_1 . rhat_2 with radial
+ * coefficients zeta_l(r1, r2); by the addition theorem these are the m-sums of
+ * the anisotropic coefficients of Sec. 3.1.  For every catalog c, l <= lmax and
+ * bin pair (b1, b2):
+ *     out[c][l][b1][b2] = Re zeta^0_ll(b1,b2) + 2 sum_{m=1}^{l} Re zeta^m_ll(b1,b2)
+ *                       = (2l+1)/(4 pi) sum_i w_i sum_{j in b1, k in b2} w_j w_k P_l(rhat_ij . rhat_ik)
+ * (j = k terms included, the m < 0 blocks folded in through zeta^{-m} = conj(zeta^m)).
+ *   zeta: device, ncat x g3pcf_zeta_size(nbins, lmax) complex FP64 (interleaved), as
+ *         written by g3pcf_compute* (caller-owned, read only).
+ *   out:  device, ncat x (lmax + 1) x nbins x nbins FP64, row-major (caller-owned).
+ *   stream: cudaStream_t or NULL.  Asynchronous; allocates nothing.
+ * Errors: G3PCF_ERR_ARG for nbins / lmax / ncat out of range or null pointers;
+ * G3PCF_ERR_CUDA if the launch fails. */
+int g3pcf_isotropic(int nbins, int lmax, int ncat, const double* zeta, double* out, void* stream);
+
 /* Diagnostic: measured FP32 FMA throughput of the current device (TFLOP/s,
  * one FMA = 2 flop), best of 5 timed launches of an FMA-chain kernel that fills
  * every SM.  The denominator of the pair stage's roofline.  stream may be NULL.

@@ -61,6 +61,8 @@ def lib():
         L.g3pcf_destroy.argtypes = [P]
         L.g3pcf_autotune.argtypes = [P, P, P, I64, I, P]
         L.g3pcf_autotune.restype = I
+        L.g3pcf_isotropic.argtypes = [I, I, I, P, P, P]
+        L.g3pcf_isotropic.restype = I
         L.g3pcf_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), P]
         L.g3pcf_fp32_peak.restype = I
         L.g3pcf_set_option.argtypes = [P, I, I64]
@@ -85,6 +87,22 @@ def fp32_peak_tflops(stream=None) -> float:
     v = ctypes.c_double(0.0)
     _check(lib().g3pcf_fp32_peak(ctypes.byref(v), stream))
     return v.value
+
+
+def isotropic(z, nbins: int, lmax: int):
+    """Isotropic Legendre 3PCF zeta_l(b1, b2) from zeta (g3pcf_isotropic).
+
+    z: CUDA complex128 tensor (zsize,) or (ncat, zsize) as returned by Plan.compute /
+    compute_batch (or its float64 (..., 2) real view).  Returns (lmax+1, nbins, nbins) or
+    (ncat, lmax+1, nbins, nbins) float64."""
+    import torch
+    zz = (torch.view_as_real(z) if z.is_complex() else z).contiguous()
+    single = zz.dim() == 2
+    ncat = 1 if single else zz.shape[0]
+    out = torch.empty((ncat, lmax + 1, nbins, nbins), dtype=torch.float64, device=zz.device)
+    stream = torch.cuda.current_stream(zz.device).cuda_stream
+    _check(lib().g3pcf_isotropic(nbins, lmax, ncat, _ptr(zz), _ptr(out), stream))
+    return out[0] if single else out
 
 
 def zeta_size(nbins: int, lmax: int) -> int:

@@ -140,6 +140,21 @@ def large_radial(n: int = 50_000_000, seed: int = 7, box: float = 3000.0) -> Cat
                    name="radial-%d-L%g" % (n, box))
 
 
+def data_minus_randoms(data: Catalog, nrand_factor: int = 2, seed: int = 0) -> Catalog:
+    """A D - R catalog (the random-catalog correction of Sec. 6): the data points
+    with their weights followed by nrand_factor x n uniform randoms in the same
+    box with the equal negative weight -sum(w_D) / n_R, so the total weight is ~0.
+    The randoms take the data's position dtype; the parameters are the data's."""
+    rng = np.random.default_rng(seed)
+    n_r = nrand_factor * data.n
+    rpos = uniform_positions(rng, n_r, data.box, data.pos.dtype.type)
+    alpha = float(np.sum(data.w, dtype=np.float64)) / max(n_r, 1)
+    rw = np.full(n_r, -alpha, dtype=np.float32)
+    return Catalog(np.concatenate([data.pos, rpos]), np.concatenate([data.w, rw]), data.box,
+                   data.nbins, data.rmin, data.rmax, data.lmax, data.los_mode,
+                   name="%s-minus-%dR" % (data.name, nrand_factor))
+
+
 def small_case(kind: str, n: int, seed: int, box: float, nbins: int, rmin: float, rmax: float,
                lmax: int, los_mode: int = 0, dtype=np.float32, weight_kind="uniform_0.5_1.5"):
     """A small catalog with an explicit recipe, for parity tests."""

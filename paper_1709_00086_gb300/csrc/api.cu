@@ -1308,6 +1308,18 @@ int g3pcf_stats(g3pcf_plan_t P, double* vals, int nvals) {
     return G3PCF_OK;
 }
 
+int g3pcf_isotropic(int nbins, int lmax, int ncat, const double* zeta, double* out, void* stream) {
+    g_err.clear();
+    if (nbins < 1 || nbins > G3PCF_MAX_NBINS || lmax < 0 || lmax > G3PCF_MAX_LMAX || ncat < 0)
+        return fail(G3PCF_ERR_ARG, "isotropic: nbins in [1, %d], lmax in [0, %d], ncat >= 0", G3PCF_MAX_NBINS,
+                    G3PCF_MAX_LMAX);
+    if (ncat == 0) return G3PCF_OK;
+    if (!zeta || !out) return fail(G3PCF_ERR_ARG, "isotropic: null pointer");
+    if (launch_isotropic(zeta, nbins, lmax, ncat, out, static_cast<cudaStream_t>(stream)) != 0)
+        return fail(G3PCF_ERR_CUDA, "isotropic launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return G3PCF_OK;
+}
+
 int g3pcf_destroy(g3pcf_plan_t P) {
     g_err.clear();
     if (!P) return G3PCF_OK;

@@ -138,6 +138,28 @@ __global__ void k_reduce(const double* partials, int part_stride, const int* seg
     z[1] = im;
 }
 
+// Isotropic 3PCF from zeta: out[c][l][b1][b2] = Re zeta^0_ll(b1,b2)
+// + 2 sum_{m=1}^{l} Re zeta^m_ll(b1,b2) (the m < 0 blocks folded in by
+// zeta^{-m} = conj(zeta^m) for real weights).
+__global__ void k_isotropic(const double* zeta, BlockInfo bi, int nbins, int lmax, int64_t zsize,
+                            int ncat, double* out) {
+    const int64_t per_cat = (int64_t)(lmax + 1) * nbins * nbins;
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= per_cat * ncat) return;
+    const int cat = (int)(e / per_cat);
+    const int64_t r = e - cat * per_cat;
+    const int l = (int)(r / ((int64_t)nbins * nbins));
+    const int b1 = (int)((r / nbins) % nbins), b2 = (int)(r % nbins);
+    const double* z = zeta + 2 * (int64_t)cat * zsize;
+    double acc = 0.0;
+    for (int m = 0; m <= l; ++m) {
+        const int K = nbins * (lmax + 1 - m);
+        const int64_t idx = bi.zoff[m] + (int64_t)((l - m) * nbins + b1) * K + (l - m) * nbins + b2;
+        acc += (m == 0 ? 1.0 : 2.0) * z[2 * idx];
+    }
+    out[e] = acc;
+}
+
 }  // namespace
 
 int contract_tile_dim_fp32() { return kT; }
@@ -198,6 +220,20 @@ int launch_reduce(const double* partials, int part_stride, const int* seg_first,
     dim3 grid((unsigned)((zsize + 255) / 256), ncat);
     k_reduce<<<grid, 256, 0, st>>>(partials, part_stride, seg_first, ncat, tiles, bi, nbins, lmax,
                                    T, colmajor, zsize, zeta);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_isotropic(const double* zeta, int nbins, int lmax, int ncat, double* out, cudaStream_t st) {
+    BlockInfo bi{};
+    int64_t zo = 0;
+    for (int m = 0; m <= lmax; ++m) {
+        const int64_t K = (int64_t)nbins * (lmax + 1 - m);
+        bi.zoff[m] = (int)zo;
+        zo += K * K;
+    }
+    const int64_t total = (int64_t)(lmax + 1) * nbins * nbins * ncat;
+    if (total == 0) return 0;
+    k_isotropic<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(zeta, bi, nbins, lmax, zo, ncat, out);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

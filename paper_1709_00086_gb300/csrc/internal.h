@@ -197,6 +197,7 @@ int launch_reduce(const double* partials, int part_stride, const int* seg_first,
                   int nbins, int lmax, const Tile* tiles, int T, double* zeta, cudaStream_t st,
                   int colmajor = 0);
 int pair_nrp(int lmax);
+int launch_isotropic(const double* zeta, int nbins, int lmax, int ncat, double* out, cudaStream_t st);
 // contract_tc.cu: split-BF16 tcgen05 contraction
 int contract_tile_dim_tc();
 int contract_tc_kblock();
