@@ -114,6 +114,13 @@ struct g3pcf_plan_s {
     int* h_need = nullptr;
     int* h_base = nullptr;
     size_t h_list_cap = 0;
+    // graph capture of the list path: per A-chunk {total chunks, largest need} of
+    // the uncaptured warm-up run, consumed in order by the capture run
+    std::vector<std::pair<int64_t, int64_t>> gl_warm;
+    size_t gl_idx = 0;
+    bool warm_for_graph = false;
+    int gl_events = 0;  // events the capture run will record
+    DevBuf l_gbase, l_scantmp, l_passq;
     // events around every k_scan / k_accum launch of the last forward (4 per pass)
     std::vector<cudaEvent_t> lev;
     int lev_used = 0;
@@ -425,6 +432,25 @@ int read_status(g3pcf_plan_t P) {
     return G3PCF_OK;
 }
 
+// Device-planned passes of a captured forward over a pool of C chunks, for a
+// warm-up run that needed `total` chunks with `most` for one primary: stride
+// between pass bases, slack for the primary that straddles a pass end, passes.
+void graph_plan_sizes(int64_t C, int64_t total, int64_t most, int nbins, int64_t& slack, int64_t& stride,
+                      int& npass) {
+    slack = std::min<int64_t>(C / 2, 2 * most + nbins + 64);
+    stride = C - slack;
+    npass = stride > 0 ? (int)((total + total / 4 + stride - 1) / stride) + 1 : 0;
+}
+
+int ensure_events(g3pcf_plan_t P, int n) {
+    while ((int)P->lev.size() < n) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        P->lev.push_back(e);
+    }
+    return 0;
+}
+
 // Forward pair stage through pair lists for the primaries [pa.q0, pa.nprim):
 // count candidates, bring the per-primary chunk bounds to the host, split the
 // range into passes whose lists fit the pool, then scan + accumulate each pass.
@@ -476,6 +502,55 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st) {
     la.qa = qa;
     la.qb = qb;
     la.ncand = reinterpret_cast<unsigned long long*>(pa.status + 24);  // zeroed with the status word
+    if (P->capturing) {
+        // no host round trip inside a graph: plan the passes on the device from
+        // the pool the warm-up run sized (sizes of that run, same A-chunk order)
+        if (P->gl_idx >= P->gl_warm.size())
+            return fail(G3PCF_ERR_STATE, "graph capture without a matching warm-up forward");
+        const std::pair<int64_t, int64_t> wm = P->gl_warm[P->gl_idx++];
+        const int64_t C = (int64_t)(P->l_pool.bytes / 128);
+        int64_t slack = 0, stride = 0;
+        int npass = 0;
+        graph_plan_sizes(C, wm.first, wm.second, P->nbins, slack, stride, npass);
+        if (wm.first > ((int64_t)1 << 30) || stride < 1 || (int64_t)P->l_tag.bytes / 4 < C ||
+            (int64_t)P->l_ord.bytes / 4 < C || P->l_gbase.bytes < 4 * (size_t)nq ||
+            P->l_passq.bytes < 4 * (size_t)(npass + 1) || P->l_scantmp.bytes < 4 * scan_tmp_ints(nq) ||
+            (int)P->lev.size() < P->lev_used + 4 * npass) {
+            ++P->launches;  // lists too large for a device-planned graph: the fused kernel
+            if (launch_pair(P->lmax, pa, P->nsm, st) != 0)
+                return fail(G3PCF_ERR_CUDA, "pair kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+            return G3PCF_OK;
+        }
+        la.chunks = P->l_pool.as<int>();
+        la.tag = P->l_tag.as<int>();
+        la.ord = P->l_ord.as<int>();
+        ++P->launches;
+        if (launch_count(la, P->nsm, st) != 0)
+            return fail(G3PCF_ERR_CUDA, "pair count launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        P->launches += 5;
+        if (scan_exclusive(la.need + qa, P->l_gbase.as<int>(), nq, P->l_scantmp.as<int>(), st) != 0 ||
+            launch_plan(la.need, P->l_gbase.as<int>(), qa, qb, (int)stride, (int)slack, npass,
+                        P->l_base.as<int>(), P->l_passq.as<int>(), pa.status, st) != 0)
+            return fail(G3PCF_ERR_CUDA, "pair-list plan launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        for (int k = 0; k < npass; ++k) {
+            la.qrange = P->l_passq.as<int>() + k;
+            cudaEvent_t* ev = P->lev.data() + P->lev_used;
+            P->lev_used += 4;
+            CK(cudaMemsetAsync(la.queue, 0, sizeof(int), st));
+            P->launches += 2;
+            CK(cudaEventRecord(ev[0], st));
+            if (launch_scan(la, P->nsm, st) != 0)
+                return fail(G3PCF_ERR_CUDA, "pair scan launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+            CK(cudaEventRecord(ev[1], st));
+            CK(cudaMemsetAsync(la.queue, 0, sizeof(int), st));
+            CK(cudaEventRecord(ev[2], st));
+            if (launch_accum(P->lmax, la, P->nsm, st) != 0)
+                return fail(G3PCF_ERR_CUDA, "pair accumulate launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+            CK(cudaEventRecord(ev[3], st));
+        }
+        P->stats[10] += (double)npass;
+        return G3PCF_OK;
+    }
     ++P->launches;
     if (launch_count(la, P->nsm, st) != 0)
         return fail(G3PCF_ERR_CUDA, "pair count launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -498,7 +573,10 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st) {
     }
     int64_t cap = (int64_t)(budget / 136.0);
     if (cap > ((int64_t)1 << 30)) cap = (int64_t)1 << 30;
-    if (cap > total) cap = total;
+    P->gl_warm.emplace_back(total, most);
+    // a warm-up for a graph capture keeps headroom for the device-planned passes
+    const int64_t want = P->warm_for_graph ? total + total / 4 + 2 * most + P->nbins + 64 : total;
+    if (cap > want) cap = want;
     if (cap < most)
         return fail(G3PCF_ERR_ALLOC, "pair lists of one primary (%lld chunks) exceed the list budget (%lld)",
                     (long long)most, (long long)cap);
@@ -509,6 +587,17 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st) {
     la.chunks = P->l_pool.as<int>();
     la.tag = P->l_tag.as<int>();
     la.ord = P->l_ord.as<int>();
+    if (P->warm_for_graph && cap > 0) {  // what the capture run will need (no allocation while capturing)
+        int64_t slack = 0, stride = 0;
+        int npass = 0;
+        graph_plan_sizes(cap, total, most, P->nbins, slack, stride, npass);
+        if (ensure(P->l_gbase, 4 * (size_t)nq, "pair-list plan") ||
+            ensure(P->l_scantmp, 4 * (scan_tmp_ints(nq) + 16), "pair-list plan") ||
+            ensure(P->l_passq, 4 * (size_t)(npass + 1), "pair-list plan"))
+            return G3PCF_ERR_ALLOC;
+        P->gl_events += 4 * npass;
+        if (int r = ensure_events(P, P->gl_events)) return r;
+    }
     std::vector<int> cuts{qa};
     int64_t acc = 0;
     for (int64_t k = 0; k < nq; ++k) {
@@ -525,11 +614,7 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st) {
         la.qa = cuts[k];
         la.qb = cuts[k + 1];
         if (la.qb <= la.qa) continue;
-        while ((int)P->lev.size() < P->lev_used + 4) {
-            cudaEvent_t e;
-            CK(cudaEventCreate(&e));
-            P->lev.push_back(e);
-        }
+        if (int r = ensure_events(P, P->lev_used + 4)) return r;
         cudaEvent_t* ev = P->lev.data() + P->lev_used;
         P->lev_used += 4;
         CK(cudaMemsetAsync(la.queue, 0, sizeof(int), st));
@@ -561,6 +646,12 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
     P->launches = 0;
     P->stats[9] = P->stats[10] = 0.0;
     P->lev_used = 0;
+    if (P->capturing) {
+        P->gl_idx = 0;
+    } else {
+        P->gl_warm.clear();
+        P->gl_events = 0;
+    }
     P->stage_off = 0;
     CK(cudaEventRecord(P->ev[0], st));
     // zero outputs and counters
@@ -784,7 +875,7 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
                 pa.bins = P->bins;
                 pa.bintab = P->d_bintab.as<unsigned char>();
                 pa.bin_tscale = P->bin_tscale;
-                const bool use_list = P->opt_pair == 2 || (P->opt_pair == 0 && !P->capturing);
+                const bool use_list = P->opt_pair != 1;
                 if (use_list) {
                     if (int r = run_pair_lists(P, pa, st)) return r;
                 } else {
@@ -885,7 +976,10 @@ int forward_entry(g3pcf_plan_t P, CallSpec& c) {
         }
         CallSpec warm = c;
         warm.flags &= ~(G3PCF_F_GRAPH | G3PCF_F_NO_SYNC);
-        if (int r = run_forward(P, warm)) return r;
+        P->warm_for_graph = true;
+        const int rw = run_forward(P, warm);
+        P->warm_for_graph = false;
+        if (rw) return rw;
         CallSpec cap = c;
         cap.flags = (c.flags & ~G3PCF_F_GRAPH) | G3PCF_F_NO_SYNC;
         P->stream = P->gstream;
@@ -917,6 +1011,16 @@ int forward_entry(g3pcf_plan_t P, CallSpec& c) {
     CK(cudaStreamWaitEvent(user, P->gev[1], 0));
     if (c.flags & G3PCF_F_NO_SYNC) return G3PCF_OK;
     CK(cudaStreamSynchronize(user));
+    if (P->h_status[0] & kStatusOverflow) {
+        // the data outgrew the lists planned at capture: drop the graph (the next
+        // graph call captures again) and run this call uncaptured
+        cudaGraphExecDestroy(P->gexec);
+        P->gexec = nullptr;
+        P->gkey.clear();
+        CallSpec plain = c;
+        plain.flags &= ~G3PCF_F_GRAPH;
+        return run_forward(P, plain);
+    }
     return read_status(P);
 }
 
@@ -1266,6 +1370,11 @@ int g3pcf_status(g3pcf_plan_t P) {
     if (int r = check_plan(P)) return r;
     if (!P->h_status) return G3PCF_OK;
     CK(cudaStreamSynchronize(P->stream));
+    if ((P->h_status[0] & kStatusOverflow) && P->gexec) {  // see forward_entry
+        cudaGraphExecDestroy(P->gexec);
+        P->gexec = nullptr;
+        P->gkey.clear();
+    }
     return read_status(P);
 }
 
@@ -1329,7 +1438,8 @@ int g3pcf_destroy(g3pcf_plan_t P) {
                       &P->small, &P->counts, &P->A, &P->partials, &P->d_tiles, &P->d_segs,
                       &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_colconv, &P->d_colcoef, &P->d_bintab_s, &P->d_catoff, &P->d_ranges,
                       &P->d_tiles_tc, &P->ops, &P->d_cats, &P->d_mreal, &P->d_V, &P->d_bintab,
-                      &P->wrow, &P->l_need, &P->l_base, &P->l_nch, &P->l_pool, &P->l_tag, &P->l_ord};
+                      &P->wrow, &P->l_need, &P->l_base, &P->l_nch, &P->l_pool, &P->l_tag, &P->l_ord,
+                      &P->l_gbase, &P->l_scantmp, &P->l_passq};
     for (DevBuf* b : bufs) b->release();
     if (P->h_need) cudaFreeHost(P->h_need);
     if (P->h_base) cudaFreeHost(P->h_base);

@@ -170,6 +170,7 @@ struct ListArgs {
     unsigned long long* ncand;  // candidates visited (k_count adds)
     const int* base;         // [q] first chunk of q, relative to the pool arrays
     int* nchunks;            // [q]
+    const int* qrange;       // if set: qa = qrange[0], qb = qrange[1] (device-planned pass)
     int* chunks;             // pool: 32 ints per chunk
     int* tag;                // pool: (rank among its bin's chunks) << 5 | bin, per chunk
     int* ord;                // pool: the primary's chunks listed by bin (stable), chunk | bin << 26
@@ -177,6 +178,12 @@ struct ListArgs {
     Bins bins;
 };
 int launch_count(const ListArgs& a, int nsm, cudaStream_t st);
+// Device-side pass plan (graph capture): gbase = exclusive prefix of need over
+// [qa, qb); primary q goes to pass p = gbase / stride at base gbase - p * stride
+// (base -1 and the overflow bit when p >= npass or need > slack); passq[p] =
+// first primary of pass p (passq[npass] = qb).
+int launch_plan(const int* need, const int* gbase, int qa, int qb, int stride, int slack, int npass,
+                int* base, int* passq, int* status, cudaStream_t st);
 int launch_scan(const ListArgs& a, int nsm, cudaStream_t st);
 int launch_accum(int lmax, const ListArgs& a, int nsm, cudaStream_t st);
 

@@ -119,11 +119,16 @@ __global__ void __launch_bounds__(kLThreads, 6) k_scan(ListArgs a) {
     unsigned long long my_total = 0;
     long long cur_cat = -1;
 
+    const int qa = a.qrange ? a.qrange[0] : a.qa, qb = a.qrange ? a.qrange[1] : a.qb;
     for (;;) {
         int q = 0;
-        if (lane == 0) q = a.qa + atomicAdd(a.queue, 1);
+        if (lane == 0) q = qa + atomicAdd(a.queue, 1);
         q = __shfl_sync(kFull, q, 0);
-        if (q >= a.qb) break;
+        if (q >= qb) break;
+        if (a.base[q] < 0) {  // no room in the planned passes (flagged by the planner)
+            if (lane == 0) a.nchunks[q] = 0;
+            continue;
+        }
         const int p = a.plist ? a.plist[q] : q;
         const long long cat = (long long)(a.key[p] / (unsigned long long)g.cells_per_cat);
         if (cat != cur_cat) {
@@ -326,6 +331,24 @@ __global__ void __launch_bounds__(kLThreads, 6) k_scan(ListArgs a) {
     if (cur_cat >= 0 && lane < B && my_total) atomicAdd(&a.counts[cur_cat * B + lane], my_total);
 }
 
+__global__ void k_plan_init(int* passq, int npass, int qb) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p <= npass; p += gridDim.x * blockDim.x) passq[p] = qb;
+}
+
+__global__ void k_plan(const int* need, const int* gbase, int qa, int qb, int stride, int slack, int npass,
+                       int* base, int* passq, int* status) {
+    for (int q = qa + blockIdx.x * blockDim.x + threadIdx.x; q < qb; q += gridDim.x * blockDim.x) {
+        const int gb = gbase[q - qa];
+        const int pq = gb / stride;
+        const bool ok = pq < npass && need[q] <= slack;
+        base[q] = ok ? gb - pq * stride : -1;
+        if (!ok) atomicOr(status, kStatusOverflow);
+        // first primary of every pass that starts here
+        const int pprev = q == qa ? -1 : gbase[q - 1 - qa] / stride;
+        for (int pp = pprev + 1; pp <= pq && pp < npass; ++pp) passq[pp] = q;
+    }
+}
+
 // Asynchronous global -> shared copies (one per lane) and their groups.
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -406,11 +429,12 @@ __global__ void __launch_bounds__(kLThreads, 3) k_accum(ListArgs a) {
     float* res = reinterpret_cast<float*>(base + 27 * 16 + 64 + kPtRing * 32 * 16 + kEntRing * 32 * 4);
     const Grid& g = a.g;
     const float Lb = g.box;
+    const int qa = a.qrange ? a.qrange[0] : a.qa, qb = a.qrange ? a.qrange[1] : a.qb;
     for (;;) {
         int q = 0;
-        if (lane == 0) q = a.qa + atomicAdd(a.queue, 1);
+        if (lane == 0) q = qa + atomicAdd(a.queue, 1);
         q = __shfl_sync(kFull, q, 0);
-        if (q >= a.qb) break;
+        if (q >= qb) break;
         const int p = a.plist ? a.plist[q] : q;
         const float4 P0 = a.pts[p];
         if (lane < 27) {
@@ -427,7 +451,7 @@ __global__ void __launch_bounds__(kLThreads, 3) k_accum(ListArgs a) {
             Rs[lane] = g.radial ? los_rotation_entry(lane, x0, x1, x2, g.boxd)
                                 : ((lane % 4 == 0) ? 1.f : 0.f);
         }
-        const int cb = a.base[q];
+        const int cb = a.base[q] < 0 ? 0 : a.base[q];
         const int nch = a.nchunks[q];
         const int* chunks = a.chunks + (int64_t)cb * kChunk;
         const int* ordp = a.ord + cb;
@@ -529,7 +553,7 @@ int launch_accum_t(const ListArgs& a, int nsm, cudaStream_t st) {
         return -1;
     int blocks = per_sm * nsm;
     const int need = (a.qb - a.qa + kLWarps - 1) / kLWarps;
-    if (blocks > need) blocks = need > 0 ? need : 1;
+    if (!a.qrange && blocks > need) blocks = need > 0 ? need : 1;
     k_accum<L><<<blocks, kLThreads, smem, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -544,7 +568,7 @@ int launch_scan_k(const ListArgs& a, int nsm, cudaStream_t st) {
         return -1;
     int blocks = per_sm * nsm;
     const int need = (a.qb - a.qa + kLWarps - 1) / kLWarps;
-    if (blocks > need) blocks = need;
+    if (!a.qrange && blocks > need) blocks = need;
     k_scan<<<blocks, kLThreads, smem, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -561,12 +585,23 @@ int launch_count(const ListArgs& a, int nsm, cudaStream_t st) {
 }
 
 int launch_scan(const ListArgs& a, int nsm, cudaStream_t st) {
-    if (a.qb <= a.qa) return 0;
+    if (!a.qrange && a.qb <= a.qa) return 0;
     return launch_scan_k(a, nsm, st);
 }
 
+int launch_plan(const int* need, const int* gbase, int qa, int qb, int stride, int slack, int npass,
+                int* base, int* passq, int* status, cudaStream_t st) {
+    k_plan_init<<<1, 256, 0, st>>>(passq, npass, qb);
+    if (qb > qa) {
+        int blocks = (qb - qa + 255) / 256;
+        if (blocks > 4096) blocks = 4096;
+        k_plan<<<blocks, 256, 0, st>>>(need, gbase, qa, qb, stride, slack, npass, base, passq, status);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int launch_accum(int lmax, const ListArgs& a, int nsm, cudaStream_t st) {
-    if (a.qb <= a.qa) return 0;
+    if (!a.qrange && a.qb <= a.qa) return 0;
     switch (lmax) {
         case 0: return launch_accum_t<0>(a, nsm, st);
         case 1: return launch_accum_t<1>(a, nsm, st);

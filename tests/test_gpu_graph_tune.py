@@ -1,10 +1,11 @@
 """CUDA-graph replay of the batched forward and the autotuner.
 
-A captured graph runs the fused pair kernel, so it must reproduce a plain call
-made with the fused kernel bit for bit (same kernels and inputs; every
-reduction has a fixed order) and the default pair-list call within tolerance;
-a replay after the input buffers were overwritten in place must compute the
-new data.  The autotuner must return settings inside their ranges and leave
+A captured graph runs the pair lists with passes planned on the device, so it
+must reproduce a plain call bit for bit (the same per-primary lists and kernels;
+every reduction has a fixed order), and the fused pair kernel within tolerance;
+a replay after the input buffers were overwritten in place must compute the new
+data, and data whose lists outgrow the captured pool fall back to an uncaptured
+call.  The autotuner must return settings inside their ranges and leave
 the plan producing the oracle's counts and zeta.
 """
 import numpy as np
@@ -36,12 +37,12 @@ def test_graph_replay_matches_plain_and_follows_new_data(tc):
     plan = g3.Plan(**cats[0].params())
     dpos = torch.from_numpy(pos).cuda()
     dw = torch.from_numpy(w).cuda()
-    zl, cl = plan.compute_batch(dpos, dw, offs, fp32_contraction=not tc)  # pair lists
     plan.set_option(g3.OPT_PAIR_KERNELS, 1)
-    z0, c0 = plan.compute_batch(dpos, dw, offs, fp32_contraction=not tc)  # fused kernel
+    zf, cf = plan.compute_batch(dpos, dw, offs, fp32_contraction=not tc)  # fused kernel
     plan.set_option(g3.OPT_PAIR_KERNELS, 0)
-    assert torch.equal(cl, c0)
-    assert maxrel(zl.cpu().numpy(), z0.cpu().numpy()) < (1e-4 if tc else 1e-5)
+    z0, c0 = plan.compute_batch(dpos, dw, offs, fp32_contraction=not tc)  # pair lists
+    assert torch.equal(cf, c0)
+    assert maxrel(zf.cpu().numpy(), z0.cpu().numpy()) < (1e-4 if tc else 1e-5)
     zbuf = torch.empty((len(cats), plan.zsize, 2), dtype=torch.float64, device="cuda")
     cbuf = torch.empty((len(cats), plan.nbins), dtype=torch.int64, device="cuda")
     for _ in range(3):  # capture, then two replays
@@ -88,3 +89,27 @@ def test_autotune_choices_and_result():
     zo, co = oracle_zeta(cat, n_primary=300)
     np.testing.assert_array_equal(c.cpu().numpy(), co)
     assert maxrel(z.cpu().numpy(), zo) < 1e-4
+
+
+def test_graph_replay_with_denser_data_falls_back():
+    # capture on a catalog of scattered points, then overwrite the buffers with
+    # a tightly clustered catalog of the same size: its lists outgrow the pool
+    # planned at capture; the call must still return the right zeta
+    n = 4000
+    sparse = catalogs.small_case("uniform", n, seed=81, box=400.0, nbins=6, rmin=0.0, rmax=60.0, lmax=4)
+    dense = catalogs.small_case("clustered", n, seed=82, box=400.0, nbins=6, rmin=0.0, rmax=60.0, lmax=4)
+    dense.pos[:] = (dense.pos * 0.25).astype(dense.pos.dtype)  # everything in one corner
+    plan = g3.Plan(**sparse.params())
+    dpos, dw = to_dev(sparse, torch)
+    zb = torch.empty((plan.zsize, 2), dtype=torch.float64, device="cuda")
+    cb = torch.empty(plan.nbins, dtype=torch.int64, device="cuda")
+    plan.compute(dpos, dw, graph=True, out=zb, counts_out=cb, fp32_contraction=True)
+    dpos.copy_(torch.from_numpy(dense.pos))
+    dw.copy_(torch.from_numpy(dense.w))
+    z, c = plan.compute(dpos, dw, graph=True, out=zb, counts_out=cb, fp32_contraction=True)
+    zo, co = oracle_zeta(dense)
+    np.testing.assert_array_equal(c.cpu().numpy(), co)
+    assert maxrel(z.cpu().numpy(), zo) < 1e-5
+    # and the next graph call captures again and agrees
+    z2, c2 = plan.compute(dpos, dw, graph=True, out=zb, counts_out=cb, fp32_contraction=True)
+    assert torch.equal(c2, c) and maxrel(z2.cpu().numpy(), zo) < 1e-5
