@@ -277,6 +277,36 @@ def run_ours(args):
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_val = ws * pairs / (float(np.mean(e2e_ms)) / 1e3)
 
+    # the adjoint (differentiation workload: clustered N = 500,000, L = 800, Rmax = 120,
+    # 8 bins, lmax = 6): forward with multipoles kept, then g3pcf_backward
+    adj = None
+    if not args.no_adjoint:
+        from paper_1709_00086_gb300 import catalogs as cats
+        dcat = cats.differentiation()
+        dplan = g3.Plan(**dcat.params())
+        dpos = torch.from_numpy(dcat.pos).to(dev)
+        dwt = torch.from_numpy(dcat.w).to(dev)
+        rng = np.random.default_rng(5)
+        dz = torch.from_numpy(rng.normal(size=(dplan.zsize, 2))).to(dev)
+        fwd_ms, bwd_ms = [], []
+        for k in range(3):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            dplan.compute(dpos, dwt, keep_alm=True, with_counts=False, fp32_contraction=True)
+            e1.record(stream)
+            dplan.backward(dz)
+            e2.record(stream)
+            e2.synchronize()
+            if k > 0:
+                fwd_ms.append(e0.elapsed_time(e1))
+                bwd_ms.append(e1.elapsed_time(e2))
+        dpairs = dplan.stats()["pairs"]
+        adj = {"workload": "clustered N=500,000, periodic L=800, Rmax=120, 8 bins, lmax=6",
+               "pairs": dpairs, "forward_ms": float(np.mean(fwd_ms)),
+               "backward_ms": float(np.mean(bwd_ms)),
+               "backward_pairs_per_s": dpairs / (float(np.mean(bwd_ms)) / 1e3)}
+        del dplan, dpos, dwt
+
     if rank != 0:
         return
     pk = peaks()
@@ -319,6 +349,7 @@ def run_ours(args):
         "e2e": {"value": e2e_val, "unit": "pairs/s",
                 "h2d_bytes_per_step": int(hpos.numel() * 4 + hw.numel() * 4),
                 "d2h_bytes_per_step": int(hz.numel() * 8)},
+        "adjoint": adj,
         "clocks": clocks,
         "gpu_launches": int(st_tc[-1]["launches"]) * args.steps,
     }
@@ -343,6 +374,7 @@ def main():
     ap.add_argument("--cpu-primaries", type=int, default=300)
     ap.add_argument("--ref-primaries", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
