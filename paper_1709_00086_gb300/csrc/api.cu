@@ -83,6 +83,8 @@ struct g3pcf_plan_s {
     std::vector<float> colscale;
     std::vector<int4> colconv;     // Chebyshev-form columns (pair-list path)
     std::vector<float> colcoef;
+    std::vector<int4> slotconv;    // the transposed connection (pair-list adjoint)
+    std::vector<float> slotcoef;
     std::vector<Tile> tiles;      // FP32 contraction tiles (edge T)
     std::vector<Tile> tiles_tc;   // tensor-core contraction tiles (edge T_tc)
     int T = 0, T_tc = 0;
@@ -91,7 +93,7 @@ struct g3pcf_plan_s {
     DevBuf key_a, key_b, val_a, val_b, hist, hist_off, scan_tmp, pts, pts64, orig, cstart, plist;
     DevBuf small;       // status, queue
     DevBuf counts, A, partials, d_tiles, d_segs, d_segfirst, d_colmap, d_colscale, d_catoff;
-    DevBuf d_colconv, d_colcoef, d_bintab_s;
+    DevBuf d_colconv, d_colcoef, d_bintab_s, d_slotconv, d_slotcoef;
     DevBuf d_ranges, d_tiles_tc, ops, d_cats, d_mreal, d_V, d_bintab, wrow;
     int64_t opt_chunk = 0;   // G3PCF_OPT_CHUNK_ROWS
     // pinned staging for host -> device tables (capturable copies); offset
@@ -215,6 +217,11 @@ int upload_consts(g3pcf_plan_t P) {
         return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (constants)");
     CK(cudaMemcpy(P->d_colconv.p, P->colconv.data(), P->colconv.size() * sizeof(int4), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->d_colcoef.p, P->colcoef.data(), P->colcoef.size() * sizeof(float), cudaMemcpyHostToDevice));
+    if (P->d_slotconv.ensure(P->slotconv.size() * sizeof(int4)) ||
+        P->d_slotcoef.ensure(P->slotcoef.size() * sizeof(float)))
+        return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (constants)");
+    CK(cudaMemcpy(P->d_slotconv.p, P->slotconv.data(), P->slotconv.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->d_slotcoef.p, P->slotcoef.data(), P->slotcoef.size() * sizeof(float), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->d_tiles.p, P->tiles.data(), P->tiles.size() * sizeof(Tile),
                   cudaMemcpyHostToDevice));
     P->consts_uploaded = true;
@@ -394,6 +401,29 @@ void compute_columns(g3pcf_plan_t P) {
                 ++col;
             }
     }
+    // adjoint: per accumulator slot (m, k, part) the A columns (l = m + n, n = k..L-m,
+    // stride B from bin 0) and coefficients c^(m)_{n,k} K_lm of the transposed connection
+    const int NR = (L + 1) * (L + 1);
+    P->slotconv.assign(NR, int4{0, 0, 0, 0});
+    P->slotcoef.clear();
+    int colm = 0;
+    for (int m = 0; m <= L; ++m) {
+        const int K = B * (L + 1 - m);
+        for (int part = 0; part < (m == 0 ? 1 : 2); ++part)
+            for (int k = 0; k <= L - m; ++k) {
+                const int slot = (m == 0) ? k : acc_base(L, m) + 2 * k + part;
+                P->slotconv[slot] = int4{colm + part * K + k * B, B, L - m - k + 1, (int)P->slotcoef.size()};
+                for (int nn = k; nn <= L - m; ++nn) {
+                    const int l = m + nn;
+                    const double lnN = 0.5 * (std::log((2.0 * l + 1.0) / (4.0 * M_PI)) + lfact(l - m) - lfact(l + m));
+                    const double lnLead = lfact(2 * l) - l * std::log(2.0) - lfact(l) - lfact(l - m);
+                    double kl = std::exp(lnN + lnLead);
+                    if (m & 1) kl = -kl;
+                    P->slotcoef.push_back((float)(cheb_coeffs(m, nn)[k] * kl));
+                }
+            }
+        colm += (m == 0) ? K : 2 * K;
+    }
 }
 
 int64_t zsize_of(int nbins, int lmax) {
@@ -454,7 +484,7 @@ int ensure_events(g3pcf_plan_t P, int n) {
 // Forward pair stage through pair lists for the primaries [pa.q0, pa.nprim):
 // count candidates, bring the per-primary chunk bounds to the host, split the
 // range into passes whose lists fit the pool, then scan + accumulate each pass.
-int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st) {
+int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode = 0) {
     const int qa = pa.q0, qb = pa.nprim;
     const int64_t nq = (int64_t)qb - qa;
     if (nq <= 0) return G3PCF_OK;
@@ -496,6 +526,13 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st) {
     la.bin_tscale = pa.bin_tscale;
     la.g = pa.g;
     la.bins = pa.bins;
+    if (mode == 1) {
+        la.V = pa.V;
+        la.dw = pa.dw;
+        la.dpos = pa.dpos;
+        la.slotconv = P->d_slotconv.as<int4>();
+        la.slotcoef = P->d_slotcoef.as<float>();
+    }
     la.need = P->l_need.as<int>();
     la.base = P->l_base.as<int>();
     la.nchunks = P->l_nch.as<int>();
@@ -626,7 +663,7 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st) {
         CK(cudaMemsetAsync(la.queue, 0, sizeof(int), st));
         ++P->launches;
         CK(cudaEventRecord(ev[2], st));
-        if (launch_accum(P->lmax, la, P->nsm, st) != 0)
+        if ((mode == 1 ? launch_adj(P->lmax, la, P->nsm, st) : launch_accum(P->lmax, la, P->nsm, st)) != 0)
             return fail(G3PCF_ERR_CUDA, "pair accumulate launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         CK(cudaEventRecord(ev[3], st));
     }
@@ -1240,8 +1277,14 @@ int g3pcf_backward(g3pcf_plan_t P, const double* dzeta, double* dpos, double* dw
     pa.bins = P->bins;
     pa.bintab = P->d_bintab.as<unsigned char>();
     pa.bin_tscale = P->bin_tscale;
-    if (launch_pair(P->lmax, pa, P->nsm, st, 1) != 0)
+    if (P->opt_pair != 1) {
+        pa.q0 = 0;
+        pa.chunked = 0;
+        P->lev_used = 0;
+        if (int r = run_pair_lists(P, pa, st, 1)) return r;
+    } else if (launch_pair(P->lmax, pa, P->nsm, st, 1) != 0) {
         return fail(G3PCF_ERR_CUDA, "adjoint pair kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    }
     CK(cudaMemcpyAsync(P->h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return read_status(P);
@@ -1436,7 +1479,7 @@ int g3pcf_destroy(g3pcf_plan_t P) {
     DevBuf* bufs[] = {&P->key_a, &P->key_b, &P->val_a, &P->val_b, &P->hist, &P->hist_off,
                       &P->scan_tmp, &P->pts, &P->pts64, &P->orig, &P->cstart, &P->plist,
                       &P->small, &P->counts, &P->A, &P->partials, &P->d_tiles, &P->d_segs,
-                      &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_colconv, &P->d_colcoef, &P->d_bintab_s, &P->d_catoff, &P->d_ranges,
+                      &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_colconv, &P->d_colcoef, &P->d_bintab_s, &P->d_slotconv, &P->d_slotcoef, &P->d_catoff, &P->d_ranges,
                       &P->d_tiles_tc, &P->ops, &P->d_cats, &P->d_mreal, &P->d_V, &P->d_bintab,
                       &P->wrow, &P->l_need, &P->l_base, &P->l_nch, &P->l_pool, &P->l_tag, &P->l_ord,
                       &P->l_gbase, &P->l_scantmp, &P->l_passq};

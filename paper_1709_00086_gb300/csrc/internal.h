@@ -171,6 +171,13 @@ struct ListArgs {
     const int* base;         // [q] first chunk of q, relative to the pool arrays
     int* nchunks;            // [q]
     const int* qrange;       // if set: qa = qrange[0], qb = qrange[1] (device-planned pass)
+    // adjoint pass (k_adj): V rows (row = original index), slot tables of the
+    // transposed Chebyshev connection, outputs (FP64, original order)
+    const float* V;
+    const int4* slotconv;    // NR entries: {first A column (bin 0), column stride, terms, coefficient offset}
+    const float* slotcoef;
+    double* dw;
+    double* dpos;
     int* chunks;             // pool: 32 ints per chunk
     int* tag;                // pool: (rank among its bin's chunks) << 5 | bin, per chunk
     int* ord;                // pool: the primary's chunks listed by bin (stable), chunk | bin << 26
@@ -186,6 +193,7 @@ int launch_plan(const int* need, const int* gbase, int qa, int qb, int stride, i
                 int* base, int* passq, int* status, cudaStream_t st);
 int launch_scan(const ListArgs& a, int nsm, cudaStream_t st);
 int launch_accum(int lmax, const ListArgs& a, int nsm, cudaStream_t st);
+int launch_adj(int lmax, const ListArgs& a, int nsm, cudaStream_t st);
 
 // ---- contract.cu -----------------------------------------------------------
 struct Tile {          // one output tile of one m block of C_m = sum_i w_i v_i v_i^T

@@ -540,6 +540,205 @@ __global__ void __launch_bounds__(kLThreads, 3) k_accum(ListArgs a) {
     }
 }
 
+// Adjoint pair pass over the pair lists (the derivative of Sec. 3.1's a_lm
+// with the pair set and bins held fixed).  Per primary i and bin b the adjoint
+// multipoles H_lm = w_i K_lm V_i (V = M A, slot layout) are carried to the
+// Chebyshev form, G_{m,k} = sum_l c^(m)_{l-m,k} H_lm (the transpose of the
+// forward's connection), so that for a pair with unit separation (x, y, z)
+//     F = sum_{m,k} Re(conj(G_{m,k}) T_k(z) (x + iy)^m)
+// with dF/dz through T_k' = k U_{k-1} and dF/dx, dF/dy through (x + iy)^m.
+// Secondary j receives dL/dw_j += 2F and dL/dpos_j += g, primary i gets -g,
+// g = (2 w_j / r)(grad F - (grad F . d) d) (FP64 atomics; the primary's share
+// is summed per lane and reduced once).
+template <int L>
+__global__ void __launch_bounds__(kLThreads) k_adj(ListArgs a) {
+    constexpr int NR = Shape<L>::NR, NRP = Shape<L>::NRP;
+    extern __shared__ __align__(16) unsigned char la_raw[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int B = a.bins.nbins;
+    unsigned char* base = la_raw + (size_t)wid * accum_smem_per_warp(B, NRP);
+    float4* img = reinterpret_cast<float4*>(base);
+    float4* pring = reinterpret_cast<float4*>(base + 27 * 16 + 64);
+    unsigned* ering = reinterpret_cast<unsigned*>(base + 27 * 16 + 64 + kPtRing * 32 * 16);
+    float* G = reinterpret_cast<float*>(base + 27 * 16 + 64 + kPtRing * 32 * 16 + kEntRing * 32 * 4);
+    const Grid& g = a.g;
+    const float Lb = g.box;
+    const int qa = a.qrange ? a.qrange[0] : a.qa, qb = a.qrange ? a.qrange[1] : a.qb;
+    for (;;) {
+        int q = 0;
+        if (lane == 0) q = qa + atomicAdd(a.queue, 1);
+        q = __shfl_sync(kFull, q, 0);
+        if (q >= qb) break;
+        const int p = a.plist ? a.plist[q] : q;
+        const float4 P0 = a.pts[p];
+        if (lane < 27) {
+            const int sx = lane % 3 - 1, sy = (lane / 3) % 3 - 1, sz = lane / 9 - 1;
+            img[lane] = make_float4(P0.x - sx * Lb, P0.y - sy * Lb, P0.z - sz * Lb, 0.f);
+        }
+        const int row = a.orig[p];
+        const float* Vrow = a.V + (int64_t)row * a.RLP;
+        for (int idx = lane; idx < B * NR; idx += 32) {
+            const int b = idx / NR, sl = idx - b * NR;
+            const int4 cv = __ldg(a.slotconv + sl);
+            float v = 0.f;
+            for (int t = 0; t < cv.z; ++t) v = fmaf(__ldg(a.slotcoef + cv.w + t), __ldg(Vrow + cv.x + b + t * cv.y), v);
+            G[b * NRP + sl] = P0.w * v;
+        }
+        const int cb = a.base[q] < 0 ? 0 : a.base[q];
+        const int nch = a.nchunks[q];
+        const int* chunks = a.chunks + (int64_t)cb * kChunk;
+        const int* ordp = a.ord + cb;
+        __syncwarp();
+        double di0 = 0.0, di1 = 0.0, di2 = 0.0;  // -dL/dpos_i, this lane's share
+        if (nch > 0) {
+            auto ent_async = [&](int i, unsigned o) {
+                cp_async4(ering + (i & (kEntRing - 1)) * 32 + lane,
+                          chunks + (int64_t)(o & 0x3ffffffu) * kChunk + lane);
+            };
+            auto pt_async = [&](int i) {
+                const unsigned e = ering[(i & (kEntRing - 1)) * 32 + lane];
+                const bool v = e != kNoPair;
+                cp_async16(pring + (i & (kPtRing - 1)) * 32 + lane, a.pts + (v ? (e & kIdxMask) : 0u), v);
+            };
+            auto slot = [&](int i) -> unsigned { return i < nch ? (unsigned)__ldg(ordp + i) : 0u; };
+            unsigned o0 = slot(0), o1 = slot(1), o2 = slot(2), o3 = slot(3);
+            ent_async(0, o0);
+            if (nch > 1) ent_async(1, o1);
+            cp_async_commit();
+            cp_async_wait<0>();
+            pt_async(0);
+            if (nch > 2) ent_async(2, o2);
+            cp_async_commit();
+            if (nch > 1) pt_async(1);
+            if (nch > 3) ent_async(3, o3);
+            cp_async_commit();
+            unsigned s4 = slot(4), s5 = slot(5), s6 = slot(6);
+            unsigned sA = o0, sB = o1, sC = o2, sD = o3;
+            float pix = 0.f, piy = 0.f, piz = 0.f;
+            int curb = (int)(sA >> 26);
+            for (int i = 0; i < nch; ++i) {
+                cp_async_wait<1>();
+                if (i + 2 < nch) pt_async(i + 2);
+                if (i + 4 < nch) ent_async(i + 4, s4);
+                cp_async_commit();
+                const unsigned s7 = slot(i + 7);
+                const int bA = (int)(sA >> 26);
+                if (bA != curb) {
+                    di0 -= pix;
+                    di1 -= piy;
+                    di2 -= piz;
+                    pix = piy = piz = 0.f;
+                    curb = bA;
+                }
+                const unsigned e = ering[(i & (kEntRing - 1)) * 32 + lane];
+                if (e != kNoPair) {
+                    const float4 qv = pring[(i & (kPtRing - 1)) * 32 + lane];
+                    const float4 o = img[e >> kIdxBits];
+                    const int jj = __ldg(a.orig + (e & kIdxMask));
+                    const float dx = qv.x - o.x, dy = qv.y - o.y, dz = qv.z - o.z;
+                    const float rinv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                    const float z = dz * rinv, ux = dx * rinv, uy = dy * rinv;
+                    const float* Gb = G + bA * NRP;
+                    // T_k(z) and T_k'(z) = k U_{k-1}(z)
+                    float T[L + 1], D[L + 1];
+                    T[0] = 1.f;
+                    D[0] = 0.f;
+                    if constexpr (L >= 1) {
+                        T[1] = z;
+                        D[1] = 1.f;
+                        const float z2 = z + z;
+                        float u0 = 1.f, u1 = z2;  // U_0, U_1
+                        static_for<2, L + 1>([&](auto kc) {
+                            constexpr int k = decltype(kc)::value;
+                            T[k] = fmaf(z2, T[k - 1], -T[k - 2]);
+                            D[k] = (float)k * u1;  // k U_{k-1}
+                            const float u2 = fmaf(z2, u1, -u0);
+                            u0 = u1;
+                            u1 = u2;
+                        });
+                    }
+                    float F = 0.f, Fz = 0.f, Fx = 0.f, Fy = 0.f;
+                    static_for<0, L + 1>([&](auto kc) {
+                        constexpr int k = decltype(kc)::value;
+                        const float gk = Gb[k];
+                        F = fmaf(gk, T[k], F);
+                        Fz = fmaf(gk, D[k], Fz);
+                    });
+                    float pr = 1.f, pim = 0.f;  // (x + iy)^(m-1)
+                    static_for<1, L + 1>([&](auto mc) {
+                        constexpr int m = decltype(mc)::value;
+                        constexpr int b0 = acc_base(L, m);
+                        float2 gm = make_float2(0.f, 0.f), gz = make_float2(0.f, 0.f);
+                        static_for<0, L - m + 1>([&](auto kc) {
+                            constexpr int k = decltype(kc)::value;
+                            const float2 gg = *reinterpret_cast<const float2*>(Gb + b0 + 2 * k);
+                            gm = __ffma2_rn(make_float2(T[k], T[k]), gg, gm);
+                            gz = __ffma2_rn(make_float2(D[k], D[k]), gg, gz);
+                        });
+                        const float ur = fmaf(pr, ux, -pim * uy), ui = fmaf(pr, uy, pim * ux);  // (x+iy)^m
+                        F = fmaf(gm.x, ur, fmaf(gm.y, ui, F));
+                        Fz = fmaf(gz.x, ur, fmaf(gz.y, ui, Fz));
+                        Fx = fmaf((float)m, fmaf(gm.x, pr, gm.y * pim), Fx);
+                        Fy = fmaf((float)m, fmaf(gm.y, pr, -gm.x * pim), Fy);
+                        pr = ur;
+                        pim = ui;
+                    });
+                    const float gdr = fmaf(Fx, ux, fmaf(Fy, uy, Fz * z));
+                    const float sc = 2.f * qv.w * rinv;
+                    const float gx = sc * fmaf(-gdr, ux, Fx), gy = sc * fmaf(-gdr, uy, Fy),
+                                gz3 = sc * fmaf(-gdr, z, Fz);
+                    atomicAdd(a.dw + jj, (double)(2.f * F));
+                    atomicAdd(a.dpos + 3 * (int64_t)jj, (double)gx);
+                    atomicAdd(a.dpos + 3 * (int64_t)jj + 1, (double)gy);
+                    atomicAdd(a.dpos + 3 * (int64_t)jj + 2, (double)gz3);
+                    pix += gx;
+                    piy += gy;
+                    piz += gz3;
+                }
+                sA = sB;
+                sB = sC;
+                sC = sD;
+                sD = s4;
+                s4 = s5;
+                s5 = s6;
+                s6 = s7;
+            }
+            cp_async_wait<0>();
+            di0 -= pix;
+            di1 -= piy;
+            di2 -= piz;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            di0 += __shfl_xor_sync(kFull, di0, o);
+            di1 += __shfl_xor_sync(kFull, di1, o);
+            di2 += __shfl_xor_sync(kFull, di2, o);
+        }
+        if (lane == 0) {
+            atomicAdd(a.dpos + 3 * (int64_t)row, di0);
+            atomicAdd(a.dpos + 3 * (int64_t)row + 1, di1);
+            atomicAdd(a.dpos + 3 * (int64_t)row + 2, di2);
+        }
+        __syncwarp();
+    }
+}
+
+template <int L>
+int launch_adj_t(const ListArgs& a, int nsm, cudaStream_t st) {
+    const size_t smem = accum_smem_per_warp(a.bins.nbins, Shape<L>::NRP) * kLWarps;
+    if (cudaFuncSetAttribute(k_adj<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return -1;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj<L>, kLThreads, smem) != cudaSuccess ||
+        per_sm < 1)
+        return -1;
+    int blocks = per_sm * nsm;
+    const int need = (a.qb - a.qa + kLWarps - 1) / kLWarps;
+    if (!a.qrange && blocks > need) blocks = need > 0 ? need : 1;
+    k_adj<L><<<blocks, kLThreads, smem, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 template <int L>
 int launch_accum_t(const ListArgs& a, int nsm, cudaStream_t st) {
     const size_t smem = accum_smem_per_warp(a.bins.nbins, Shape<L>::NRP) * kLWarps;
@@ -598,6 +797,24 @@ int launch_plan(const int* need, const int* gbase, int qa, int qb, int stride, i
         k_plan<<<blocks, 256, 0, st>>>(need, gbase, qa, qb, stride, slack, npass, base, passq, status);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_adj(int lmax, const ListArgs& a, int nsm, cudaStream_t st) {
+    if (!a.qrange && a.qb <= a.qa) return 0;
+    switch (lmax) {
+        case 0: return launch_adj_t<0>(a, nsm, st);
+        case 1: return launch_adj_t<1>(a, nsm, st);
+        case 2: return launch_adj_t<2>(a, nsm, st);
+        case 3: return launch_adj_t<3>(a, nsm, st);
+        case 4: return launch_adj_t<4>(a, nsm, st);
+        case 5: return launch_adj_t<5>(a, nsm, st);
+        case 6: return launch_adj_t<6>(a, nsm, st);
+        case 7: return launch_adj_t<7>(a, nsm, st);
+        case 8: return launch_adj_t<8>(a, nsm, st);
+        case 9: return launch_adj_t<9>(a, nsm, st);
+        case 10: return launch_adj_t<10>(a, nsm, st);
+        default: return -1;
+    }
 }
 
 int launch_accum(int lmax, const ListArgs& a, int nsm, cudaStream_t st) {
