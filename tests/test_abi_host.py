@@ -95,3 +95,14 @@ def test_set_option_validation():
             p.set_option(opt, val)
         assert ei.value.name == "ERR_ARG"
     p.close()
+
+
+def test_isotropic_argument_errors_before_device_work():
+    lib = g3.lib()
+    dummy = ctypes.c_void_p(16)
+    assert lib.g3pcf_isotropic(0, 2, 1, dummy, dummy, None) == -1      # nbins < 1
+    assert lib.g3pcf_isotropic(33, 2, 1, dummy, dummy, None) == -1     # nbins > 32
+    assert lib.g3pcf_isotropic(4, 11, 1, dummy, dummy, None) == -1     # lmax > 10
+    assert lib.g3pcf_isotropic(4, 2, -1, dummy, dummy, None) == -1     # ncat < 0
+    assert lib.g3pcf_isotropic(4, 2, 1, None, dummy, None) == -1       # null zeta
+    assert lib.g3pcf_isotropic(4, 2, 0, None, None, None) == 0         # nothing to do
