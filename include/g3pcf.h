@@ -141,10 +141,12 @@ int g3pcf_compute_batch(g3pcf_plan_t plan, const float* pos, const float* w,
                         const int64_t* offsets, int ncat, double* zeta, int64_t* counts,
                         int flags);
 
-/* Adjoint of the last forward on this plan (LOS = z modes, single catalog).
- * dzeta: device, same layout as zeta, the gradient of a real loss with respect
- * to (Re zeta, Im zeta) interleaved.  dpos: device, n x 3 doubles; dw: device,
- * n doubles; both overwritten.  Pair set and bins are held fixed.  The pos and w
+/* Adjoint of the last forward on this plan (LOS = z modes; g3pcf_compute* or
+ * g3pcf_compute_batch).  dzeta: device, same layout as the forward's zeta (for a
+ * batch, ncat consecutive blocks, catalog c's gradient in block c), the gradient
+ * of a real loss with respect to (Re zeta, Im zeta) interleaved.  dpos: device,
+ * n x 3 doubles; dw: device, n doubles (all points of the forward, its order);
+ * both overwritten.  Pair set and bins are held fixed.  The pos and w
  * buffers of the forward must still hold the same values.  Not in the paper:
  * dL/dw_i and dL/dpos_i of zeta through Y_lm and the weights. */
 int g3pcf_backward(g3pcf_plan_t plan, const double* dzeta, double* dpos, double* dw);

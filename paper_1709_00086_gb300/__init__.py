@@ -208,7 +208,7 @@ class Plan:
                  (F_GRAPH if graph else 0))
         self._stream()
         self._token += 1
-        self._last_n = 0
+        self._last_n = int(pos.shape[0])
         _check(lib().g3pcf_compute_batch(self._h, _ptr(pos), _ptr(w),
                                          offs.ctypes.data_as(ctypes.c_void_p), ncat, _ptr(zeta),
                                          _ptr(counts), flags))
@@ -223,7 +223,8 @@ class Plan:
         return out
 
     def backward(self, dzeta):
-        """(dpos (n,3) float64, dw (n,) float64) for the last forward."""
+        """(dpos (n,3) float64, dw (n,) float64) for the last forward (compute or
+        compute_batch; for a batch dzeta is (ncat, zsize) like its zeta)."""
         import torch
         dz = torch.view_as_real(dzeta) if dzeta.is_complex() else dzeta
         dz = dz.contiguous().to(torch.float64)

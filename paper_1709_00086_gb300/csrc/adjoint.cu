@@ -7,7 +7,9 @@
 //      V_i = M_m A_i                    (k_vgemm, per m block, FP32)
 //      dL/dw_i (as a primary) = Re(A_i^H V_i)   (fused into k_vgemm)
 //      H_i = w_i V_i                    (applied by the adjoint pair pass)
-// and the pair pass (k_pair, mode 1) adds, for every pair (i, j) in bin b,
+// (per catalog c of a batched forward, M is built from that catalog's dL/dzeta_c)
+// and the pair pass (k_adj over the pair lists, or the fused k_pair mode 1)
+// adds, for every pair (i, j) in bin b,
 // 2 Re(conj(H_i,b) . Y(rhat_ij)) to dL/dw_j and the gradient of the same
 // quantity with respect to the separation to dL/dpos_j and -dL/dpos_i.
 // In the real form of an A row ([Re | Im] halves for m >= 1) M acts as
@@ -30,12 +32,13 @@ struct MInfo {
     long long zoff[kMaxL + 1];  // complex offset of block m in zeta
 };
 
-__global__ void k_build_mreal(const double* dz, MInfo mi, int lmax, float* Mr) {
-    const int m = blockIdx.y;
+__global__ void k_build_mreal(const double* dz, MInfo mi, int lmax, int64_t zsize, size_t mfloats,
+                              float* Mr) {
+    const int m = blockIdx.y, cat = blockIdx.z;
     if (m > lmax) return;
     const int K = mi.K[m], W = mi.W[m];
-    const double* Z = dz + 2 * mi.zoff[m];
-    float* out = Mr + mi.moff[m];
+    const double* Z = dz + 2 * ((int64_t)cat * zsize + mi.zoff[m]);
+    float* out = Mr + (size_t)cat * mfloats + mi.moff[m];
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < W * W; e += gridDim.x * blockDim.x) {
         const int rr = e / W, cc = e % W;
         const int r = rr % K, c = cc % K;
@@ -53,12 +56,18 @@ __global__ void k_build_mreal(const double* dz, MInfo mi, int lmax, float* Mr) {
     }
 }
 
+// One CTA per block of up to kRows rows of one catalog: blk = {catalog, first
+// row, rows}; the catalog picks its M.
 __global__ void __launch_bounds__(kVThreads) k_vgemm(const float* __restrict__ A, int RLP, int RL,
-                                                     int64_t rows, const float* __restrict__ Mr,
+                                                     const int4* __restrict__ blks,
+                                                     const float* __restrict__ Mall, size_t mfloats,
                                                      MInfo mi, int lmax, float* V, double* dw) {
     extern __shared__ float sA[];  // kRows x RL
     __shared__ float red[kRows][kVThreads / 32];
-    const int64_t r0 = (int64_t)blockIdx.x * kRows;
+    const int4 blk = blks[blockIdx.x];
+    const float* __restrict__ Mr = Mall + (size_t)blk.x * mfloats;
+    const int64_t r0 = blk.y;
+    const int64_t rows = r0 + blk.z;
     for (int k = threadIdx.x; k < kRows * RL; k += kVThreads) {
         const int rr = k / RL, c = k % RL;
         sA[k] = (r0 + rr < rows) ? A[(r0 + rr) * RLP + c] : 0.f;
@@ -134,18 +143,21 @@ size_t adjoint_m_floats(int nbins, int lmax) {
     return s;
 }
 
-int launch_adjoint_prep(const double* dzeta, int nbins, int lmax, const float* A, int RLP, int RL,
-                        int64_t rows, float* Mr, float* V, double* dw, cudaStream_t st) {
+int adjoint_rows_per_block() { return kRows; }
+
+int launch_adjoint_prep(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, const float* A,
+                        int RLP, int RL, const int4* blks, int nblks, float* Mr, float* V, double* dw,
+                        cudaStream_t st) {
     const MInfo mi = make_info(nbins, lmax);
-    dim3 g1(64, lmax + 1);
-    k_build_mreal<<<g1, 256, 0, st>>>(dzeta, mi, lmax, Mr);
-    if (rows > 0) {
+    const size_t mfl = adjoint_m_floats(nbins, lmax);
+    dim3 g1(64, lmax + 1, ncat);
+    k_build_mreal<<<g1, 256, 0, st>>>(dzeta, mi, lmax, zsize, mfl, Mr);
+    if (nblks > 0) {
         const size_t smem = sizeof(float) * kRows * RL;
         if (cudaFuncSetAttribute(k_vgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return -1;
-        k_vgemm<<<(unsigned)((rows + kRows - 1) / kRows), kVThreads, smem, st>>>(A, RLP, RL, rows, Mr,
-                                                                             mi, lmax, V, dw);
+        k_vgemm<<<(unsigned)nblks, kVThreads, smem, st>>>(A, RLP, RL, blks, Mr, mfl, mi, lmax, V, dw);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -94,7 +94,7 @@ struct g3pcf_plan_s {
     DevBuf small;       // status, queue
     DevBuf counts, A, partials, d_tiles, d_segs, d_segfirst, d_colmap, d_colscale, d_catoff;
     DevBuf d_colconv, d_colcoef, d_bintab_s, d_slotconv, d_slotcoef;
-    DevBuf d_ranges, d_tiles_tc, ops, d_cats, d_mreal, d_V, d_bintab, wrow;
+    DevBuf d_ranges, d_tiles_tc, ops, d_cats, d_mreal, d_V, d_bintab, wrow, d_vblk;
     int64_t opt_chunk = 0;   // G3PCF_OPT_CHUNK_ROWS
     // pinned staging for host -> device tables (capturable copies); offset
     // restarts at every forward
@@ -140,6 +140,7 @@ struct g3pcf_plan_s {
     bool have_alm = false;
     int64_t last_n = 0, last_np = 0;
     int last_ncat = 0;
+    std::vector<int64_t> last_offs;  // catalog offsets of the last forward
     const void* last_pos = nullptr;
     const float* last_w = nullptr;
     int last_pos_f64 = 0;
@@ -971,6 +972,7 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
     P->last_n = n;
     P->last_np = nprim;
     P->last_ncat = c.ncat;
+    P->last_offs = c.offs;
     P->last_pos = c.pos;
     P->last_w = c.w;
     P->last_pos_f64 = c.pos_f64;
@@ -1232,7 +1234,6 @@ int g3pcf_backward(g3pcf_plan_t P, const double* dzeta, double* dpos, double* dw
     if (!dzeta || !dpos || !dw) return fail(G3PCF_ERR_ARG, "dzeta, dpos and dw must be non-null");
     if (P->los_mode == G3PCF_LOS_RADIAL_OPEN)
         return fail(G3PCF_ERR_UNSUPPORTED, "the adjoint supports the z line-of-sight modes only");
-    if (P->last_ncat != 1) return fail(G3PCF_ERR_UNSUPPORTED, "the adjoint of a batched call is not built");
     if (P->last_chunked)
         return fail(G3PCF_ERR_STATE, "the last forward ran in chunks; rerun it with all primaries in one chunk");
     cudaStream_t st = P->stream;
@@ -1243,15 +1244,27 @@ int g3pcf_backward(g3pcf_plan_t P, const double* dzeta, double* dpos, double* dw
         CK(cudaStreamSynchronize(st));
         return G3PCF_OK;
     }
-    if (ensure(P->d_mreal, sizeof(float) * adjoint_m_floats(P->nbins, P->lmax), "adjoint M") ||
-        ensure(P->d_V, sizeof(float) * (size_t)P->RLP * rows, "adjoint V"))
+    const int ncat = P->last_ncat;
+    // row blocks of one catalog each (rows are original indices; catalog c holds
+    // [offs[c], offs[c+1]) of a batched forward, every row of a single one)
+    const int RB = adjoint_rows_per_block();
+    std::vector<int4> blks;
+    for (int c = 0; c < ncat; ++c) {
+        const int64_t r0 = ncat > 1 ? P->last_offs[c] : 0, r1 = ncat > 1 ? P->last_offs[c + 1] : rows;
+        for (int64_t r = r0; r < r1; r += RB) blks.push_back(int4{c, (int)r, (int)std::min<int64_t>(RB, r1 - r), 0});
+    }
+    if (ensure(P->d_mreal, sizeof(float) * adjoint_m_floats(P->nbins, P->lmax) * ncat, "adjoint M") ||
+        ensure(P->d_V, sizeof(float) * (size_t)P->RLP * rows, "adjoint V") ||
+        ensure(P->d_vblk, sizeof(int4) * (blks.size() + 1), "adjoint blocks"))
         return G3PCF_ERR_ALLOC;
+    CK(cudaMemcpyAsync(P->d_vblk.p, blks.data(), sizeof(int4) * blks.size(), cudaMemcpyHostToDevice, st));
     int* d_status = P->small.as<int>();
     int* d_queue = d_status + 16;
     CK(cudaMemsetAsync(P->small.p, 0, 256, st));
-    CK(cudaMemsetAsync(P->counts.p, 0, sizeof(unsigned long long) * P->nbins, st));
-    if (launch_adjoint_prep(dzeta, P->nbins, P->lmax, P->A.as<float>(), P->RLP, P->RL, rows,
-                            P->d_mreal.as<float>(), P->d_V.as<float>(), dw, st) != 0)
+    CK(cudaMemsetAsync(P->counts.p, 0, sizeof(unsigned long long) * P->nbins * ncat, st));
+    if (launch_adjoint_prep(dzeta, P->nbins, P->lmax, ncat, zsize_of(P->nbins, P->lmax), P->A.as<float>(),
+                            P->RLP, P->RL, P->d_vblk.as<int4>(), (int)blks.size(), P->d_mreal.as<float>(),
+                            P->d_V.as<float>(), dw, st) != 0)
         return fail(G3PCF_ERR_CUDA, "adjoint preparation launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     PairArgs pa{};
     pa.pts = P->pts.as<float4>();
@@ -1480,7 +1493,7 @@ int g3pcf_destroy(g3pcf_plan_t P) {
                       &P->scan_tmp, &P->pts, &P->pts64, &P->orig, &P->cstart, &P->plist,
                       &P->small, &P->counts, &P->A, &P->partials, &P->d_tiles, &P->d_segs,
                       &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_colconv, &P->d_colcoef, &P->d_bintab_s, &P->d_slotconv, &P->d_slotcoef, &P->d_catoff, &P->d_ranges,
-                      &P->d_tiles_tc, &P->ops, &P->d_cats, &P->d_mreal, &P->d_V, &P->d_bintab,
+                      &P->d_tiles_tc, &P->ops, &P->d_cats, &P->d_mreal, &P->d_V, &P->d_bintab, &P->d_vblk,
                       &P->wrow, &P->l_need, &P->l_base, &P->l_nch, &P->l_pool, &P->l_tag, &P->l_ord,
                       &P->l_gbase, &P->l_scantmp, &P->l_passq};
     for (DevBuf* b : bufs) b->release();

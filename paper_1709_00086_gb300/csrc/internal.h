@@ -224,8 +224,12 @@ int launch_contract_tc(const void* ops, int64_t P_pad, int RL, const Tile* tiles
 
 // ---- adjoint.cu ----------------------------------------------------------------
 size_t adjoint_m_floats(int nbins, int lmax);
-int launch_adjoint_prep(const double* dzeta, int nbins, int lmax, const float* A, int RLP, int RL,
-                        int64_t rows, float* Mr, float* V, double* dw, cudaStream_t st);
+int adjoint_rows_per_block();
+// M_c = G_c + G_c^H per catalog c (ncat x adjoint_m_floats), then V = M_c A and
+// the primary-weight term of dL/dw per row block blks[] = {catalog, first row, rows}
+int launch_adjoint_prep(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, const float* A,
+                        int RLP, int RL, const int4* blks, int nblks, float* Mr, float* V, double* dw,
+                        cudaStream_t st);
 
 // ---- api.cu / noalloc.cu -----------------------------------------------------
 void set_last_error(const char* msg);
