@@ -234,8 +234,9 @@ int g3pcf_fp32_peak(double* tflops, void* stream);
  *                             large catalogs are processed in chunks so that the
  *                             per-primary multipoles never exceed the memory budget
  *                             (automatic: all primaries if they fit, else chunks);
- *                             after a chunked forward g3pcf_alm and g3pcf_backward
- *                             return G3PCF_ERR_STATE
+ *                             after a chunked forward g3pcf_alm returns
+ *                             G3PCF_ERR_STATE and g3pcf_backward recomputes the
+ *                             multipoles chunk by chunk (pair lists only)
  *   G3PCF_OPT_CELLS_PER_RMAX  cell-list resolution s (cell side >= rmax / s, 1..8)
  *   G3PCF_OPT_KFLUSH          pairs per lane per bucket flush of the fused pair
  *                             kernel (2..16)

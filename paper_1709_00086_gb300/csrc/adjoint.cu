@@ -57,14 +57,25 @@ __global__ void k_build_mreal(const double* dz, MInfo mi, int lmax, int64_t zsiz
 }
 
 // One CTA per block of up to kRows rows of one catalog: blk = {catalog, first
-// row, rows}; the catalog picks its M.
+// row, rows}; the catalog picks its M.  Without a block table (blks null) block
+// b covers rows row_lo + kRows b .. of catalog 0 below row_hi.  The row's
+// primary-weight term is added to dw[row], or, for rows of a chunk of
+// primaries (rorig non-null), to dw[rorig[rplist ? rplist[q0 + row] : q0 + row]].
 __global__ void __launch_bounds__(kVThreads) k_vgemm(const float* __restrict__ A, int RLP, int RL,
-                                                     const int4* __restrict__ blks,
-                                                     const float* __restrict__ Mall, size_t mfloats,
-                                                     MInfo mi, int lmax, float* V, double* dw) {
+                                                     const int4* __restrict__ blks, int64_t row_lo,
+                                                     int64_t row_hi, const float* __restrict__ Mall,
+                                                     size_t mfloats, MInfo mi, int lmax, float* V,
+                                                     double* dw, const int* rplist, const int* rorig,
+                                                     int64_t q0) {
     extern __shared__ float sA[];  // kRows x RL
     __shared__ float red[kRows][kVThreads / 32];
-    const int4 blk = blks[blockIdx.x];
+    int4 blk;
+    if (blks) {
+        blk = blks[blockIdx.x];
+    } else {
+        const int64_t b0 = row_lo + (int64_t)blockIdx.x * kRows;
+        blk = make_int4(0, (int)b0, (int)(row_hi - b0 < kRows ? row_hi - b0 : kRows), 0);
+    }
     const float* __restrict__ Mr = Mall + (size_t)blk.x * mfloats;
     const int64_t r0 = blk.y;
     const int64_t rows = r0 + blk.z;
@@ -108,7 +119,13 @@ __global__ void __launch_bounds__(kVThreads) k_vgemm(const float* __restrict__ A
     if (threadIdx.x < kRows && r0 + threadIdx.x < rows) {
         double s = 0.0;
         for (int k = 0; k < kVThreads / 32; ++k) s += (double)red[threadIdx.x][k];
-        dw[r0 + threadIdx.x] = s;  // the primary-weight term; pair terms are added later
+        const int64_t row = r0 + threadIdx.x;
+        int64_t idx = row;
+        if (rorig) {
+            const int64_t q = q0 + row;
+            idx = rorig[rplist ? rplist[q] : q];
+        }
+        dw[idx] += s;  // the primary-weight term (dw starts at zero; pair terms add atomically)
     }
 }
 
@@ -148,17 +165,40 @@ int adjoint_rows_per_block() { return kRows; }
 int launch_adjoint_prep(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, const float* A,
                         int RLP, int RL, const int4* blks, int nblks, float* Mr, float* V, double* dw,
                         cudaStream_t st) {
-    const MInfo mi = make_info(nbins, lmax);
-    const size_t mfl = adjoint_m_floats(nbins, lmax);
-    dim3 g1(64, lmax + 1, ncat);
-    k_build_mreal<<<g1, 256, 0, st>>>(dzeta, mi, lmax, zsize, mfl, Mr);
+    if (launch_adjoint_m(dzeta, nbins, lmax, ncat, zsize, Mr, st) != 0) return -1;
     if (nblks > 0) {
+        const MInfo mi = make_info(nbins, lmax);
         const size_t smem = sizeof(float) * kRows * RL;
         if (cudaFuncSetAttribute(k_vgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return -1;
-        k_vgemm<<<(unsigned)nblks, kVThreads, smem, st>>>(A, RLP, RL, blks, Mr, mfl, mi, lmax, V, dw);
+        k_vgemm<<<(unsigned)nblks, kVThreads, smem, st>>>(A, RLP, RL, blks, 0, 0, Mr,
+                                                         adjoint_m_floats(nbins, lmax), mi, lmax, V, dw,
+                                                         nullptr, nullptr, 0);
     }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_adjoint_m(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, float* Mr,
+                     cudaStream_t st) {
+    const MInfo mi = make_info(nbins, lmax);
+    dim3 g1(64, lmax + 1, ncat);
+    k_build_mreal<<<g1, 256, 0, st>>>(dzeta, mi, lmax, zsize, adjoint_m_floats(nbins, lmax), Mr);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_vgemm_rows(const float* A, int RLP, int RL, int64_t row_lo, int64_t row_hi, const float* Mr,
+                      int nbins, int lmax, float* V, double* dw, const int* plist, const int* orig,
+                      int64_t q0, cudaStream_t st) {
+    if (row_hi <= row_lo) return 0;
+    const MInfo mi = make_info(nbins, lmax);
+    const size_t smem = sizeof(float) * kRows * RL;
+    if (cudaFuncSetAttribute(k_vgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return -1;
+    const int64_t nb = (row_hi - row_lo + kRows - 1) / kRows;
+    k_vgemm<<<(unsigned)nb, kVThreads, smem, st>>>(A, RLP, RL, nullptr, row_lo, row_hi, Mr,
+                                                   adjoint_m_floats(nbins, lmax), mi, lmax, V, dw, plist,
+                                                   orig, q0);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

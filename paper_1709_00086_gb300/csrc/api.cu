@@ -527,7 +527,7 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode
     la.bin_tscale = pa.bin_tscale;
     la.g = pa.g;
     la.bins = pa.bins;
-    if (mode == 1) {
+    if (mode >= 1) {
         la.V = pa.V;
         la.dw = pa.dw;
         la.dpos = pa.dpos;
@@ -664,7 +664,18 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode
         CK(cudaMemsetAsync(la.queue, 0, sizeof(int), st));
         ++P->launches;
         CK(cudaEventRecord(ev[2], st));
-        if ((mode == 1 ? launch_adj(P->lmax, la, P->nsm, st) : launch_accum(P->lmax, la, P->nsm, st)) != 0)
+        if (mode == 2) {
+            // recompute: the chunk-local multipole rows of this pass, their V = M A and
+            // primary-weight terms, then the adjoint pair pass over the same lists
+            P->launches += 2;
+            if (launch_accum(P->lmax, la, P->nsm, st) != 0 ||
+                launch_vgemm_rows(la.A, la.RLP, la.RL, la.qa - la.q0, la.qb - la.q0, P->d_mreal.as<float>(),
+                                  P->nbins, P->lmax, P->d_V.as<float>(), pa.dw, la.plist, la.orig, la.q0,
+                                  st) != 0)
+                return fail(G3PCF_ERR_CUDA, "adjoint recompute launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+            CK(cudaMemsetAsync(la.queue, 0, sizeof(int), st));
+        }
+        if ((mode >= 1 ? launch_adj(P->lmax, la, P->nsm, st) : launch_accum(P->lmax, la, P->nsm, st)) != 0)
             return fail(G3PCF_ERR_CUDA, "pair accumulate launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         CK(cudaEventRecord(ev[3], st));
     }
@@ -1234,8 +1245,8 @@ int g3pcf_backward(g3pcf_plan_t P, const double* dzeta, double* dpos, double* dw
     if (!dzeta || !dpos || !dw) return fail(G3PCF_ERR_ARG, "dzeta, dpos and dw must be non-null");
     if (P->los_mode == G3PCF_LOS_RADIAL_OPEN)
         return fail(G3PCF_ERR_UNSUPPORTED, "the adjoint supports the z line-of-sight modes only");
-    if (P->last_chunked)
-        return fail(G3PCF_ERR_STATE, "the last forward ran in chunks; rerun it with all primaries in one chunk");
+    if (P->last_chunked && P->opt_pair == 1)
+        return fail(G3PCF_ERR_UNSUPPORTED, "a chunked backward recomputes the multipoles through the pair lists");
     cudaStream_t st = P->stream;
     const int64_t n = P->last_n, rows = P->last_np;
     CK(cudaMemsetAsync(dpos, 0, sizeof(double) * 3 * (n > 0 ? n : 1), st));
@@ -1245,6 +1256,56 @@ int g3pcf_backward(g3pcf_plan_t P, const double* dzeta, double* dpos, double* dw
         return G3PCF_OK;
     }
     const int ncat = P->last_ncat;
+    if (P->last_chunked) {
+        // the multipoles did not fit: recompute them chunk by chunk (same chunks as the
+        // forward) and run each chunk's adjoint on the lists that recomputed them
+        const int64_t C = P->fixed_chunk;
+        if (ensure(P->d_mreal, sizeof(float) * adjoint_m_floats(P->nbins, P->lmax), "adjoint M") ||
+            ensure(P->d_V, sizeof(float) * (size_t)P->RLP * C, "adjoint V"))
+            return G3PCF_ERR_ALLOC;
+        int* d_status = P->small.as<int>();
+        int* d_queue = d_status + 16;
+        CK(cudaMemsetAsync(P->small.p, 0, 256, st));
+        CK(cudaMemsetAsync(P->counts.p, 0, sizeof(unsigned long long) * P->nbins, st));
+        if (launch_adjoint_m(dzeta, P->nbins, P->lmax, 1, zsize_of(P->nbins, P->lmax), P->d_mreal.as<float>(),
+                             st) != 0)
+            return fail(G3PCF_ERR_CUDA, "adjoint preparation launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        P->lev_used = 0;
+        for (int64_t q0 = 0; q0 < rows; q0 += C) {
+            PairArgs pa{};
+            pa.pts = P->pts.as<float4>();
+            pa.pts64 = P->last_pos_f64 ? P->pts64.as<double>() : nullptr;
+            pa.orig = P->orig.as<int>();
+            pa.cstart = P->cstart.as<int>();
+            pa.plist = P->last_plist ? P->plist.as<int>() : nullptr;
+            pa.key = P->key_sorted;
+            pa.q0 = (int)q0;
+            pa.nprim = (int)std::min<int64_t>(rows, q0 + C);
+            pa.chunked = 1;
+            pa.wrow = P->wrow.as<float>();
+            pa.A = P->A.as<float>();
+            pa.RLP = P->RLP;
+            pa.colmap = P->d_colmap.as<int>();
+            pa.colscale = P->d_colscale.as<float>();
+            pa.RL = P->RL;
+            pa.counts = P->counts.as<unsigned long long>();
+            pa.queue = d_queue;
+            pa.status = d_status;
+            pa.kflush = P->kflush;
+            pa.V = P->d_V.as<float>();
+            pa.dw = dw;
+            pa.dpos = dpos;
+            pa.g = P->last_grid;
+            pa.bins = P->bins;
+            pa.bintab = P->d_bintab.as<unsigned char>();
+            pa.bin_tscale = P->bin_tscale;
+            CK(cudaMemsetAsync(d_queue, 0, sizeof(int), st));
+            if (int r = run_pair_lists(P, pa, st, 2)) return r;
+        }
+        CK(cudaMemcpyAsync(P->h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return read_status(P);
+    }
     // row blocks of one catalog each (rows are original indices; catalog c holds
     // [offs[c], offs[c+1]) of a batched forward, every row of a single one)
     const int RB = adjoint_rows_per_block();

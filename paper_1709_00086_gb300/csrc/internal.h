@@ -230,6 +230,14 @@ int adjoint_rows_per_block();
 int launch_adjoint_prep(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, const float* A,
                         int RLP, int RL, const int4* blks, int nblks, float* Mr, float* V, double* dw,
                         cudaStream_t st);
+// the two halves of it for a chunked backward: M of every catalog, then V and the
+// primary-weight term for the A rows [row_lo, row_hi) of the chunk starting at
+// processing-order primary q0 (dw indexed through plist/orig)
+int launch_adjoint_m(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, float* Mr,
+                     cudaStream_t st);
+int launch_vgemm_rows(const float* A, int RLP, int RL, int64_t row_lo, int64_t row_hi, const float* Mr,
+                      int nbins, int lmax, float* V, double* dw, const int* plist, const int* orig,
+                      int64_t q0, cudaStream_t st);
 
 // ---- api.cu / noalloc.cu -----------------------------------------------------
 void set_last_error(const char* msg);

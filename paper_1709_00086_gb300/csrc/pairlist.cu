@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(kLThreads) k_adj(ListArgs a) {
             img[lane] = make_float4(P0.x - sx * Lb, P0.y - sy * Lb, P0.z - sz * Lb, 0.f);
         }
         const int row = a.orig[p];
-        const float* Vrow = a.V + (int64_t)row * a.RLP;
+        const float* Vrow = a.V + (int64_t)(a.chunked ? q - a.q0 : row) * a.RLP;
         for (int idx = lane; idx < B * NR; idx += 32) {
             const int b = idx / NR, sl = idx - b * NR;
             const int4 cv = __ldg(a.slotconv + sl);
