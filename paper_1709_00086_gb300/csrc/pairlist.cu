@@ -364,6 +364,27 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// Image `code` of the primary (its position minus the code's box shift) as an
+// FP32 head img[code] and tail img[27 + code] of the FP64 value (the primary's
+// FP64 position when the input is FP64): the separation (q - head) - tail is
+// then as exact as FP32 allows even where the shift is a whole box side.
+__device__ __forceinline__ void set_image(float4* img, int code, const float4& P0, const double* pts64, int p,
+                                          double boxd) {
+    const int sx = code % 3 - 1, sy = (code / 3) % 3 - 1, sz = code / 9 - 1;
+    double x = P0.x, y = P0.y, z = P0.z;
+    if (pts64) {
+        x = pts64[3 * (int64_t)p];
+        y = pts64[3 * (int64_t)p + 1];
+        z = pts64[3 * (int64_t)p + 2];
+    }
+    x -= sx * boxd;
+    y -= sy * boxd;
+    z -= sz * boxd;
+    const float hx = (float)x, hy = (float)y, hz = (float)z;
+    img[code] = make_float4(hx, hy, hz, 0.f);
+    img[27 + code] = make_float4((float)(x - hx), (float)(y - hy), (float)(z - hz), 0.f);
+}
+
 // Separation of one list entry from the primary (image img[code]), rotated
 // to the primary's line of sight in radial mode, as a unit vector and weight.
 __device__ __forceinline__ void pair_dir(const float4& q, unsigned e, const float4* img, const float* R,
@@ -371,10 +392,10 @@ __device__ __forceinline__ void pair_dir(const float4& q, unsigned e, const floa
     float dx = 1.f, dy = 0.f, dz = 0.f;
     w = 0.f;
     if (e != kNoPair) {
-        const float4 o = img[e >> kIdxBits];
-        dx = q.x - o.x;
-        dy = q.y - o.y;
-        dz = q.z - o.z;
+        const float4 o = img[e >> kIdxBits], ol = img[27 + (e >> kIdxBits)];
+        dx = (q.x - o.x) - ol.x;
+        dy = (q.y - o.y) - ol.y;
+        dz = (q.z - o.z) - ol.z;
         w = q.w;
         if (radial) {
             const float rx = fmaf(R[0], dx, fmaf(R[1], dy, R[2] * dz));
@@ -407,12 +428,14 @@ __device__ __forceinline__ void reduce_cheb(float (&acc0)[L + 1], float2 (&accc)
     butterfly_add<L>(acc, lane, res_b);
 }
 
-// Per-warp shared memory of k_accum: res[B][NRP] float, img[27] float4, R[16]
-// float, entry ring [kEntRing][32] uint, point ring [kPtRing][32] float4.
+// Per-warp shared memory of k_accum / k_adj: img[27] float4 and its low parts
+// imglo[27] float4 (below), R[16] float, point ring [kPtRing][32] float4, entry
+// ring [kEntRing][32] uint, res[B][NRP] float.
+constexpr int kImgBytes = 2 * 27 * 16;
 constexpr int kEntRing = 8;
 constexpr int kPtRing = 4;
 __host__ __device__ constexpr size_t accum_smem_per_warp(int B, int NRP) {
-    return (size_t)B * NRP * 4 + 27 * 16 + 64 + kEntRing * 32 * 4 + kPtRing * 32 * 16;
+    return (size_t)B * NRP * 4 + kImgBytes + 64 + kEntRing * 32 * 4 + kPtRing * 32 * 16;
 }
 
 template <int L>
@@ -423,12 +446,11 @@ __global__ void __launch_bounds__(kLThreads, 3) k_accum(ListArgs a) {
     const int B = a.bins.nbins;
     unsigned char* base = la_raw + (size_t)wid * accum_smem_per_warp(B, NRP);
     float4* img = reinterpret_cast<float4*>(base);
-    float* Rs = reinterpret_cast<float*>(base + 27 * 16);
-    float4* pring = reinterpret_cast<float4*>(base + 27 * 16 + 64);
-    unsigned* ering = reinterpret_cast<unsigned*>(base + 27 * 16 + 64 + kPtRing * 32 * 16);
-    float* res = reinterpret_cast<float*>(base + 27 * 16 + 64 + kPtRing * 32 * 16 + kEntRing * 32 * 4);
+    float* Rs = reinterpret_cast<float*>(base + kImgBytes);
+    float4* pring = reinterpret_cast<float4*>(base + kImgBytes + 64);
+    unsigned* ering = reinterpret_cast<unsigned*>(base + kImgBytes + 64 + kPtRing * 32 * 16);
+    float* res = reinterpret_cast<float*>(base + kImgBytes + 64 + kPtRing * 32 * 16 + kEntRing * 32 * 4);
     const Grid& g = a.g;
-    const float Lb = g.box;
     const int qa = a.qrange ? a.qrange[0] : a.qa, qb = a.qrange ? a.qrange[1] : a.qb;
     for (;;) {
         int q = 0;
@@ -437,10 +459,7 @@ __global__ void __launch_bounds__(kLThreads, 3) k_accum(ListArgs a) {
         if (q >= qb) break;
         const int p = a.plist ? a.plist[q] : q;
         const float4 P0 = a.pts[p];
-        if (lane < 27) {
-            const int sx = lane % 3 - 1, sy = (lane / 3) % 3 - 1, sz = lane / 9 - 1;
-            img[lane] = make_float4(P0.x - sx * Lb, P0.y - sy * Lb, P0.z - sz * Lb, 0.f);
-        }
+        if (lane < 27) set_image(img, lane, P0, a.pts64, p, g.boxd);
         if (lane < 9) {
             double x0 = P0.x, x1 = P0.y, x2 = P0.z;
             if (a.pts64) {
@@ -558,11 +577,10 @@ __global__ void __launch_bounds__(kLThreads) k_adj(ListArgs a) {
     const int B = a.bins.nbins;
     unsigned char* base = la_raw + (size_t)wid * accum_smem_per_warp(B, NRP);
     float4* img = reinterpret_cast<float4*>(base);
-    float4* pring = reinterpret_cast<float4*>(base + 27 * 16 + 64);
-    unsigned* ering = reinterpret_cast<unsigned*>(base + 27 * 16 + 64 + kPtRing * 32 * 16);
-    float* G = reinterpret_cast<float*>(base + 27 * 16 + 64 + kPtRing * 32 * 16 + kEntRing * 32 * 4);
+    float4* pring = reinterpret_cast<float4*>(base + kImgBytes + 64);
+    unsigned* ering = reinterpret_cast<unsigned*>(base + kImgBytes + 64 + kPtRing * 32 * 16);
+    float* G = reinterpret_cast<float*>(base + kImgBytes + 64 + kPtRing * 32 * 16 + kEntRing * 32 * 4);
     const Grid& g = a.g;
-    const float Lb = g.box;
     const int qa = a.qrange ? a.qrange[0] : a.qa, qb = a.qrange ? a.qrange[1] : a.qb;
     for (;;) {
         int q = 0;
@@ -571,10 +589,7 @@ __global__ void __launch_bounds__(kLThreads) k_adj(ListArgs a) {
         if (q >= qb) break;
         const int p = a.plist ? a.plist[q] : q;
         const float4 P0 = a.pts[p];
-        if (lane < 27) {
-            const int sx = lane % 3 - 1, sy = (lane / 3) % 3 - 1, sz = lane / 9 - 1;
-            img[lane] = make_float4(P0.x - sx * Lb, P0.y - sy * Lb, P0.z - sz * Lb, 0.f);
-        }
+        if (lane < 27) set_image(img, lane, P0, a.pts64, p, g.boxd);
         const int row = a.orig[p];
         const float* Vrow = a.V + (int64_t)(a.chunked ? q - a.q0 : row) * a.RLP;
         for (int idx = lane; idx < B * NR; idx += 32) {
@@ -633,9 +648,9 @@ __global__ void __launch_bounds__(kLThreads) k_adj(ListArgs a) {
                 const unsigned e = ering[(i & (kEntRing - 1)) * 32 + lane];
                 if (e != kNoPair) {
                     const float4 qv = pring[(i & (kPtRing - 1)) * 32 + lane];
-                    const float4 o = img[e >> kIdxBits];
+                    const float4 o = img[e >> kIdxBits], ol = img[27 + (e >> kIdxBits)];
                     const int jj = __ldg(a.orig + (e & kIdxMask));
-                    const float dx = qv.x - o.x, dy = qv.y - o.y, dz = qv.z - o.z;
+                    const float dx = (qv.x - o.x) - ol.x, dy = (qv.y - o.y) - ol.y, dz = (qv.z - o.z) - ol.z;
                     const float rinv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
                     const float z = dz * rinv, ux = dx * rinv, uy = dy * rinv;
                     const float* Gb = G + bA * NRP;

@@ -6,8 +6,8 @@ gradient is itself pinned to finite differences in test_oracle_grad.py.  The
 target zeta comes from the oracle on a second catalog, so no expected value
 comes from the CUDA path.  Tolerance: max |g - g_ref| / max |g_ref| per
 quantity.  The target is 1e-6; measured over seeded cases the error is
-3.4e-7 to 2.0e-6, bounded by the FP32 evaluation of Y_lm in the forward
-multipoles (their own error against the oracle is 4e-7 to 1.1e-6), so the
+3.3e-7 to 1.05e-6, bounded by the FP32 evaluation of Y_lm in the forward
+multipoles (their own error against the oracle is 2.8e-7 to 8.7e-7), so the
 tests assert 3e-6.
 """
 import numpy as np
