@@ -87,8 +87,10 @@ enum {
                                    of split-BF16 (hi+lo, 3 products) tcgen05 tensor cores */
     G3PCF_F_NO_SYNC = 4,        /* do not synchronise at the end; device status is then
                                    read by g3pcf_status()                                 */
-    G3PCF_F_KEEP_ALM = 8,       /* keep the multipoles of the call for g3pcf_alm and
-                                   g3pcf_backward (implied when requires_grad is used)    */
+    G3PCF_F_KEEP_ALM = 8,       /* the multipoles of the call are meant for g3pcf_alm and
+                                   g3pcf_backward (implied when requires_grad is used):
+                                   separations across a periodic box face are formed from
+                                   the exact FP64 image (about 5% more pair-stage time) */
     G3PCF_F_GRAPH = 16          /* replay a captured CUDA graph: the first call with a new
                                    signature (pointers, sizes, offsets, flags, options) runs
                                    once and captures its device work on an internal stream;

@@ -190,7 +190,7 @@ class Plan:
         return torch.view_as_complex(zeta), counts
 
     def compute_batch(self, pos, w, offsets, fp32_contraction=False, sync=True, graph=False,
-                      out=None, counts_out=None):
+                      out=None, counts_out=None, keep_alm=False):
         """Batched zeta over catalogs [offsets[c], offsets[c+1]): (ncat, zsize) complex.
 
         graph=True replays a captured CUDA graph for repeated calls with the same
@@ -205,7 +205,7 @@ class Plan:
         counts = counts_out if counts_out is not None else torch.empty(
             (ncat, self.nbins), dtype=torch.int64, device=pos.device)
         flags = ((F_CONTRACT_FP32 if fp32_contraction else 0) | (0 if sync else F_NO_SYNC) |
-                 (F_GRAPH if graph else 0))
+                 (F_GRAPH if graph else 0) | (F_KEEP_ALM if keep_alm else 0))
         self._stream()
         self._token += 1
         self._last_n = int(pos.shape[0])

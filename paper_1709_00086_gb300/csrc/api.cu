@@ -121,6 +121,7 @@ struct g3pcf_plan_s {
     std::vector<std::pair<int64_t, int64_t>> gl_warm;
     size_t gl_idx = 0;
     bool warm_for_graph = false;
+    bool exact_alm = false;  // this forward runs with G3PCF_F_KEEP_ALM
     int gl_events = 0;  // events the capture run will record
     DevBuf l_gbase, l_scantmp, l_passq;
     // events around every k_scan / k_accum launch of the last forward (4 per pass)
@@ -527,6 +528,8 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode
     la.bin_tscale = pa.bin_tscale;
     la.g = pa.g;
     la.bins = pa.bins;
+    // multipoles that will be differentiated take the exact image separations
+    la.exact_img = (mode >= 1 || P->exact_alm) ? 1 : 0;
     if (mode >= 1) {
         la.V = pa.V;
         la.dw = pa.dw;
@@ -695,6 +698,7 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
     P->launches = 0;
     P->stats[9] = P->stats[10] = 0.0;
     P->lev_used = 0;
+    P->exact_alm = (c.flags & G3PCF_F_KEEP_ALM) != 0;
     if (P->capturing) {
         P->gl_idx = 0;
     } else {

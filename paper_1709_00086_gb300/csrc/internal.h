@@ -171,6 +171,7 @@ struct ListArgs {
     const int* base;         // [q] first chunk of q, relative to the pool arrays
     int* nchunks;            // [q]
     const int* qrange;       // if set: qa = qrange[0], qb = qrange[1] (device-planned pass)
+    int exact_img;           // k_accum: separations from the head + tail of the primary's images
     // adjoint pass (k_adj): V rows (row = original index), slot tables of the
     // transposed Chebyshev connection, outputs (FP64, original order)
     const float* V;

@@ -387,15 +387,22 @@ __device__ __forceinline__ void set_image(float4* img, int code, const float4& P
 
 // Separation of one list entry from the primary (image img[code]), rotated
 // to the primary's line of sight in radial mode, as a unit vector and weight.
+template <bool EXACT>
 __device__ __forceinline__ void pair_dir(const float4& q, unsigned e, const float4* img, const float* R,
                                          int radial, float& z, float& ux, float& uy, float& w) {
     float dx = 1.f, dy = 0.f, dz = 0.f;
     w = 0.f;
     if (e != kNoPair) {
-        const float4 o = img[e >> kIdxBits], ol = img[27 + (e >> kIdxBits)];
-        dx = (q.x - o.x) - ol.x;
-        dy = (q.y - o.y) - ol.y;
-        dz = (q.z - o.z) - ol.z;
+        const float4 o = img[e >> kIdxBits];
+        dx = q.x - o.x;
+        dy = q.y - o.y;
+        dz = q.z - o.z;
+        if constexpr (EXACT) {  // the tail of the image (nonzero across a box face)
+            const float4 ol = img[27 + (e >> kIdxBits)];
+            dx -= ol.x;
+            dy -= ol.y;
+            dz -= ol.z;
+        }
         w = q.w;
         if (radial) {
             const float rx = fmaf(R[0], dx, fmaf(R[1], dy, R[2] * dz));
@@ -438,7 +445,7 @@ __host__ __device__ constexpr size_t accum_smem_per_warp(int B, int NRP) {
     return (size_t)B * NRP * 4 + kImgBytes + 64 + kEntRing * 32 * 4 + kPtRing * 32 * 16;
 }
 
-template <int L>
+template <int L, bool EXACT>
 __global__ void __launch_bounds__(kLThreads, 3) k_accum(ListArgs a) {
     constexpr int NRP = Shape<L>::NRP;
     extern __shared__ __align__(16) unsigned char la_raw[];
@@ -528,7 +535,7 @@ __global__ void __launch_bounds__(kLThreads, 3) k_accum(ListArgs a) {
                     const unsigned e = ering[(i & (kEntRing - 1)) * 32 + lane];
                     const float4 qv = pring[(i & (kPtRing - 1)) * 32 + lane];
                     float z, ux, uy, w;
-                    pair_dir(qv, e, img, Rs, g.radial, z, ux, uy, w);
+                    pair_dir<EXACT>(qv, e, img, Rs, g.radial, z, ux, uy, w);
                     accum_pair_cheb<L>(acc0, accc, z, ux, uy, w);
                 }
                 sA = sB;
@@ -754,22 +761,27 @@ int launch_adj_t(const ListArgs& a, int nsm, cudaStream_t st) {
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-template <int L>
-int launch_accum_t(const ListArgs& a, int nsm, cudaStream_t st) {
+template <int L, bool EXACT>
+int launch_accum_e(const ListArgs& a, int nsm, cudaStream_t st) {
     const size_t smem = accum_smem_per_warp(a.bins.nbins, Shape<L>::NRP) * kLWarps;
-    if (cudaFuncSetAttribute(k_accum<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (cudaFuncSetAttribute(k_accum<L, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return -1;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_accum<L>, kLThreads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_accum<L, EXACT>, kLThreads, smem) !=
             cudaSuccess ||
         per_sm < 1)
         return -1;
     int blocks = per_sm * nsm;
     const int need = (a.qb - a.qa + kLWarps - 1) / kLWarps;
     if (!a.qrange && blocks > need) blocks = need > 0 ? need : 1;
-    k_accum<L><<<blocks, kLThreads, smem, st>>>(a);
+    k_accum<L, EXACT><<<blocks, kLThreads, smem, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <int L>
+int launch_accum_t(const ListArgs& a, int nsm, cudaStream_t st) {
+    return a.exact_img ? launch_accum_e<L, true>(a, nsm, st) : launch_accum_e<L, false>(a, nsm, st);
 }
 
 int launch_scan_k(const ListArgs& a, int nsm, cudaStream_t st) {

