@@ -105,7 +105,7 @@ def test_tiny_catalogs(n):
         assert maxrel(z, zo) < TOL_FP32
 
 
-@pytest.mark.parametrize("nbins,lmax", [(1, 0), (1, 10), (32, 2), (7, 5)])
+@pytest.mark.parametrize("nbins,lmax", [(1, 0), (1, 10), (32, 2), (7, 5), (32, 10)])
 def test_degenerate_shapes(nbins, lmax):
     cat = catalogs.small_case("uniform", 1500, seed=nbins * 13 + lmax, box=100.0, nbins=nbins,
                               rmin=0.0, rmax=25.0, lmax=lmax)
