@@ -553,11 +553,10 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode
         int64_t slack = 0, stride = 0;
         int npass = 0;
         graph_plan_sizes(C, wm.first, wm.second, P->nbins, slack, stride, npass);
-        if (wm.first > ((int64_t)1 << 30) || stride < 1 || (int64_t)P->l_tag.bytes / 4 < C ||
-            (int64_t)P->l_ord.bytes / 4 < C || P->l_gbase.bytes < 4 * (size_t)nq ||
-            P->l_passq.bytes < 4 * (size_t)(npass + 1) || P->l_scantmp.bytes < 4 * scan_tmp_ints(nq) ||
-            (int)P->lev.size() < P->lev_used + 4 * npass) {
-            ++P->launches;  // lists too large for a device-planned graph: the fused kernel
+        if (stride < 1 || (int64_t)P->l_tag.bytes / 4 < C || (int64_t)P->l_ord.bytes / 4 < C ||
+            P->l_gbase.bytes < 8 * (size_t)nq || P->l_passq.bytes < 4 * (size_t)(npass + 1) ||
+            P->l_scantmp.bytes < plan_scan_tmp_bytes(nq) || (int)P->lev.size() < P->lev_used + 4 * npass) {
+            ++P->launches;  // the warm-up did not size the plan (cannot happen): the fused kernel
             if (launch_pair(P->lmax, pa, P->nsm, st) != 0)
                 return fail(G3PCF_ERR_CUDA, "pair kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
             return G3PCF_OK;
@@ -569,9 +568,8 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode
         if (launch_count(la, P->nsm, st) != 0)
             return fail(G3PCF_ERR_CUDA, "pair count launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         P->launches += 5;
-        if (scan_exclusive(la.need + qa, P->l_gbase.as<int>(), nq, P->l_scantmp.as<int>(), st) != 0 ||
-            launch_plan(la.need, P->l_gbase.as<int>(), qa, qb, (int)stride, (int)slack, npass,
-                        P->l_base.as<int>(), P->l_passq.as<int>(), pa.status, st) != 0)
+        if (launch_plan(la.need, P->l_gbase.as<long long>(), P->l_scantmp.as<long long>(), qa, qb, stride,
+                        (int)slack, npass, P->l_base.as<int>(), P->l_passq.as<int>(), pa.status, st) != 0)
             return fail(G3PCF_ERR_CUDA, "pair-list plan launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         for (int k = 0; k < npass; ++k) {
             la.qrange = P->l_passq.as<int>() + k;
@@ -632,8 +630,8 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode
         int64_t slack = 0, stride = 0;
         int npass = 0;
         graph_plan_sizes(cap, total, most, P->nbins, slack, stride, npass);
-        if (ensure(P->l_gbase, 4 * (size_t)nq, "pair-list plan") ||
-            ensure(P->l_scantmp, 4 * (scan_tmp_ints(nq) + 16), "pair-list plan") ||
+        if (ensure(P->l_gbase, 8 * (size_t)nq, "pair-list plan") ||
+            ensure(P->l_scantmp, plan_scan_tmp_bytes(nq), "pair-list plan") ||
             ensure(P->l_passq, 4 * (size_t)(npass + 1), "pair-list plan"))
             return G3PCF_ERR_ALLOC;
         P->gl_events += 4 * npass;

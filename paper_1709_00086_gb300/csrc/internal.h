@@ -187,11 +187,13 @@ struct ListArgs {
 };
 int launch_count(const ListArgs& a, int nsm, cudaStream_t st);
 // Device-side pass plan (graph capture): gbase = exclusive prefix of need over
-// [qa, qb); primary q goes to pass p = gbase / stride at base gbase - p * stride
-// (base -1 and the overflow bit when p >= npass or need > slack); passq[p] =
-// first primary of pass p (passq[npass] = qb).
-int launch_plan(const int* need, const int* gbase, int qa, int qb, int stride, int slack, int npass,
-                int* base, int* passq, int* status, cudaStream_t st);
+// [qa, qb) (64-bit; tmp holds plan_scan_tmp_bytes); primary q goes to pass
+// p = gbase / stride at base gbase - p * stride (base -1 and the overflow bit
+// when p >= npass or need > slack); passq[p] = first primary of pass p
+// (passq[npass] = qb).
+size_t plan_scan_tmp_bytes(int64_t n);
+int launch_plan(const int* need, long long* gbase, long long* tmp, int qa, int qb, long long stride, int slack,
+                int npass, int* base, int* passq, int* status, cudaStream_t st);
 int launch_scan(const ListArgs& a, int nsm, cudaStream_t st);
 int launch_accum(int lmax, const ListArgs& a, int nsm, cudaStream_t st);
 int launch_adj(int lmax, const ListArgs& a, int nsm, cudaStream_t st);

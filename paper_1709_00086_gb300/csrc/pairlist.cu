@@ -335,16 +335,72 @@ __global__ void k_plan_init(int* passq, int npass, int qb) {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p <= npass; p += gridDim.x * blockDim.x) passq[p] = qb;
 }
 
-__global__ void k_plan(const int* need, const int* gbase, int qa, int qb, int stride, int slack, int npass,
-                       int* base, int* passq, int* status) {
+// Exclusive prefix sums of need[qa..qb) in 64 bits (the chunks of a large
+// batch exceed 2^31): per-block sums, a scan of those, then the blocks.
+constexpr int kScan64 = 1024;
+__device__ long long block_scan64(long long v, long long* sh, long long& total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        long long t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(kFull, t, o);
+            if (lane >= o) t += y;
+        }
+        sh[lane] = t;
+    }
+    __syncthreads();
+    const long long pre = (wid > 0 ? sh[wid - 1] : 0) + x - v;
+    total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return pre;
+}
+__global__ void k_need_sums(const int* need, int64_t n, long long* bsum) {
+    __shared__ long long sh[32];
+    const int64_t i = blockIdx.x * (int64_t)kScan64 + threadIdx.x;
+    long long tot;
+    block_scan64(i < n ? need[i] : 0, sh, tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+__global__ void k_need_top(long long* bsum, int nb) {
+    __shared__ long long sh[32];
+    long long carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += kScan64) {
+        const int i = b0 + threadIdx.x;
+        long long tot;
+        const long long pre = block_scan64(i < nb ? bsum[i] : 0, sh, tot);
+        if (i < nb) bsum[i] = carry + pre;
+        carry += tot;
+    }
+}
+__global__ void k_need_final(const int* need, int64_t n, const long long* bsum, long long* out) {
+    __shared__ long long sh[32];
+    const int64_t i = blockIdx.x * (int64_t)kScan64 + threadIdx.x;
+    long long tot;
+    const long long pre = block_scan64(i < n ? need[i] : 0, sh, tot);
+    if (i < n) out[i] = bsum[blockIdx.x] + pre;
+}
+
+__global__ void k_plan(const int* need, const long long* gbase, int qa, int qb, long long stride, int slack,
+                       int npass, int* base, int* passq, int* status) {
     for (int q = qa + blockIdx.x * blockDim.x + threadIdx.x; q < qb; q += gridDim.x * blockDim.x) {
-        const int gb = gbase[q - qa];
-        const int pq = gb / stride;
+        const long long gb = gbase[q - qa];
+        const long long pql = gb / stride;
+        const int pq = pql < npass ? (int)pql : npass;
         const bool ok = pq < npass && need[q] <= slack;
-        base[q] = ok ? gb - pq * stride : -1;
+        base[q] = ok ? (int)(gb - pql * stride) : -1;
         if (!ok) atomicOr(status, kStatusOverflow);
         // first primary of every pass that starts here
-        const int pprev = q == qa ? -1 : gbase[q - 1 - qa] / stride;
+        const long long pprevl = q == qa ? -1 : gbase[q - 1 - qa] / stride;
+        const int pprev = pprevl < npass ? (int)pprevl : npass;
         for (int pp = pprev + 1; pp <= pq && pp < npass; ++pp) passq[pp] = q;
     }
 }
@@ -815,8 +871,17 @@ int launch_scan(const ListArgs& a, int nsm, cudaStream_t st) {
     return launch_scan_k(a, nsm, st);
 }
 
-int launch_plan(const int* need, const int* gbase, int qa, int qb, int stride, int slack, int npass,
-                int* base, int* passq, int* status, cudaStream_t st) {
+size_t plan_scan_tmp_bytes(int64_t n) { return 8 * (size_t)((n + kScan64 - 1) / kScan64 + 1); }
+
+int launch_plan(const int* need, long long* gbase, long long* tmp, int qa, int qb, long long stride, int slack,
+                int npass, int* base, int* passq, int* status, cudaStream_t st) {
+    const int64_t n = (int64_t)qb - qa;
+    if (n > 0) {
+        const int nb = (int)((n + kScan64 - 1) / kScan64);
+        k_need_sums<<<nb, kScan64, 0, st>>>(need + qa, n, tmp);
+        k_need_top<<<1, kScan64, 0, st>>>(tmp, nb);
+        k_need_final<<<nb, kScan64, 0, st>>>(need + qa, n, tmp, gbase);
+    }
     k_plan_init<<<1, 256, 0, st>>>(passq, npass, qb);
     if (qb > qa) {
         int blocks = (qb - qa + 255) / 256;
