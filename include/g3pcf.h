@@ -251,13 +251,18 @@ int g3pcf_fp32_peak(double* tflops, void* stream);
  *   G3PCF_OPT_LIST_BYTES      device bytes for the pair lists (0: up to 40% of free
  *                             memory, at most 32 GB); more pairs than fit are
  *                             processed in several passes
+ *   G3PCF_OPT_BASIS           multipoles of the pair-list forward: 0 = Chebyshev form
+ *                             (FP32, the fast path); 1 = the paper's monomial power
+ *                             sums sum w x^a y^b z^c, a + b + c <= lmax (Sec. 3.3.2),
+ *                             accumulated and converted in FP64 -- a slow cross-check
  * Returns G3PCF_ERR_ARG for unknown options or values out of range. */
 enum {
     G3PCF_OPT_CHUNK_ROWS = 1,
     G3PCF_OPT_CELLS_PER_RMAX = 2,
     G3PCF_OPT_KFLUSH = 3,
     G3PCF_OPT_PAIR_KERNELS = 4,
-    G3PCF_OPT_LIST_BYTES = 5
+    G3PCF_OPT_LIST_BYTES = 5,
+    G3PCF_OPT_BASIS = 7
 };
 int g3pcf_set_option(g3pcf_plan_t plan, int option, int64_t value);
 

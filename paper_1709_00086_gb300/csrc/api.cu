@@ -85,6 +85,10 @@ struct g3pcf_plan_s {
     std::vector<float> colcoef;
     std::vector<int4> slotconv;    // the transposed connection (pair-list adjoint)
     std::vector<float> slotcoef;
+    std::vector<int> monoexp, monoidx;  // monomial-basis tables (k_mono)
+    std::vector<int4> monoconv;
+    std::vector<double> monocoef;
+    int opt_basis = 0;             // G3PCF_OPT_BASIS
     std::vector<Tile> tiles;      // FP32 contraction tiles (edge T)
     std::vector<Tile> tiles_tc;   // tensor-core contraction tiles (edge T_tc)
     int T = 0, T_tc = 0;
@@ -93,7 +97,7 @@ struct g3pcf_plan_s {
     DevBuf key_a, key_b, val_a, val_b, hist, hist_off, scan_tmp, pts, pts64, orig, cstart, plist;
     DevBuf small;       // status, queue
     DevBuf counts, A, partials, d_tiles, d_segs, d_segfirst, d_colmap, d_colscale, d_catoff;
-    DevBuf d_colconv, d_colcoef, d_bintab_s, d_slotconv, d_slotcoef;
+    DevBuf d_colconv, d_colcoef, d_bintab_s, d_slotconv, d_slotcoef, d_monoexp, d_monoconv, d_monoidx, d_monocoef;
     DevBuf d_ranges, d_tiles_tc, ops, d_cats, d_mreal, d_V, d_bintab, wrow, d_vblk;
     int64_t opt_chunk = 0;   // G3PCF_OPT_CHUNK_ROWS
     // pinned staging for host -> device tables (capturable copies); offset
@@ -224,6 +228,13 @@ int upload_consts(g3pcf_plan_t P) {
         return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (constants)");
     CK(cudaMemcpy(P->d_slotconv.p, P->slotconv.data(), P->slotconv.size() * sizeof(int4), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->d_slotcoef.p, P->slotcoef.data(), P->slotcoef.size() * sizeof(float), cudaMemcpyHostToDevice));
+    if (P->d_monoexp.ensure(P->monoexp.size() * sizeof(int)) || P->d_monoconv.ensure(P->monoconv.size() * sizeof(int4)) ||
+        P->d_monoidx.ensure(P->monoidx.size() * sizeof(int)) || P->d_monocoef.ensure(P->monocoef.size() * sizeof(double)))
+        return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (constants)");
+    CK(cudaMemcpy(P->d_monoexp.p, P->monoexp.data(), P->monoexp.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->d_monoconv.p, P->monoconv.data(), P->monoconv.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->d_monoidx.p, P->monoidx.data(), P->monoidx.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->d_monocoef.p, P->monocoef.data(), P->monocoef.size() * sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->d_tiles.p, P->tiles.data(), P->tiles.size() * sizeof(Tile),
                   cudaMemcpyHostToDevice));
     P->consts_uploaded = true;
@@ -336,13 +347,9 @@ void compute_bins(g3pcf_plan_t P) {
 // polynomials of the first kind), k = 0..n.  D follows the monic recurrence
 // D_{l+1} = z D_l - (l^2 - m^2)/(4 l^2 - 1) D_{l-1}; both sides are expanded in
 // powers of z (FP64) and the T_k are peeled off from the top degree down.
-std::vector<double> cheb_coeffs(int m, int n) {
-    std::vector<std::vector<double>> T(n + 1, std::vector<double>(n + 1, 0.0));
-    T[0][0] = 1.0;
-    if (n >= 1) T[1][1] = 1.0;
-    for (int k = 1; k < n; ++k)
-        for (int d = 0; d <= n; ++d)
-            T[k + 1][d] = (d > 0 ? 2.0 * T[k][d - 1] : 0.0) - T[k - 1][d];
+// Powers-of-z coefficients of the monic D_{m+n,m}(z) (degree n), from the
+// recurrence D_{l+1} = z D_l - (l^2 - m^2)/(4 l^2 - 1) D_{l-1}, FP64.
+std::vector<double> monic_poly(int m, int n) {
     std::vector<double> d0(n + 1, 0.0), d1(n + 1, 0.0);
     d0[0] = 1.0;
     if (n >= 1) d1[1] = 1.0;
@@ -355,6 +362,17 @@ std::vector<double> cheb_coeffs(int m, int n) {
         d1 = d2;
         D = d2;
     }
+    return D;
+}
+
+std::vector<double> cheb_coeffs(int m, int n) {
+    std::vector<std::vector<double>> T(n + 1, std::vector<double>(n + 1, 0.0));
+    T[0][0] = 1.0;
+    if (n >= 1) T[1][1] = 1.0;
+    for (int k = 1; k < n; ++k)
+        for (int d = 0; d <= n; ++d)
+            T[k + 1][d] = (d > 0 ? 2.0 * T[k][d - 1] : 0.0) - T[k - 1][d];
+    std::vector<double> D = monic_poly(m, n);
     std::vector<double> c(n + 1, 0.0);
     for (int k = n; k >= 0; --k) {
         c[k] = D[k] / T[k][k];
@@ -423,6 +441,51 @@ void compute_columns(g3pcf_plan_t P) {
                     if (m & 1) kl = -kl;
                     P->slotcoef.push_back((float)(cheb_coeffs(m, nn)[k] * kl));
                 }
+            }
+        colm += (m == 0) ? K : 2 * K;
+    }
+    // monomial basis (Sec. 3.3.2): monomial (a, b, c), a + b + c <= L, in a fixed
+    // order; per (l, m, part) the terms K_lm d_k C(m, j) Re / Im(i^j) of a_lm on
+    // M_{m-j, j, k}
+    P->monoexp.clear();
+    std::vector<int> mindex((L + 1) * (L + 1) * (L + 1), -1);
+    for (int a = 0; a <= L; ++a)
+        for (int bb = 0; a + bb <= L; ++bb)
+            for (int c = 0; a + bb + c <= L; ++c) {
+                mindex[(a * (L + 1) + bb) * (L + 1) + c] = (int)P->monoexp.size();
+                P->monoexp.push_back(a | (bb << 8) | (c << 16));
+            }
+    P->monoconv.assign(NR, int4{0, 0, 0, 0});
+    P->monoidx.clear();
+    P->monocoef.clear();
+    colm = 0;
+    int u = 0;
+    for (int m = 0; m <= L; ++m) {
+        const int K = B * (L + 1 - m);
+        for (int part = 0; part < (m == 0 ? 1 : 2); ++part)
+            for (int l = m; l <= L; ++l) {
+                const double lnN = 0.5 * (std::log((2.0 * l + 1.0) / (4.0 * M_PI)) + lfact(l - m) - lfact(l + m));
+                const double lnLead = lfact(2 * l) - l * std::log(2.0) - lfact(l) - lfact(l - m);
+                double kl = std::exp(lnN + lnLead);
+                if (m & 1) kl = -kl;
+                const std::vector<double> d = monic_poly(m, l - m);
+                const int first = (int)P->monoidx.size();
+                for (int k = 0; k <= l - m; ++k) {
+                    if (d[k] == 0.0) continue;
+                    double binom = 1.0;  // C(m, j)
+                    for (int j = 0; j <= m; ++j) {
+                        if (j > 0) binom = binom * (m - j + 1) / j;
+                        // i^j: 1, i, -1, -i
+                        const int r = j % 4;
+                        double f = 0.0;
+                        if (part == 0 && (r == 0 || r == 2)) f = r == 0 ? 1.0 : -1.0;
+                        if (part == 1 && (r == 1 || r == 3)) f = r == 1 ? 1.0 : -1.0;
+                        if (f == 0.0) continue;
+                        P->monoidx.push_back(mindex[((m - j) * (L + 1) + j) * (L + 1) + k]);
+                        P->monocoef.push_back(kl * d[k] * binom * f);
+                    }
+                }
+                P->monoconv[u++] = int4{first, (int)P->monoidx.size() - first, colm + part * K + (l - m) * B, 0};
             }
         colm += (m == 0) ? K : 2 * K;
     }
@@ -530,6 +593,10 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode
     la.bins = pa.bins;
     // multipoles that will be differentiated take the exact image separations
     la.exact_img = (mode >= 1 || P->exact_alm) ? 1 : 0;
+    la.monoexp = P->d_monoexp.as<int>();
+    la.monoconv = P->d_monoconv.as<int4>();
+    la.monoidx = P->d_monoidx.as<int>();
+    la.monocoef = P->d_monocoef.as<double>();
     if (mode >= 1) {
         la.V = pa.V;
         la.dw = pa.dw;
@@ -583,7 +650,7 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode
             CK(cudaEventRecord(ev[1], st));
             CK(cudaMemsetAsync(la.queue, 0, sizeof(int), st));
             CK(cudaEventRecord(ev[2], st));
-            if (launch_accum(P->lmax, la, P->nsm, st) != 0)
+            if ((P->opt_basis == 1 ? launch_mono(P->lmax, la, P->nsm, st) : launch_accum(P->lmax, la, P->nsm, st)) != 0)
                 return fail(G3PCF_ERR_CUDA, "pair accumulate launch failed: %s", cudaGetErrorString(cudaGetLastError()));
             CK(cudaEventRecord(ev[3], st));
         }
@@ -676,7 +743,9 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode
                 return fail(G3PCF_ERR_CUDA, "adjoint recompute launch failed: %s", cudaGetErrorString(cudaGetLastError()));
             CK(cudaMemsetAsync(la.queue, 0, sizeof(int), st));
         }
-        if ((mode >= 1 ? launch_adj(P->lmax, la, P->nsm, st) : launch_accum(P->lmax, la, P->nsm, st)) != 0)
+        if ((mode >= 1 ? launch_adj(P->lmax, la, P->nsm, st)
+                       : (P->opt_basis == 1 ? launch_mono(P->lmax, la, P->nsm, st)
+                                            : launch_accum(P->lmax, la, P->nsm, st))) != 0)
             return fail(G3PCF_ERR_CUDA, "pair accumulate launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         CK(cudaEventRecord(ev[3], st));
     }
@@ -1390,6 +1459,10 @@ int g3pcf_set_option(g3pcf_plan_t P, int option, int64_t value) {
             if (value < 0 || value > 2) return fail(G3PCF_ERR_ARG, "pair kernels must be 0, 1 or 2");
             P->opt_pair = (int)value;
             return G3PCF_OK;
+        case G3PCF_OPT_BASIS:
+            if (value < 0 || value > 1) return fail(G3PCF_ERR_ARG, "basis must be 0 (Chebyshev) or 1 (monomials)");
+            P->opt_basis = (int)value;
+            return G3PCF_OK;
         case G3PCF_OPT_LIST_BYTES:
             if (value < 0) return fail(G3PCF_ERR_ARG, "list bytes must be >= 0");
             if (value > 0 && value < (int64_t)1 << 20) return fail(G3PCF_ERR_ARG, "list bytes must be >= 1 MiB");
@@ -1555,7 +1628,7 @@ int g3pcf_destroy(g3pcf_plan_t P) {
     DevBuf* bufs[] = {&P->key_a, &P->key_b, &P->val_a, &P->val_b, &P->hist, &P->hist_off,
                       &P->scan_tmp, &P->pts, &P->pts64, &P->orig, &P->cstart, &P->plist,
                       &P->small, &P->counts, &P->A, &P->partials, &P->d_tiles, &P->d_segs,
-                      &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_colconv, &P->d_colcoef, &P->d_bintab_s, &P->d_slotconv, &P->d_slotcoef, &P->d_catoff, &P->d_ranges,
+                      &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_colconv, &P->d_colcoef, &P->d_bintab_s, &P->d_slotconv, &P->d_slotcoef, &P->d_monoexp, &P->d_monoconv, &P->d_monoidx, &P->d_monocoef, &P->d_catoff, &P->d_ranges,
                       &P->d_tiles_tc, &P->ops, &P->d_cats, &P->d_mreal, &P->d_V, &P->d_bintab, &P->d_vblk,
                       &P->wrow, &P->l_need, &P->l_base, &P->l_nch, &P->l_pool, &P->l_tag, &P->l_ord,
                       &P->l_gbase, &P->l_scantmp, &P->l_passq};

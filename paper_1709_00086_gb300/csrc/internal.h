@@ -172,6 +172,12 @@ struct ListArgs {
     int* nchunks;            // [q]
     const int* qrange;       // if set: qa = qrange[0], qb = qrange[1] (device-planned pass)
     int exact_img;           // k_accum: separations from the head + tail of the primary's images
+    // monomial-basis multipoles (k_mono): exponents a | b << 8 | c << 16 per monomial;
+    // per (l, m, part) {first term, terms, A column of bin 0}; terms (monomial, coefficient)
+    const int* monoexp;
+    const int4* monoconv;
+    const int* monoidx;
+    const double* monocoef;
     // adjoint pass (k_adj): V rows (row = original index), slot tables of the
     // transposed Chebyshev connection, outputs (FP64, original order)
     const float* V;
@@ -197,6 +203,9 @@ int launch_plan(const int* need, long long* gbase, long long* tmp, int qa, int q
 int launch_scan(const ListArgs& a, int nsm, cudaStream_t st);
 int launch_accum(int lmax, const ListArgs& a, int nsm, cudaStream_t st);
 int launch_adj(int lmax, const ListArgs& a, int nsm, cudaStream_t st);
+// monomial.cu: the multipoles through the paper's monomial power sums (FP64)
+int mono_count(int lmax);
+int launch_mono(int lmax, const ListArgs& a, int nsm, cudaStream_t st);
 
 // ---- contract.cu -----------------------------------------------------------
 struct Tile {          // one output tile of one m block of C_m = sum_i w_i v_i v_i^T

@@ -295,10 +295,10 @@ __device__ __forceinline__ void row_pieces(int r, int W, int K, int cy, int cz, 
 // of sight (box centre -> primary at x) to +z (radial mode, Sec. 2): with
 // n = unit LOS and v = n x z, R = I + [v]x + [v]x^2 / (1 + n.z); the
 // antiparallel case is the half turn about x.  A primary at the centre keeps I.
-__device__ __forceinline__ float los_rotation_entry(int lane, double x0, double x1, double x2,
-                                                    double boxd) {
+__device__ __forceinline__ double los_rotation_entry_d(int lane, double x0, double x1, double x2,
+                                                       double boxd) {
     const int r = lane / 3, s = lane % 3;
-    float Rv = (r == s) ? 1.f : 0.f;
+    double Rv = (r == s) ? 1.0 : 0.0;
     const double c = 0.5 * boxd;
     double n0 = x0 - c, n1 = x1 - c, n2 = x2 - c;
     const double nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
@@ -307,7 +307,7 @@ __device__ __forceinline__ float los_rotation_entry(int lane, double x0, double 
         n1 /= nn;
         n2 /= nn;
         if (n2 < -1.0 + 1e-12) {
-            Rv = (lane == 0) ? 1.f : ((lane == 4 || lane == 8) ? -1.f : 0.f);
+            Rv = (lane == 0) ? 1.0 : ((lane == 4 || lane == 8) ? -1.0 : 0.0);
         } else {
             const double v0 = n1, v1 = -n0, f = 1.0 / (1.0 + n2);
             // [v]x = [[0, 0, v1], [0, 0, -v0], [-v1, v0, 0]] (v2 = 0)
@@ -319,10 +319,14 @@ __device__ __forceinline__ float los_rotation_entry(int lane, double x0, double 
                                             : 0.0;
             };
             const double k2 = kx(r, 0) * kx(0, s) + kx(r, 1) * kx(1, s) + kx(r, 2) * kx(2, s);
-            Rv = (float)(((r == s) ? 1.0 : 0.0) + kx(r, s) + k2 * f);
+            Rv = ((r == s) ? 1.0 : 0.0) + kx(r, s) + k2 * f;
         }
     }
     return Rv;
+}
+__device__ __forceinline__ float los_rotation_entry(int lane, double x0, double x1, double x2,
+                                                    double boxd) {
+    return (float)los_rotation_entry_d(lane, x0, x1, x2, boxd);
 }
 
 // Cell coordinates of a position (the index build's formula).

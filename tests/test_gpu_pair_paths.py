@@ -90,3 +90,22 @@ def test_list_path_batch_matches_single_calls():
         zo, co = oracle_zeta(cat)
         np.testing.assert_array_equal(cb[k].cpu().numpy(), co)
         assert maxrel(zb[k].cpu().numpy(), zo) < TOL, k
+
+
+@pytest.mark.parametrize("name", ["uniform_f64", "clustered_radial", "bins32"])
+def test_monomial_basis_matches_oracle(name):
+    # the paper's monomial power sums (Sec. 3.3.2), FP64 accumulation and conversion
+    cat = CASES[name]()
+    npri = min(cat.pos.shape[0], 400)
+    plan = g3.Plan(**cat.params())
+    plan.set_option(g3.OPT_BASIS, 1)
+    pos, w = to_dev(cat, torch)
+    z, c = plan.compute(pos, w, n_primary=npri, fp32_contraction=True, keep_alm=True)
+    zo, co = oracle_zeta(cat, n_primary=npri)
+    np.testing.assert_array_equal(c.cpu().numpy(), co)
+    assert maxrel(z.cpu().numpy(), zo) < TOL
+    prims = np.array([0, npri // 3, npri - 1])
+    a = plan.alm(prims)
+    ao = oracle_alm(cat, prims)
+    for k in range(prims.size):
+        assert maxrel(a[k], ao[k]) < TOL, k
