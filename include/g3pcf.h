@@ -77,7 +77,7 @@ enum {
     G3PCF_ERR_CUDA = -5,        /* a CUDA runtime call failed                            */
     G3PCF_ERR_TIMEOUT = -6,     /* a bounded device wait expired (kernel returned early) */
     G3PCF_ERR_STATE = -7,       /* backward/alm without a matching forward on this plan  */
-    G3PCF_ERR_UNSUPPORTED = -8  /* valid request this build does not implement           */
+    G3PCF_ERR_UNSUPPORTED = -8  /* valid request the library does not implement           */
 };
 
 /* Flags for g3pcf_compute_ex / g3pcf_compute_batch. */
@@ -99,7 +99,7 @@ enum {
                                    the graph.                                             */
 };
 
-/* Limits of this build. */
+/* Limits of the library. */
 #define G3PCF_MAX_LMAX 10
 #define G3PCF_MAX_NBINS 32
 #define G3PCF_MAX_POINTS ((int64_t)1 << 27)
