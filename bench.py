@@ -128,6 +128,22 @@ def dist_info():
     return ws, rank, local
 
 
+def max_over_ranks(t: float, device, ws: int) -> float:
+    """The slowest rank's step time (all ranks take part; one rank: t)."""
+    if ws <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(pairs_per_rank: float, ws: int, t_max: float) -> float:
+    """Whole-job pairs/s of ws replicas that each processed pairs_per_rank."""
+    return ws * pairs_per_rank / t_max
+
+
 def make_catalog(args):
     from paper_1709_00086_gb300 import catalogs
     if args.workload == "clustered2m":
@@ -288,13 +304,8 @@ def run_ours(args):
     pairs = st_tc[-1]["pairs"]
     nprim = st_tc[-1]["primaries"]
     t_step = float(np.mean(ms_tc)) / 1e3
-    t_max = t_step
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = ws * pairs / t_max
+    t_max = max_over_ranks(t_step, dev, ws)
+    value = job_value(pairs, ws, t_max)
     pair_ms = float(np.mean([s["pair_ms"] for s in st_tc]))
     con_tc = float(np.mean([s["contract_ms"] for s in st_tc]))
     con_32 = float(np.mean([s["contract_ms"] for s in st_32]))
