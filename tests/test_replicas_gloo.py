@@ -33,7 +33,7 @@ def _rank(rank, ws, port, times, out):
 def test_two_replicas_take_the_slowest_rank():
     ws = 2
     times = [0.25, 0.40]
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork: the parent may hold CUDA state
         out = m.dict()
         mp.spawn(_rank, args=(ws, _free_port(), times, out), nprocs=ws, join=True)
         res = dict(out)
