@@ -240,6 +240,10 @@ int g3pcf_fp32_peak(double* tflops, void* stream);
  *                             G3PCF_ERR_STATE and g3pcf_backward recomputes the
  *                             multipoles chunk by chunk (pair lists only)
  *   G3PCF_OPT_CELLS_PER_RMAX  cell-list resolution s (cell side >= rmax / s, 1..8)
+ *   G3PCF_OPT_X_REFINE        cells are this many times narrower along x than
+ *                             along y and z (1..16; automatic: 8): an x-row of
+ *                             cells is one contiguous slot range, so a finer x step
+ *                             clips each row to the sphere more tightly
  *   G3PCF_OPT_KFLUSH          pairs per lane per bucket flush of the fused pair
  *                             kernel (2..16)
  *   G3PCF_OPT_PAIR_KERNELS    forward pair stage: 1 = the fused kernel (bucket and
@@ -262,7 +266,8 @@ enum {
     G3PCF_OPT_KFLUSH = 3,
     G3PCF_OPT_PAIR_KERNELS = 4,
     G3PCF_OPT_LIST_BYTES = 5,
-    G3PCF_OPT_BASIS = 7
+    G3PCF_OPT_BASIS = 7,
+    G3PCF_OPT_X_REFINE = 8
 };
 int g3pcf_set_option(g3pcf_plan_t plan, int option, int64_t value);
 

@@ -112,6 +112,7 @@ struct g3pcf_plan_s {
     std::vector<long long> gkey;
     cudaEvent_t gev[2] = {};
     int opt_cells = 0;       // G3PCF_OPT_CELLS_PER_RMAX
+    int opt_xref = 0;        // G3PCF_OPT_X_REFINE
     int opt_pair = 0;        // G3PCF_OPT_PAIR_KERNELS
     int64_t opt_list_bytes = 0;  // G3PCF_OPT_LIST_BYTES
     // pair lists (forward, pairlist.cu): per-primary need / base / nchunks,
@@ -254,22 +255,28 @@ Grid choose_grid(g3pcf_plan_t P, double density, int ncat) {
     int nc = (int)std::floor(P->box * s / P->rmax);
     if (nc < 1) nc = 1;
     if (nc > 256) nc = 256;
-    for (;;) {
+    int fx = P->opt_xref > 0 ? P->opt_xref : 8;
+    for (;;) {  // keys stay below 2^31: coarsen x first, then the whole grid
         int span = 1;
         while (span < nc) span <<= 1;
-        long long cpc = (long long)span * span * nc;
-        if ((long long)ncat * cpc < (1ll << 31) || nc == 1) {
+        long long cpc = (long long)span * span * nc * fx;
+        if ((long long)ncat * cpc < (1ll << 31) || (nc == 1 && fx == 1)) {
             g.span = span;
             g.cells_per_cat = cpc;
             break;
         }
-        nc = nc / 2;
+        if (fx > 1)
+            fx = fx / 2;
+        else
+            nc = nc / 2;
     }
     g.nc = nc;
+    g.ncx = nc * fx;
     g.boxd = P->box;
     g.box = (float)P->box;
     g.cell = (float)(P->box / nc);
     g.inv_cell = (float)(nc / P->box);
+    g.inv_cellx = (float)(g.ncx / P->box);
     g.reach = (int)std::ceil(P->rmax * nc / P->box - 1e-9);
     if (g.reach < 1) g.reach = 1;
     g.periodic = (P->los_mode == G3PCF_LOS_Z_PERIODIC);
@@ -1458,6 +1465,10 @@ int g3pcf_set_option(g3pcf_plan_t P, int option, int64_t value) {
         case G3PCF_OPT_PAIR_KERNELS:
             if (value < 0 || value > 2) return fail(G3PCF_ERR_ARG, "pair kernels must be 0, 1 or 2");
             P->opt_pair = (int)value;
+            return G3PCF_OK;
+        case G3PCF_OPT_X_REFINE:
+            if (value < 0 || value > 16) return fail(G3PCF_ERR_ARG, "x refinement must be in [0, 16]");
+            P->opt_xref = (int)value;
             return G3PCF_OK;
         case G3PCF_OPT_BASIS:
             if (value < 0 || value > 1) return fail(G3PCF_ERR_ARG, "basis must be 0 (Chebyshev) or 1 (monomials)");

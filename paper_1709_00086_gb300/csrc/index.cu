@@ -48,9 +48,10 @@ __global__ void k_keys(IndexArgs a, const int64_t* cat_off, int ncat, unsigned* 
             bad = true;
             x[d] = 0.0;
         }
-        float xf = (float)x[d];
-        int cc = (int)(xf * a.g.inv_cell);
-        c[d] = cc < 0 ? 0 : (cc >= a.g.nc ? a.g.nc - 1 : cc);
+        const float xf = (float)x[d];
+        const int n = d == 0 ? a.g.ncx : a.g.nc;
+        const int cc = (int)(xf * (d == 0 ? a.g.inv_cellx : a.g.inv_cell));
+        c[d] = cc < 0 ? 0 : (cc >= n ? n - 1 : cc);
     }
     if (bad) atomicOr(status, kStatusRange);
     long long cat = 0;
@@ -62,7 +63,7 @@ __global__ void k_keys(IndexArgs a, const int64_t* cat_off, int ncat, unsigned* 
         }
         cat = lo;
     }
-    long long k = cat * a.g.cells_per_cat + (long long)morton2(c[1], c[2]) * a.g.nc + c[0];
+    long long k = cat * a.g.cells_per_cat + (long long)morton2(c[1], c[2]) * a.g.ncx + c[0];
     key[i] = (unsigned)k;
     val[i] = (int)i;
 }

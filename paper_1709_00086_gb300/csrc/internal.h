@@ -25,18 +25,22 @@ constexpr int kWarp = 32;
 #define G3_BIN_TABLE 2048
 
 // Cell grid of one compute call.  Key of cell (cx, cy, cz) of catalog c:
-// c * cells_per_cat + morton2(cy, cz) * nc + cx, so that an x-row of cells is a
-// contiguous range of keys and neighbouring rows are close in memory.
+// c * cells_per_cat + morton2(cy, cz) * ncx + cx, so that an x-row of cells is a
+// contiguous range of keys and neighbouring rows are close in memory.  Cells
+// are ncx / nc times narrower along x than along y and z: a row's slot range is
+// clipped to the sphere's chord at the finer x step at no extra lookup cost.
 struct Grid {
     float box;        // L (FP32)
-    float cell;       // L / nc
+    float cell;       // L / nc (y and z)
     float inv_cell;   // nc / L
-    int nc;           // cells per dimension
+    float inv_cellx;  // ncx / L
+    int nc;           // cells per dimension along y and z
+    int ncx;          // cells along x
     int span;         // next power of two >= nc (Morton span of (cy, cz))
-    int reach;        // max |cell offset| that can hold a neighbour
+    int reach;        // max |cell offset| in y or z that can hold a neighbour
     int periodic;
     int radial;
-    long long cells_per_cat;  // span * span * nc
+    long long cells_per_cat;  // span * span * ncx
     double boxd;
 };
 

@@ -266,22 +266,23 @@ __device__ __forceinline__ void row_pieces(int r, int W, int K, int cy, int cz, 
     const float rem = rmax2 - ddy * ddy - ddz * ddz;
     if (rem < 0.f) return;
     const float h = sqrtf(rem) + slack;
-    int xlo = (int)floorf((P0.x - h) * g.inv_cell);
-    int xhi = (int)floorf((P0.x + h) * g.inv_cell);
+    const int nx = g.ncx;
+    int xlo = (int)floorf((P0.x - h) * g.inv_cellx);
+    int xhi = (int)floorf((P0.x + h) * g.inv_cellx);
     if (!g.periodic) {
         xlo = max(xlo, 0);
-        xhi = min(xhi, g.nc - 1);
+        xhi = min(xhi, nx - 1);
     } else {
-        xlo = max(xlo, -g.nc);
-        xhi = min(xhi, 2 * g.nc - 1);
+        xlo = max(xlo, -nx);
+        xhi = min(xhi, 2 * nx - 1);
     }
-    const long long pk = kbase + (long long)morton2(wy, wz) * g.nc;
+    const long long pk = kbase + (long long)morton2(wy, wz) * nx;
     auto piece = [&](int s) {
         int4 v = make_int4(0, 0, 0, 0);
-        const int a0 = max(xlo, s * g.nc), a1 = min(xhi, s * g.nc + g.nc - 1);
+        const int a0 = max(xlo, s * nx), a1 = min(xhi, s * nx + nx - 1);
         if (a0 <= a1 && (g.periodic || s == 0)) {
-            v.x = cstart[pk + (a0 - s * g.nc)];
-            v.y = cstart[pk + (a1 - s * g.nc) + 1];
+            v.x = cstart[pk + (a0 - s * nx)];
+            v.y = cstart[pk + (a1 - s * nx) + 1];
             v.z = (s + 1) + 3 * (sy + 1) + 9 * (sz + 1);
         }
         return v;

@@ -10,11 +10,12 @@
 //               sphere's cell rows; the host turns ceil(candidates/32) + B
 //               into exact, non-overlapping list offsets and into passes that
 //               fit the list pool.
-//   k_scan   -- per primary (one warp), streams the candidates, decides each
-//               pair's bin exactly and appends accepted pairs to a per-bin
-//               staging ring in shared memory; every 32 pairs of a bin leave
-//               as one 128-byte chunk, tagged with its bin, for this primary.
-//               Few registers: many warps hide the candidate loads.
+//   k_scan   -- per primary (one warp), streams the candidates of 32 cell rows
+//               at a time, slot range by slot range, decides each pair's bin
+//               exactly and compacts the accepted pairs into a staging ring in
+//               shared memory; every 32 staged pairs are placed into per-bin
+//               chunks of 32 entries (128 bytes, tagged with the bin) of this
+//               primary.  Few registers: many warps hide the candidate loads.
 //   k_accum  -- per primary (one warp), walks its chunks bin by bin: each
 //               lane takes one pair of a chunk, evaluates Y_lm (FP32
 //               recurrence, pair_common.cuh) into (lmax+1)^2 register
@@ -38,8 +39,9 @@ constexpr int kTrip = 4;        // candidate sub-iterations per trip in k_scan
 constexpr unsigned kNoPair = 0xffffffffu;  // padding entry of a list chunk (image code 31 is unused)
 
 // Per-warp shared memory of k_scan: img[27] float4, pd[4] double,
-// pcs[kMaxPieces] int4, stage[kStage + 32] int2 (accepted pairs: entry, bin;
-// the last 32 are scratch), per-bin fill / open chunk / chunk count.
+// pcs[kMaxPieces] int4 (the slot ranges of a row batch: first, end, image
+// code), stage[kStage + 32] int2 (accepted pairs: entry, bin; the last 32 are
+// scratch), per-bin fill / open chunk / chunk count.
 struct ScanSmem {
     float4* img;
     double* pd;
@@ -93,7 +95,7 @@ __global__ void __launch_bounds__(kLThreads) k_count(ListArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(kLThreads, 6) k_scan(ListArgs a) {
+__global__ void __launch_bounds__(kLThreads, 7) k_scan(ListArgs a) {
     extern __shared__ __align__(16) unsigned char ls_raw[];
     __shared__ double s_e2[kMaxBins + 1];
     __shared__ float2 s_dec[kMaxBins];
