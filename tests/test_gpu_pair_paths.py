@@ -109,3 +109,42 @@ def test_monomial_basis_matches_oracle(name):
     ao = oracle_alm(cat, prims)
     for k in range(prims.size):
         assert maxrel(a[k], ao[k]) < TOL, k
+
+
+@pytest.mark.parametrize("name", ["uniform_f64", "clustered_open", "clustered_radial"])
+@pytest.mark.parametrize("xref", [1, 3, 16])
+def test_x_refinement_matches_oracle(name, xref):
+    # cells 1, 3 or 16 times narrower along x than along y and z: the slot
+    # ranges change, the pair decisions must not
+    cat = CASES[name]()
+    npri = min(cat.pos.shape[0], 500)
+    plan = g3.Plan(**cat.params())
+    plan.set_option(g3.OPT_X_REFINE, xref)
+    pos, w = to_dev(cat, torch)
+    z, c = plan.compute(pos, w, n_primary=npri, fp32_contraction=True)
+    zo, co = oracle_zeta(cat, n_primary=npri)
+    np.testing.assert_array_equal(c.cpu().numpy(), co)
+    assert maxrel(z.cpu().numpy(), zo) < TOL
+
+
+def test_cell_keys_at_their_limit():
+    # 16 catalogs on a 256^3 grid (s = 8, rmax = box / 32): with the default x
+    # refinement of 8 the cell keys would reach 2^31, so the grid takes a
+    # coarser x step (16 * 256^3 * 4 cells, a 4.3 GB cell-start table)
+    box, rmax = 1000.0, 31.25
+    cats = []
+    for c in range(16):
+        rng = np.random.default_rng([49, c])
+        pos = catalogs.uniform_positions(rng, 4000, box, np.float32)
+        cats.append(catalogs.Catalog(pos, catalogs.weights(rng, 4000), box, 4, 2.0, rmax, 2, 0))
+    plan = g3.Plan(**cats[0].params())
+    plan.set_option(g3.OPT_CELLS_PER_RMAX, 8)
+    pos = torch.from_numpy(np.concatenate([c.pos for c in cats])).cuda()
+    w = torch.from_numpy(np.concatenate([c.w for c in cats])).cuda()
+    offs = np.cumsum([0] + [c.n for c in cats])
+    zb, cb = plan.compute_batch(pos, w, offs, fp32_contraction=True)
+    assert plan.stats()["cells_per_rmax"] == 8.0
+    for k in (0, 7, 15):
+        zo, co = oracle_zeta(cats[k])
+        np.testing.assert_array_equal(cb[k].cpu().numpy(), co)
+        assert maxrel(zb[k].cpu().numpy(), zo) < TOL, k
