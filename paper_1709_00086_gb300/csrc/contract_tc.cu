@@ -297,18 +297,23 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
 // product.  pr is the padded primary position: catalog c occupies
 // [cats[c].x, cats[c].x + cats[c].z) with its rows starting at cats[c].y,
 // and every catalog starts on a multiple of kKB; the gaps are written as 0.
-__global__ void k_split(const float* __restrict__ A, int RLP, int RL, const float* __restrict__ w,
-                        const int4* __restrict__ cats, int ncat, int64_t P_pad,
-                        __nv_bfloat16* Lh, __nv_bfloat16* Ll, __nv_bfloat16* Rh,
-                        __nv_bfloat16* Rl) {
-    __shared__ float tl[32][33];
-    __shared__ float tw[32];
-    __shared__ int trow[32];
-    const int64_t p0 = (int64_t)blockIdx.x * 32;  // padded primary positions
-    const int c0 = blockIdx.y * 32;               // A columns
+// One block per kSplitP = 64 padded primaries sweeps all columns in tiles of
+// 32 (rows read as 128-byte lines, each column written as one 128-byte line
+// of bf16 pairs per operand), so the pass streams at memory speed instead of
+// paying a block per 32 x 32 tile.
+constexpr int kSplitP = 64;
+
+__global__ void __launch_bounds__(256) k_split(const float* __restrict__ A, int RLP, int RL,
+                                               const float* __restrict__ w, const int4* __restrict__ cats,
+                                               int ncat, int64_t P_pad, __nv_bfloat16* Lh, __nv_bfloat16* Ll,
+                                               __nv_bfloat16* Rh, __nv_bfloat16* Rl) {
+    __shared__ float tl[kSplitP][33];
+    __shared__ float tw[kSplitP];
+    __shared__ int trow[kSplitP];
+    const int64_t p0 = (int64_t)blockIdx.x * kSplitP;  // padded primary positions
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-    if (ty == 0) {
-        const int64_t pr = p0 + tx;
+    if (threadIdx.x < kSplitP) {
+        const int64_t pr = p0 + threadIdx.x;
         int lo = 0, hi = ncat - 1;  // last catalog starting at or before pr
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -316,28 +321,38 @@ __global__ void k_split(const float* __restrict__ A, int RLP, int RL, const floa
         }
         const int4 ct = cats[lo];
         const int64_t k = pr - ct.x;
-        trow[tx] = (pr < P_pad && k >= 0 && k < ct.z) ? (int)(ct.y + k) : -1;
+        const int r = (pr < P_pad && k >= 0 && k < ct.z) ? (int)(ct.y + k) : -1;
+        trow[threadIdx.x] = r;
+        tw[threadIdx.x] = r >= 0 ? w[r] : 0.f;
     }
     __syncthreads();
-    for (int k = ty; k < 32; k += 8) {
-        const int r = trow[k];
-        const int c = c0 + tx;
-        tl[k][tx] = (r >= 0 && c < RL) ? A[(int64_t)r * RLP + c] : 0.f;
-    }
-    if (ty == 0) tw[tx] = trow[tx] >= 0 ? w[trow[tx]] : 0.f;
-    __syncthreads();
-    for (int k = ty; k < 32; k += 8) {
-        const int c = c0 + k;
-        const int64_t pr = p0 + tx;
-        if (c >= RL || pr >= P_pad) continue;
-        const float x = tl[tx][k];
-        const float y = x * tw[tx];
-        const __nv_bfloat16 xh = __float2bfloat16_rn(x), yh = __float2bfloat16_rn(y);
-        const int64_t o = (int64_t)c * P_pad + pr;
-        Lh[o] = xh;
-        Ll[o] = __float2bfloat16_rn(x - __bfloat162float(xh));
-        Rh[o] = yh;
-        Rl[o] = __float2bfloat16_rn(y - __bfloat162float(yh));
+    for (int c0 = 0; c0 < RL; c0 += 32) {
+        for (int k = ty; k < kSplitP; k += 8) {  // primary k, columns c0 .. c0 + 31
+            const int r = trow[k];
+            const int c = c0 + tx;
+            tl[k][tx] = (r >= 0 && c < RL) ? A[(int64_t)r * RLP + c] : 0.f;
+        }
+        __syncthreads();
+        for (int k = ty; k < 32; k += 8) {  // column c0 + k, primaries 2 tx and 2 tx + 1
+            const int c = c0 + k;
+            const int64_t pr = p0 + 2 * tx;
+            if (c < RL && pr < P_pad) {
+                const float x0 = tl[2 * tx][k], x1 = tl[2 * tx + 1][k];
+                const float y0 = x0 * tw[2 * tx], y1 = x1 * tw[2 * tx + 1];
+                const __nv_bfloat16 xh0 = __float2bfloat16_rn(x0), xh1 = __float2bfloat16_rn(x1);
+                const __nv_bfloat16 yh0 = __float2bfloat16_rn(y0), yh1 = __float2bfloat16_rn(y1);
+                const int64_t o = (int64_t)c * P_pad + pr;
+                *reinterpret_cast<__nv_bfloat162*>(Lh + o) = __halves2bfloat162(xh0, xh1);
+                *reinterpret_cast<__nv_bfloat162*>(Ll + o) =
+                    __halves2bfloat162(__float2bfloat16_rn(x0 - __bfloat162float(xh0)),
+                                       __float2bfloat16_rn(x1 - __bfloat162float(xh1)));
+                *reinterpret_cast<__nv_bfloat162*>(Rh + o) = __halves2bfloat162(yh0, yh1);
+                *reinterpret_cast<__nv_bfloat162*>(Rl + o) =
+                    __halves2bfloat162(__float2bfloat16_rn(y0 - __bfloat162float(yh0)),
+                                       __float2bfloat16_rn(y1 - __bfloat162float(yh1)));
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -377,9 +392,8 @@ int launch_split(const float* A, int RLP, int RL, const float* w, const int4* ca
     if (P_pad <= 0) return 0;
     __nv_bfloat16* base = static_cast<__nv_bfloat16*>(ops);
     const int64_t n1 = (int64_t)RL * P_pad;
-    dim3 grid((unsigned)((P_pad + 31) / 32), (unsigned)((RL + 31) / 32));
-    k_split<<<grid, 256, 0, st>>>(A, RLP, RL, w, cats, ncat, P_pad, base, base + n1, base + 2 * n1,
-                                  base + 3 * n1);
+    k_split<<<(unsigned)((P_pad + kSplitP - 1) / kSplitP), 256, 0, st>>>(A, RLP, RL, w, cats, ncat, P_pad, base,
+                                                                         base + n1, base + 2 * n1, base + 3 * n1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
