@@ -175,12 +175,13 @@ int g3pcf_autotune(g3pcf_plan_t plan, const void* pos, const float* w, int64_t n
 int g3pcf_status(g3pcf_plan_t plan);
 
 /* Per-stage device times (milliseconds, CUDA events) and counters of the last
- * compute call: [0] index build, [1] pair stage, [2] contraction, [3] reduction,
- * [4] total, [5] accepted pairs (as a double), [6] primaries, [7] cells per
- * Rmax used, [8] kernels launched by the call, [9] candidate secondaries
- * visited (pair-list path; 0 for the fused kernel), [10] passes of the pair
- * lists, [11] and [12] summed device times (ms) of the list scan and
- * accumulate kernels, [13] accumulate launches.  Synchronises the stream.
+ * compute call: [0] index build, [1] pair stage, [2] contraction (both summed
+ * over the chunks of primaries of a chunked call), [3] reduction, [4] total,
+ * [5] accepted pairs (as a double), [6] primaries, [7] cells per Rmax used,
+ * [8] kernels launched by the call, [9] candidate secondaries visited
+ * (pair-list path; 0 for the fused kernel), [10] passes of the pair lists,
+ * [11] and [12] summed device times (ms) of the list scan and accumulate
+ * kernels, [13] accumulate launches.  Synchronises the stream.
  * At most min(nvals, 14) values are written. */
 int g3pcf_stats(g3pcf_plan_t plan, double* vals, int nvals);
 

@@ -132,6 +132,9 @@ struct g3pcf_plan_s {
     // events around every k_scan / k_accum launch of the last forward (4 per pass)
     std::vector<cudaEvent_t> lev;
     int lev_used = 0;
+    // per chunk of primaries: pair stage done, contraction done (stats [1], [2])
+    std::vector<cudaEvent_t> cev;
+    int cev_used = 0;
     bool last_chunked = false;
     std::vector<unsigned char> bintab;  // r^2 -> bin lookup (see compute_bins)
     std::vector<signed char> bintab_s;  // signed form (pair-list scan)
@@ -780,6 +783,7 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
         P->gl_events = 0;
     }
     P->stage_off = 0;
+    P->cev_used = 0;
     CK(cudaEventRecord(P->ev[0], st));
     // zero outputs and counters
     if (ensure(P->small, 256, "status")) return G3PCF_ERR_ALLOC;
@@ -970,8 +974,16 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
                 return G3PCF_ERR_ALLOC;
             UP(P->d_segfirst.p, segfirst.data(), 4 * (c.ncat + 1));
         }
-        float pair_ms_acc = 0.f;
-        (void)pair_ms_acc;
+        // per-chunk stage events (created outside a capture; a capture that finds
+        // too few keeps the single-span timing)
+        P->cev_used = 0;
+        if (!P->capturing)
+            while ((int64_t)P->cev.size() < 2 * nchunks) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e));
+                P->cev.push_back(e);
+            }
+        const bool chunk_events = (int64_t)P->cev.size() >= 2 * nchunks;
         int seg_base = 0;
         for (int64_t ch = 0; ch < nchunks; ++ch) {
             const int64_t q0 = ch * C, q1 = chunked ? std::min(rows_all, q0 + C) : nprim;
@@ -1012,6 +1024,7 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
                 }
             }
             if (ch == 0) CK(cudaEventRecord(P->ev[2], st));
+            if (chunk_events) CK(cudaEventRecord(P->cev[2 * ch], st));
             const std::vector<Segment>& segs = csegs[ch];
             const int nsegs = (int)segs.size();
             if (nsegs > 0) {
@@ -1037,7 +1050,9 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
                 }
             }
             seg_base += nsegs;
+            if (chunk_events) CK(cudaEventRecord(P->cev[2 * ch + 1], st));
         }
+        if (chunk_events) P->cev_used = (int)(2 * nchunks);
         CK(cudaEventRecord(P->ev[3], st));
         if (total_segs > 0) {
             P->launches += 1;
@@ -1590,10 +1605,22 @@ int g3pcf_stats(g3pcf_plan_t P, double* vals, int nvals) {
         float ms;
         CK(cudaEventElapsedTime(&ms, P->ev[0], P->ev[1]));
         P->stats[0] = ms;
-        CK(cudaEventElapsedTime(&ms, P->ev[1], P->ev[2]));
-        P->stats[1] = ms;
-        CK(cudaEventElapsedTime(&ms, P->ev[2], P->ev[3]));
-        P->stats[2] = ms;
+        if (P->cev_used > 0) {  // summed over the chunks of primaries
+            double pair = 0.0, con = 0.0;
+            for (int k = 0; k + 1 < P->cev_used; k += 2) {
+                CK(cudaEventElapsedTime(&ms, k == 0 ? P->ev[1] : P->cev[k - 1], P->cev[k]));
+                pair += ms;
+                CK(cudaEventElapsedTime(&ms, P->cev[k], P->cev[k + 1]));
+                con += ms;
+            }
+            P->stats[1] = pair;
+            P->stats[2] = con;
+        } else {
+            CK(cudaEventElapsedTime(&ms, P->ev[1], P->ev[2]));
+            P->stats[1] = ms;
+            CK(cudaEventElapsedTime(&ms, P->ev[2], P->ev[3]));
+            P->stats[2] = ms;
+        }
         CK(cudaEventElapsedTime(&ms, P->ev[3], P->ev[4]));
         P->stats[3] = ms;
         CK(cudaEventElapsedTime(&ms, P->ev[0], P->ev[4]));
@@ -1655,6 +1682,7 @@ int g3pcf_destroy(g3pcf_plan_t P) {
     for (auto& e : P->ev)
         if (e) cudaEventDestroy(e);
     for (auto& e : P->lev) cudaEventDestroy(e);
+    for (auto& e : P->cev) cudaEventDestroy(e);
     delete P;
     return G3PCF_OK;
 }

@@ -210,3 +210,9 @@ def test_chunked_passes_match_single_pass(tc):
     with pytest.raises(g3.G3PCFError) as ei:
         plan.alm([0])
     assert ei.value.name == "ERR_STATE"
+    # stage times of a chunked call are summed over its chunks: they add up to
+    # the total, and the pair stage holds every list scan and accumulate
+    st = plan.stats()
+    parts = st["index_ms"] + st["pair_ms"] + st["contract_ms"] + st["reduce_ms"]
+    assert abs(parts - st["total_ms"]) <= 0.02 * st["total_ms"] + 0.05
+    assert st["pair_ms"] >= st["scan_ms"] + st["accum_ms"]
