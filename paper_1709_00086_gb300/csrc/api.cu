@@ -1034,11 +1034,12 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
                     UP(P->d_cats.p, ccats[ch].data(), 4 * ccats[ch].size());
                     P->launches += 2;
                     if (launch_split(P->A.as<float>(), P->RLP, P->RL, P->wrow.as<float>(), P->d_cats.as<int4>(),
-                                     (int)(ccats[ch].size() / 4), cpad[ch], P->ops.p, st) != 0)
+                                     (int)(ccats[ch].size() / 4), cpad[ch], d_status + kNegWeightSlot, P->ops.p,
+                                     st) != 0)
                         return fail(G3PCF_ERR_CUDA, "operand split launch failed: %s", cudaGetErrorString(cudaGetLastError()));
                     const int rc = launch_contract_tc(P->ops.p, cpad[ch], P->RL, d_tl, ntiles,
                                                       P->d_segs.as<Segment>(), nsegs, part, part_stride,
-                                                      d_status, st);
+                                                      d_status + kNegWeightSlot, d_status, st);
                     if (rc == -2) return fail(G3PCF_ERR_CUDA, "cuTensorMapEncodeTiled unavailable or failed");
                     if (rc != 0)
                         return fail(G3PCF_ERR_CUDA, "tensor-core contraction launch failed: %s", cudaGetErrorString(cudaGetLastError()));

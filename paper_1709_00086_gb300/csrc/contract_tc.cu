@@ -9,9 +9,10 @@
 // Precision.  Each FP32 operand x is split into x_hi = bf16(x) and
 // x_lo = bf16(x - x_hi); C = L_hi R_hi^T + L_hi R_lo^T + L_lo R_hi^T with FP32
 // accumulation in tensor memory (the lo*lo product, ~2^-16 relative, is
-// dropped).  L = A (unweighted), R = w (.) A.
+// dropped).  With no negative weight L = R = sqrt(w) (.) A, so one hi / lo
+// pair serves both sides; otherwise L = A (unweighted) and R = w (.) A.
 //
-// Data flow.  k_split writes the four operands K-major (primaries contiguous)
+// Data flow.  k_split writes the operands K-major (primaries contiguous)
 // as bf16 [column][primary].  k_contract_tc: one CTA per (128 x 128 output
 // tile, segment of primaries); one thread issues TMA tile loads (128B
 // swizzle, 3-stage mbarrier ring) and the tcgen05.mma instructions, the
@@ -117,6 +118,7 @@ struct TcArgs {
     const Segment* segs;   // row ranges in padded primary coordinates (multiples of kKB)
     double* partials;      // per (segment, tile): 128 x 128 doubles, column-major [c][r]
     int part_stride;
+    const int* negw;       // 0: the right operands are the left ones (sqrt(w) A both sides)
     int* status;
 };
 
@@ -189,6 +191,9 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
             const int xrow = t.col0 + t.r0;  // first operand row (A column) of the tile's rows
             const int xcol = t.col0 + t.c0;  // ... of the tile's columns
             const unsigned idesc = make_idesc(kTT, kTT);
+            const bool sym = *a.negw == 0;   // no negative weight: R = L = split(sqrt(w) A)
+            const CUtensorMap* mrh = sym ? &mLh : &mRh;
+            const CUtensorMap* mrl = sym ? &mLl : &mRl;
             bool ok = true;
             int issued = 0;
             auto issue_load = [&](int kb) {
@@ -198,8 +203,8 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
                 mbar_expect_tx(full0 + 8 * s, kStageBytes);
                 tma_load_2d(st + 0 * kOpBytes, &mLh, x, xrow, full0 + 8 * s);
                 tma_load_2d(st + 1 * kOpBytes, &mLl, x, xrow, full0 + 8 * s);
-                tma_load_2d(st + 2 * kOpBytes, &mRh, x, xcol, full0 + 8 * s);
-                tma_load_2d(st + 3 * kOpBytes, &mRl, x, xcol, full0 + 8 * s);
+                tma_load_2d(st + 2 * kOpBytes, mrh, x, xcol, full0 + 8 * s);
+                tma_load_2d(st + 3 * kOpBytes, mrl, x, xcol, full0 + 8 * s);
             };
             for (; issued < kStages && issued < nkb; ++issued) issue_load(issued);
             for (int kb = 0; kb < nkb && ok; ++kb) {
@@ -299,17 +304,21 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
 // and every catalog starts on a multiple of kKB; the gaps are written as 0.
 // One block per kSplitP = 64 padded primaries sweeps all columns in tiles of
 // 32 (rows read as 128-byte lines, each column written as one 128-byte line
-// of bf16 pairs per operand), so the pass streams at memory speed instead of
-// paying a block per 32 x 32 tile.
+// of bf16 pairs per operand).
+// With no negative weight (*negw == 0) both sides of w_i a a^T are sqrt(w_i) a,
+// so only its hi / lo pair is written (Lh, Ll; the contraction reads them for
+// both sides); otherwise L = A and R = w A as four arrays.
 constexpr int kSplitP = 64;
 
 __global__ void __launch_bounds__(256) k_split(const float* __restrict__ A, int RLP, int RL,
                                                const float* __restrict__ w, const int4* __restrict__ cats,
-                                               int ncat, int64_t P_pad, __nv_bfloat16* Lh, __nv_bfloat16* Ll,
-                                               __nv_bfloat16* Rh, __nv_bfloat16* Rl) {
+                                               int ncat, int64_t P_pad, const int* __restrict__ negw,
+                                               __nv_bfloat16* Lh, __nv_bfloat16* Ll, __nv_bfloat16* Rh,
+                                               __nv_bfloat16* Rl) {
     __shared__ float tl[kSplitP][33];
     __shared__ float tw[kSplitP];
     __shared__ int trow[kSplitP];
+    const bool sym = *negw == 0;
     const int64_t p0 = (int64_t)blockIdx.x * kSplitP;  // padded primary positions
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
     if (threadIdx.x < kSplitP) {
@@ -323,7 +332,8 @@ __global__ void __launch_bounds__(256) k_split(const float* __restrict__ A, int 
         const int64_t k = pr - ct.x;
         const int r = (pr < P_pad && k >= 0 && k < ct.z) ? (int)(ct.y + k) : -1;
         trow[threadIdx.x] = r;
-        tw[threadIdx.x] = r >= 0 ? w[r] : 0.f;
+        const float wr = r >= 0 ? w[r] : 0.f;
+        tw[threadIdx.x] = sym ? sqrtf(wr) : wr;
     }
     __syncthreads();
     for (int c0 = 0; c0 < RL; c0 += 32) {
@@ -336,7 +346,15 @@ __global__ void __launch_bounds__(256) k_split(const float* __restrict__ A, int 
         for (int k = ty; k < 32; k += 8) {  // column c0 + k, primaries 2 tx and 2 tx + 1
             const int c = c0 + k;
             const int64_t pr = p0 + 2 * tx;
-            if (c < RL && pr < P_pad) {
+            if (c < RL && pr < P_pad && sym) {
+                const float y0 = tl[2 * tx][k] * tw[2 * tx], y1 = tl[2 * tx + 1][k] * tw[2 * tx + 1];
+                const __nv_bfloat16 yh0 = __float2bfloat16_rn(y0), yh1 = __float2bfloat16_rn(y1);
+                const int64_t o = (int64_t)c * P_pad + pr;
+                *reinterpret_cast<__nv_bfloat162*>(Lh + o) = __halves2bfloat162(yh0, yh1);
+                *reinterpret_cast<__nv_bfloat162*>(Ll + o) =
+                    __halves2bfloat162(__float2bfloat16_rn(y0 - __bfloat162float(yh0)),
+                                       __float2bfloat16_rn(y1 - __bfloat162float(yh1)));
+            } else if (c < RL && pr < P_pad) {
                 const float x0 = tl[2 * tx][k], x1 = tl[2 * tx + 1][k];
                 const float y0 = x0 * tw[2 * tx], y1 = x1 * tw[2 * tx + 1];
                 const __nv_bfloat16 xh0 = __float2bfloat16_rn(x0), xh1 = __float2bfloat16_rn(x1);
@@ -388,18 +406,18 @@ int contract_tile_dim_tc() { return kTT; }
 int contract_tc_kblock() { return kKB; }
 
 int launch_split(const float* A, int RLP, int RL, const float* w, const int4* cats, int ncat,
-                 int64_t P_pad, void* ops, cudaStream_t st) {
+                 int64_t P_pad, const int* negw, void* ops, cudaStream_t st) {
     if (P_pad <= 0) return 0;
     __nv_bfloat16* base = static_cast<__nv_bfloat16*>(ops);
     const int64_t n1 = (int64_t)RL * P_pad;
-    k_split<<<(unsigned)((P_pad + kSplitP - 1) / kSplitP), 256, 0, st>>>(A, RLP, RL, w, cats, ncat, P_pad, base,
-                                                                         base + n1, base + 2 * n1, base + 3 * n1);
+    k_split<<<(unsigned)((P_pad + kSplitP - 1) / kSplitP), 256, 0, st>>>(A, RLP, RL, w, cats, ncat, P_pad, negw,
+                                                                         base, base + n1, base + 2 * n1, base + 3 * n1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int launch_contract_tc(const void* ops, int64_t P_pad, int RL, const Tile* tiles, int ntiles,
                        const Segment* segs, int nsegs, double* partials, int part_stride,
-                       int* status, cudaStream_t st) {
+                       const int* negw, int* status, cudaStream_t st) {
     if (ntiles <= 0 || nsegs <= 0) return 0;
     const __nv_bfloat16* base = static_cast<const __nv_bfloat16*>(ops);
     const int64_t n1 = (int64_t)RL * P_pad;
@@ -410,7 +428,7 @@ int launch_contract_tc(const void* ops, int64_t P_pad, int RL, const Tile* tiles
     if (cudaFuncSetAttribute(k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
         cudaSuccess)
         return -1;
-    TcArgs a{tiles, segs, partials, part_stride, status};
+    TcArgs a{tiles, segs, partials, part_stride, negw, status};
     dim3 grid(ntiles, nsegs);
     k_contract_tc<<<grid, kTcWarps * 32, smem, st>>>(m[0], m[1], m[2], m[3], a);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;

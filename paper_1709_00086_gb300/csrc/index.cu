@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
 
 // ---- sorted arrays, cell starts, primary list -------------------------------
 
-__global__ void k_gather(IndexArgs a, const int* val, float4* pts, double* pts64, int* orig) {
+__global__ void k_gather(IndexArgs a, const int* val, float4* pts, double* pts64, int* orig, int* negw) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= a.n) return;
     int i = val[p];
@@ -227,6 +227,7 @@ __global__ void k_gather(IndexArgs a, const int* val, float4* pts, double* pts64
         if (!(x[d] >= 0.0 && x[d] < a.g.boxd)) x[d] = 0.0;  // flagged in k_keys
     float w = a.w[i];
     if (!isfinite(w)) w = 0.f;
+    if (w < 0.f) *negw = 1;
     pts[p] = make_float4((float)x[0], (float)x[1], (float)x[2], w);
     if (pts64) {
         pts64[3 * p + 0] = x[0];
@@ -308,7 +309,7 @@ int build_index(IndexBuffers& b, const IndexArgs& a, const int64_t* cat_off_dev,
         int* tv = vin; vin = vout; vout = tv;
     }
     b.key_sorted = kin;
-    k_gather<<<grid_of(n, T), T, 0, st>>>(a, vin, b.pts, b.pts64, b.orig);
+    k_gather<<<grid_of(n, T), T, 0, st>>>(a, vin, b.pts, b.pts64, b.orig, b.status + kNegWeightSlot);
     k_cell_start<<<(int)((ncells + 1 + T - 1) / T), T, 0, st>>>(kin, n, ncells, b.cstart);
     launches += 3;
     // primary list

@@ -232,11 +232,14 @@ int launch_isotropic(const double* zeta, int nbins, int lmax, int ncat, double* 
 // contract_tc.cu: split-BF16 tcgen05 contraction
 int contract_tile_dim_tc();
 int contract_tc_kblock();
+// negw: the status block's negative-weight flag (kNegWeightSlot), read on the
+// device: 0 -> both operand sides are hi/lo of sqrt(w) A (two arrays written);
+// else the left side is hi/lo of A and the right side hi/lo of w A (four).
 int launch_split(const float* A, int RLP, int RL, const float* w, const int4* cats, int ncat,
-                 int64_t P_pad, void* ops, cudaStream_t st);
+                 int64_t P_pad, const int* negw, void* ops, cudaStream_t st);
 int launch_contract_tc(const void* ops, int64_t P_pad, int RL, const Tile* tiles, int ntiles,
                        const Segment* segs, int nsegs, double* partials, int part_stride,
-                       int* status, cudaStream_t st);
+                       const int* negw, int* status, cudaStream_t st);
 
 // ---- adjoint.cu ----------------------------------------------------------------
 size_t adjoint_m_floats(int nbins, int lmax);
@@ -259,6 +262,11 @@ int launch_vgemm_rows(const float* A, int RLP, int RL, int64_t row_lo, int64_t r
 void set_last_error(const char* msg);
 int noalloc_zeta_from_alm(int nbins, int lmax, const float* alm, int64_t ld, const float* w,
                           int64_t np, double* zeta, cudaStream_t st, char* err, size_t errlen);
+
+// Status block of a call (256 bytes, zeroed per call): int [0] status word,
+// [16] work counter, [20] set by the index build when a weight is negative,
+// [24..25] candidate count (64-bit).
+constexpr int kNegWeightSlot = 20;
 
 // status bits written by kernels
 enum : int {
