@@ -64,8 +64,12 @@ def _load():
         lib.orc_zeta_triplets.argtypes = [P, P, I64, D, I, I, D, D, I, P]
         lib.orc_iso_legendre.argtypes = [P, P, I64, D, I, I, D, D, I, P]
         lib.orc_grad.argtypes = [P, P, I64, D, I, I, D, D, I, P, P, P, I]
+        lib.orc_mono_count.restype = I64
+        lib.orc_mono_count.argtypes = [I]
+        lib.orc_alm_monomial.argtypes = [P, P, I64, P, I64, D, I, I, D, D, I, P, I]
         for f in ("orc_edges", "orc_ylm", "orc_ylm_grad", "orc_alm", "orc_zeta",
-                  "orc_zeta_from_alm", "orc_zeta_triplets", "orc_iso_legendre", "orc_grad"):
+                  "orc_zeta_from_alm", "orc_zeta_triplets", "orc_iso_legendre", "orc_grad",
+                  "orc_alm_monomial"):
             getattr(lib, f).restype = I
         _lib = lib
     return _lib
@@ -141,6 +145,25 @@ def alm(pos, w, primaries, box, nbins, rmin, rmax, lmax, los_mode=0, nthreads=0,
     if rc != 0:
         raise ValueError("orc_alm failed (%d)" % rc)
     return (out, counts) if return_counts else out
+
+
+def mono_count(lmax):
+    """Number of monomial power sums x^a y^b z^c with a + b + c <= lmax (Sec. 3.3.2)."""
+    return int(_load().orc_mono_count(lmax))
+
+
+def alm_monomial(pos, w, primaries, box, nbins, rmin, rmax, lmax, los_mode=0, nthreads=0):
+    """Per-primary multipoles through the paper's monomial power sums (Sec. 3.3.2):
+    per bin M_abc = sum_j w_j xhat^a yhat^b zhat^c, a + b + c <= lmax, converted
+    with the expansion of Y_lm in those monomials.  Same layout as ``alm``."""
+    pos, w = _f64(pos), _f64(w)
+    prim = np.ascontiguousarray(primaries, dtype=np.int64)
+    out = np.zeros((prim.size, nbins, nlm(lmax)), dtype=np.complex128)
+    rc = _load().orc_alm_monomial(_ptr(pos), _ptr(w), pos.shape[0], _ptr(prim), prim.size, box,
+                                  los_mode, nbins, rmin, rmax, lmax, _ptr(out), nthreads)
+    if rc != 0:
+        raise ValueError("orc_alm_monomial failed (%d)" % rc)
+    return out
 
 
 def zeta(pos, w, box, nbins, rmin, rmax, lmax, los_mode=0, n_primary=None, nthreads=0,

@@ -29,6 +29,11 @@
 //   * gradient     of L = sum over all stored entries |zeta - zeta_t|^2 with the
 //                  pair set and bins frozen (not in the paper; the adjoint's
 //                  definition)
+//   * monomials    the paper's own route to a_lm (Sec. 3.3.2): per primary and
+//                  bin the power sums M_abc = sum_j w_j xhat^a yhat^b zhat^c over
+//                  a + b + c <= lmax ((lmax+1)(lmax+2)(lmax+3)/6 of them, 286 at
+//                  lmax = 10), then a_lm = sum_abc C^lm_abc M_abc with the
+//                  expansion of Y_lm in those monomials
 //
 // Output layout of zeta: for m = 0..lmax a K_m x K_m complex block, K_m =
 // B*(lmax+1-m), row (l-m)*B + b1, column (l'-m)*B + b2, (re, im) interleaved.
@@ -252,6 +257,111 @@ void zeta_accumulate(int nbins, int lmax, const cplx* alm, double wi, cplx* zeta
     }
 }
 
+// ---- the monomial route (Sec. 3.3.2) -------------------------------------
+
+// Monomials xhat^a yhat^b zhat^c with a + b + c <= lmax, enumerated by degree
+// n = a + b + c, then a descending, then b descending.
+struct Monomials {
+    std::vector<int> a, b, c;
+    std::vector<int> index;  // (a * (L+1) + b) * (L+1) + c -> position, -1 if none
+    int L;
+    explicit Monomials(int lmax) : L(lmax) {
+        index.assign((size_t)(L + 1) * (L + 1) * (L + 1), -1);
+        for (int n = 0; n <= L; ++n)
+            for (int ia = n; ia >= 0; --ia)
+                for (int ib = n - ia; ib >= 0; --ib) {
+                    const int ic = n - ia - ib;
+                    index[((size_t)ia * (L + 1) + ib) * (L + 1) + ic] = (int)a.size();
+                    a.push_back(ia);
+                    b.push_back(ib);
+                    c.push_back(ic);
+                }
+    }
+    int count() const { return (int)a.size(); }
+    int at(int ia, int ib, int ic) const { return index[((size_t)ia * (L + 1) + ib) * (L + 1) + ic]; }
+};
+
+double binom(int n, int k) {
+    double r = 1.0;
+    for (int t = 1; t <= k; ++t) r = r * (n - k + t) / t;
+    return r;
+}
+
+// Y_lm on the unit sphere as a polynomial in (xhat, yhat, zhat):
+//   Y_lm = N_lm (-1)^m P_l^(m)(zhat) (xhat + i yhat)^m,
+// P_l^(m) the m-th derivative of the Legendre polynomial (so that N_lm (-1)^m
+// (1 - z^2)^(m/2) P_l^(m) is the orthonormal associated Legendre function with
+// the Condon-Shortley phase, and sin^m(theta) e^(i m phi) = (xhat + i yhat)^m),
+// P_l(z) = 2^-l sum_j (-1)^j C(l, j) C(2l - 2j, l) z^(l - 2j).  Returns, per
+// (l, m) in lm_index order, the list of (monomial, complex coefficient).
+std::vector<std::vector<std::pair<int, cplx>>> ylm_monomial_coefficients(const Monomials& M) {
+    const int L = M.L;
+    std::vector<std::vector<std::pair<int, cplx>>> out((size_t)n_lm(L));
+    for (int l = 0; l <= L; ++l) {
+        std::vector<double> p(l + 1, 0.0);  // P_l coefficients by power of z
+        for (int j = 0; 2 * j <= l; ++j)
+            p[l - 2 * j] = std::ldexp(((j & 1) ? -1.0 : 1.0) * binom(l, j) * binom(2 * l - 2 * j, l), -l);
+        for (int m = 0; m <= l; ++m) {
+            // m-th derivative: coefficient of z^k is p[k + m] (k + m)! / k!
+            std::vector<double> d(l - m + 1, 0.0);
+            for (int k = 0; k + m <= l; ++k) {
+                double f = 1.0;
+                for (int t = k + 1; t <= k + m; ++t) f *= t;
+                d[k] = p[k + m] * f;
+            }
+            double ratio = 1.0;  // (l - m)! / (l + m)!
+            for (int t = l - m + 1; t <= l + m; ++t) ratio /= t;
+            const double N = std::sqrt((2 * l + 1) / (4.0 * kPi) * ratio) * ((m & 1) ? -1.0 : 1.0);
+            auto& terms = out[lm_index(l, m)];
+            for (int k = 0; k <= l - m; ++k) {
+                if (d[k] == 0.0) continue;
+                for (int t = 0; t <= m; ++t) {  // C(m, t) xhat^(m-t) (i yhat)^t
+                    static const cplx ipow[4] = {cplx(1, 0), cplx(0, 1), cplx(-1, 0), cplx(0, -1)};
+                    terms.push_back({M.at(m - t, t, k), N * d[k] * binom(m, t) * ipow[t & 3]});
+                }
+            }
+        }
+    }
+    return out;
+}
+
+// a_lm(i, b) for one primary through the monomial power sums: the pairs and
+// frame are those of alm_one; per pair the unit separation's monomials are
+// added (weighted) to the sums of its bin, and the sums are converted at the end.
+void alm_one_monomial(const Geom& g, const Monomials& M,
+                      const std::vector<std::vector<std::pair<int, cplx>>>& C, const double* pos,
+                      const double* w, int64_t n, int64_t i, cplx* alm) {
+    const int nlm = n_lm(g.lmax), nm = M.count(), L = g.lmax;
+    std::vector<double> S((size_t)g.nbins * nm, 0.0);
+    std::vector<double> px(L + 1), py(L + 1), pz(L + 1);
+    double R[9];
+    los_rotation(g, pos + 3 * i, R);
+    for (int64_t j = 0; j < n; ++j) {
+        if (j == i) continue;
+        double d[3];
+        int sh[3];
+        const int b = pair_bin(g, pos + 3 * i, pos + 3 * j, d, sh);
+        if (b < 0) continue;
+        double dr[3];
+        for (int a = 0; a < 3; ++a) dr[a] = R[3 * a] * d[0] + R[3 * a + 1] * d[1] + R[3 * a + 2] * d[2];
+        const double r = std::sqrt(dr[0] * dr[0] + dr[1] * dr[1] + dr[2] * dr[2]);
+        px[0] = py[0] = pz[0] = 1.0;
+        for (int k = 1; k <= L; ++k) {
+            px[k] = px[k - 1] * (dr[0] / r);
+            py[k] = py[k - 1] * (dr[1] / r);
+            pz[k] = pz[k - 1] * (dr[2] / r);
+        }
+        double* Sb = S.data() + (size_t)b * nm;
+        for (int t = 0; t < nm; ++t) Sb[t] += w[j] * px[M.a[t]] * py[M.b[t]] * pz[M.c[t]];
+    }
+    for (int b = 0; b < g.nbins; ++b)
+        for (int k = 0; k < nlm; ++k) {
+            cplx v(0.0, 0.0);
+            for (const auto& tc : C[k]) v += tc.second * S[(size_t)b * nm + tc.first];
+            alm[(int64_t)b * nlm + k] = v;
+        }
+}
+
 int threads_of(int nthreads) {
 #ifdef _OPENMP
     return nthreads > 0 ? nthreads : omp_get_max_threads();
@@ -316,6 +426,26 @@ int orc_alm(const double* pos, const double* w, int64_t n, const int64_t* prim, 
     if (counts)
         for (int t = 0; t < nt; ++t)
             for (int b = 0; b < nbins; ++b) counts[b] += tc[t][b];
+    return 0;
+}
+
+// Number of monomials with a + b + c <= lmax (the paper's power sums).
+int64_t orc_mono_count(int lmax) { return lmax < 0 ? 0 : Monomials(lmax).count(); }
+
+// Per-primary multipoles through the monomial power sums (Sec. 3.3.2); same
+// arguments and output layout as orc_alm.
+int orc_alm_monomial(const double* pos, const double* w, int64_t n, const int64_t* prim, int64_t np,
+                     double box, int los_mode, int nbins, double rmin, double rmax, int lmax,
+                     double* alm, int nthreads) {
+    Geom g;
+    if (make_geom(g, nbins, rmin, rmax, lmax, box, los_mode) != 0) return -1;
+    const Monomials M(lmax);
+    const auto C = ylm_monomial_coefficients(M);
+    const int nlm = n_lm(lmax);
+    const int nt = threads_of(nthreads);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int64_t k = 0; k < np; ++k)
+        alm_one_monomial(g, M, C, pos, w, n, prim[k], reinterpret_cast<cplx*>(alm) + k * (int64_t)nbins * nlm);
     return 0;
 }
 
