@@ -64,11 +64,12 @@ def _load():
         lib.orc_zeta_triplets.argtypes = [P, P, I64, D, I, I, D, D, I, P]
         lib.orc_iso_legendre.argtypes = [P, P, I64, D, I, I, D, D, I, P]
         lib.orc_grad.argtypes = [P, P, I64, D, I, I, D, D, I, P, P, P, I]
+        lib.orc_grad_sel.argtypes = [P, P, I64, D, I, I, D, D, I, P, P, I64, P, P, I]
         lib.orc_mono_count.restype = I64
         lib.orc_mono_count.argtypes = [I]
         lib.orc_alm_monomial.argtypes = [P, P, I64, P, I64, D, I, I, D, D, I, P, I]
         for f in ("orc_edges", "orc_ylm", "orc_ylm_grad", "orc_alm", "orc_zeta",
-                  "orc_zeta_from_alm", "orc_zeta_triplets", "orc_iso_legendre", "orc_grad",
+                  "orc_zeta_from_alm", "orc_zeta_triplets", "orc_iso_legendre", "orc_grad", "orc_grad_sel",
                   "orc_alm_monomial"):
             getattr(lib, f).restype = I
         _lib = lib
@@ -219,6 +220,22 @@ def grad(pos, w, G, box, nbins, rmin, rmax, lmax, los_mode=0, nthreads=0):
                           _ptr(G), _ptr(dpos), _ptr(dw), nthreads)
     if rc != 0:
         raise ValueError("orc_grad failed (%d)" % rc)
+    return dpos, dw
+
+
+def grad_sel(pos, w, G, box, nbins, rmin, rmax, lmax, sel, los_mode=0, nthreads=0):
+    """Reference (dpos, dw) of ``grad`` for the chosen galaxies ``sel`` only:
+    arrays (len(sel), 3) and (len(sel),), in the order of ``sel``.  Evaluates the
+    multipoles of the chosen galaxies and of the primaries within rmax of them."""
+    pos, w = _f64(pos), _f64(w)
+    G = np.ascontiguousarray(G, dtype=np.complex128)
+    sel = np.ascontiguousarray(sel, dtype=np.int64)
+    dpos = np.zeros((sel.size, 3))
+    dw = np.zeros(sel.size)
+    rc = _load().orc_grad_sel(_ptr(pos), _ptr(w), pos.shape[0], box, los_mode, nbins, rmin, rmax, lmax,
+                              _ptr(G), _ptr(sel), sel.size, _ptr(dpos), _ptr(dw), nthreads)
+    if rc != 0:
+        raise ValueError("orc_grad_sel failed (%d)" % rc)
     return dpos, dw
 
 

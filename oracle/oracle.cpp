@@ -666,4 +666,121 @@ int orc_grad(const double* pos, const double* w, int64_t n, double box, int los_
     return 0;
 }
 
+// The reference gradient of orc_grad restricted to nsel chosen galaxies
+// sel[k] (each a primary and a secondary, every point a primary): galaxy s
+// receives its primary terms (the primary-weight term and -dL/dd over its own
+// pairs) and, for every primary i with s among its accepted secondaries, the
+// terms of the pair (i, s).  Only the primaries within rmax of a chosen galaxy
+// (and the chosen ones) have their multipoles evaluated, so a large catalog
+// costs about (number of such primaries) x n pair tests.  dpos: nsel x 3,
+// dw: nsel, in the order of sel.
+int orc_grad_sel(const double* pos, const double* w, int64_t n, double box, int los_mode, int nbins,
+                 double rmin, double rmax, int lmax, const double* Gz, const int64_t* sel, int64_t nsel,
+                 double* dpos, double* dw, int nthreads) {
+    Geom g;
+    if (make_geom(g, nbins, rmin, rmax, lmax, box, los_mode) != 0) return -1;
+    if (g.radial) return -2;
+    const int nlm = n_lm(lmax);
+    const cplx* G = reinterpret_cast<const cplx*>(Gz);
+    const int nt = threads_of(nthreads);
+    std::vector<int64_t> slot(n, -1);
+    for (int64_t k = 0; k < nsel; ++k) {
+        if (sel[k] < 0 || sel[k] >= n || slot[sel[k]] >= 0) return -3;
+        slot[sel[k]] = k;
+    }
+    // primaries whose multipoles are needed: the chosen galaxies and every
+    // primary that has a chosen galaxy among its accepted secondaries
+    std::vector<char> need(n, 0);
+    for (int64_t k = 0; k < nsel; ++k) need[sel[k]] = 1;
+#pragma omp parallel for schedule(static) num_threads(nt)
+    for (int64_t i = 0; i < n; ++i) {
+        if (need[i]) continue;
+        for (int64_t k = 0; k < nsel; ++k) {
+            double d[3];
+            int sh[3];
+            if (pair_bin(g, pos + 3 * i, pos + 3 * sel[k], d, sh) >= 0) {
+                need[i] = 1;
+                break;
+            }
+        }
+    }
+    std::vector<int64_t> prim;
+    for (int64_t i = 0; i < n; ++i)
+        if (need[i]) prim.push_back(i);
+    std::vector<std::vector<double>> tdpos(nt, std::vector<double>(3 * nsel, 0.0));
+    std::vector<std::vector<double>> tdw(nt, std::vector<double>(nsel, 0.0));
+#pragma omp parallel num_threads(nt)
+    {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        std::vector<cplx> alm((int64_t)nbins * nlm), H((int64_t)nbins * nlm);
+        std::vector<cplx> Y(n_lm(lmax + 1)), gY(3 * (int64_t)nlm);
+        double* mydpos = tdpos[t].data();
+        double* mydw = tdw[t].data();
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t k = 0; k < (int64_t)prim.size(); ++k) {
+            const int64_t i = prim[k];
+            const int64_t si = slot[i];
+            alm_one(g, pos, nullptr, w, n, i, alm.data(), nullptr);
+            // H = w_i (G + G^H) A and the primary-weight term, as in orc_grad
+            std::fill(H.begin(), H.end(), cplx(0.0, 0.0));
+            double dwi = 0.0;
+            for (int m = 0; m <= lmax; ++m) {
+                const int64_t K = (int64_t)nbins * (lmax + 1 - m);
+                const cplx* Gm = G + zeta_block_offset(nbins, lmax, m);
+                for (int l = m; l <= lmax; ++l)
+                    for (int b1 = 0; b1 < nbins; ++b1) {
+                        const int64_t r = (int64_t)(l - m) * nbins + b1;
+                        cplx acc(0.0, 0.0), accG(0.0, 0.0);
+                        for (int lp = m; lp <= lmax; ++lp)
+                            for (int b2 = 0; b2 < nbins; ++b2) {
+                                const int64_t c = (int64_t)(lp - m) * nbins + b2;
+                                const cplx a = alm[(int64_t)b2 * nlm + lm_index(lp, m)];
+                                acc += (Gm[r * K + c] + std::conj(Gm[c * K + r])) * a;
+                                accG += Gm[r * K + c] * a;
+                            }
+                        const cplx ar = alm[(int64_t)b1 * nlm + lm_index(l, m)];
+                        H[(int64_t)b1 * nlm + lm_index(l, m)] = w[i] * acc;
+                        dwi += 2.0 * std::real(std::conj(ar) * accG);
+                    }
+            }
+            if (si >= 0) mydw[si] += dwi;
+            // pairs (i, j) that touch a chosen galaxy: j chosen, or i chosen
+            for (int64_t j = 0; j < n; ++j) {
+                if (j == i) continue;
+                const int64_t sj = slot[j];
+                if (si < 0 && sj < 0) continue;
+                double d[3];
+                int sh[3];
+                int b = pair_bin(g, pos + 3 * i, pos + 3 * j, d, sh);
+                if (b < 0) continue;
+                ylm_all(lmax, d, Y.data());
+                ylm_grad_all(lmax, d, Y.data(), gY.data());
+                double sw = 0.0, sd[3] = {0.0, 0.0, 0.0};
+                for (int l = 0; l <= lmax; ++l)
+                    for (int m = 0; m <= l; ++m) {
+                        const cplx h = std::conj(H[(int64_t)b * nlm + lm_index(l, m)]);
+                        sw += std::real(h * Y[lm_index(l, m)]);
+                        for (int a = 0; a < 3; ++a) sd[a] += std::real(h * gY[3 * lm_index(l, m) + a]);
+                    }
+                if (sj >= 0) mydw[sj] += 2.0 * sw;
+                for (int a = 0; a < 3; ++a) {
+                    const double v = 2.0 * w[j] * sd[a];
+                    if (sj >= 0) mydpos[3 * sj + a] += v;
+                    if (si >= 0) mydpos[3 * si + a] -= v;
+                }
+            }
+        }
+    }
+    std::fill(dpos, dpos + 3 * nsel, 0.0);
+    std::fill(dw, dw + nsel, 0.0);
+    for (int t = 0; t < nt; ++t) {
+        for (int64_t k = 0; k < 3 * nsel; ++k) dpos[k] += tdpos[t][k];
+        for (int64_t k = 0; k < nsel; ++k) dw[k] += tdw[t][k];
+    }
+    return 0;
+}
+
 }  // extern "C"

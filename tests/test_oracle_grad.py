@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
+from paper_1709_00086_gb300 import catalogs
 
 
 def _setup(seed=5):
@@ -64,3 +65,30 @@ def test_radial_mode_rejected():
     kw = dict(kw, los_mode=2)
     with pytest.raises(ValueError):
         oracle.grad(pos, w, zt, **kw)
+
+
+@pytest.mark.parametrize("los_mode", [0, 1])
+def test_grad_sel_matches_full_gradient(los_mode):
+    # the chosen-galaxy gradient (used on catalogs too large for orc_grad) equals
+    # the full reference gradient at those galaxies: same terms, fewer primaries
+    cat = catalogs.small_case("clustered", 500, seed=70 + los_mode, box=220.0, nbins=6, rmin=5.0,
+                              rmax=50.0, lmax=5, los_mode=los_mode)
+    pos, w = cat.pos.astype(np.float64), cat.w.astype(np.float64)
+    K = sum(k * k for k in oracle.zeta_block_sizes(cat.nbins, cat.lmax))
+    rng = np.random.default_rng(71)
+    G = rng.normal(size=K) + 1j * rng.normal(size=K)
+    dpos, dw = oracle.grad(pos, w, G, cat.box, cat.nbins, cat.rmin, cat.rmax, cat.lmax, los_mode=los_mode)
+    sel = rng.choice(cat.n, 40, replace=False)
+    spos, sw = oracle.grad_sel(pos, w, G, cat.box, cat.nbins, cat.rmin, cat.rmax, cat.lmax, sel,
+                               los_mode=los_mode)
+    assert np.abs(spos - dpos[sel]).max() <= 1e-12 * np.abs(dpos).max()
+    assert np.abs(sw - dw[sel]).max() <= 1e-12 * np.abs(dw).max()
+    # a chosen galaxy with no neighbours gets only its (zero) primary terms
+    far = np.concatenate([pos, [[0.5 * cat.box, 0.5 * cat.box, 0.5 * cat.box]]])
+    far_w = np.concatenate([w, [1.0]])
+    keep = np.linalg.norm(far[:-1] - far[-1], axis=1) > cat.rmax + 1.0
+    far = np.concatenate([far[:-1][keep], far[-1:]])
+    far_w = np.concatenate([far_w[:-1][keep], far_w[-1:]])
+    spos, sw = oracle.grad_sel(far, far_w, G, cat.box, cat.nbins, cat.rmin, cat.rmax, cat.lmax,
+                               [far.shape[0] - 1], los_mode=los_mode)
+    assert np.all(spos == 0.0) and np.all(sw == 0.0)
