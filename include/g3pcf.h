@@ -89,8 +89,11 @@ enum {
                                    read by g3pcf_status()                                 */
     G3PCF_F_KEEP_ALM = 8,       /* the multipoles of the call are meant for g3pcf_alm and
                                    g3pcf_backward (implied when requires_grad is used):
-                                   separations across a periodic box face are formed from
-                                   the exact FP64 image (about 5% more pair-stage time) */
+                                   separations are formed from the exact FP64 image of
+                                   the primary, and the multipoles are evaluated and
+                                   summed in double-float with the connection in FP64
+                                   (G3PCF_OPT_GRAD_PRECISION); several times the FP32
+                                   pair-stage time                                       */
     G3PCF_F_GRAPH = 16          /* replay a captured CUDA graph: the first call with a new
                                    signature (pointers, sizes, offsets, flags, options) runs
                                    once and captures its device work on an internal stream;
@@ -138,7 +141,8 @@ int g3pcf_compute_ex(g3pcf_plan_t plan, const void* pos, const float* w, int64_t
  * zeta: device, ncat consecutive zeta blocks.  counts: device, ncat x nbins
  * int64, may be NULL.  One launch per stage over all catalogs (device work
  * queue, heaviest catalogs first).  flags: G3PCF_F_CONTRACT_FP32,
- * G3PCF_F_NO_SYNC. */
+ * G3PCF_F_NO_SYNC, G3PCF_F_KEEP_ALM (multipoles kept for g3pcf_backward) and
+ * G3PCF_F_GRAPH (capture and replay, as for g3pcf_compute_ex). */
 int g3pcf_compute_batch(g3pcf_plan_t plan, const float* pos, const float* w,
                         const int64_t* offsets, int ncat, double* zeta, int64_t* counts,
                         int flags);
@@ -150,7 +154,10 @@ int g3pcf_compute_batch(g3pcf_plan_t plan, const float* pos, const float* w,
  * n x 3 doubles; dw: device, n doubles (all points of the forward, its order);
  * both overwritten.  Pair set and bins are held fixed.  The pos and w
  * buffers of the forward must still hold the same values.  Not in the paper:
- * dL/dw_i and dL/dpos_i of zeta through Y_lm and the weights. */
+ * dL/dw_i and dL/dpos_i of zeta through Y_lm and the weights.
+ * Not bitwise reproducible: the secondaries' terms are summed with FP64
+ * atomic additions whose order varies between runs, so two backwards on the
+ * same input can differ in the last bits (the forward is reproducible). */
 int g3pcf_backward(g3pcf_plan_t plan, const double* dzeta, double* dpos, double* dw);
 
 /* Multipoles of the last forward (run with G3PCF_F_KEEP_ALM or before a
@@ -201,10 +208,12 @@ int g3pcf_stats(g3pcf_plan_t plan, double* vals, int nvals);
  *   stream: cudaStream_t (NULL = legacy stream).  Asynchronous; no sync.
  * Scratch: 16 MiB of FP64 partial sums and small tile tables in fixed device
  * arrays inside the library, present on every GPU that loads it until the
- * process exits.  The first call on a device looks up their addresses; make
- * that first call before any stream capture.  Every call reuses the same
- * arrays (each call overwrites what it reads, nothing needs clearing), so
- * calls that overlap on the GPU race and must be serialised by the caller.
+ * process exits.  The first call on a device looks up their addresses (with
+ * that device current; safe from several host threads); make that first call
+ * before any stream capture, and do not call this entry point on a device
+ * after cudaDeviceReset().  Every call rewrites the tables on the device and
+ * overwrites what it reads, so nothing needs clearing; calls that overlap on
+ * the GPU share the arrays and race, so the caller must serialise them.
  * Limits: nbins <= 32, lmax <= 10, np < 2^27; shapes whose tile table or one
  * segment of partials would not fit return G3PCF_ERR_ARG. */
 int g3pcf_zeta_from_alm_noalloc(int nbins, int lmax, const float* alm, int64_t ld,
@@ -248,14 +257,21 @@ int g3pcf_fp32_peak(double* tflops, void* stream);
  *   G3PCF_OPT_KFLUSH          pairs per lane per bucket flush of the fused pair
  *                             kernel (2..16)
  *   G3PCF_OPT_PAIR_KERNELS    forward pair stage: 1 = the fused kernel (bucket and
- *                             accumulate in one pass), 2 = pair lists (count, scan
- *                             into per-bin lists of 32 pairs, accumulate; one host
- *                             synchronisation per chunk of primaries), 0 = lists
- *                             except inside a captured graph (G3PCF_F_GRAPH), which
- *                             always uses the fused kernel
+ *                             accumulate in one pass), 0 or 2 = pair lists (count,
+ *                             scan into per-bin lists of 32 pairs, accumulate; one
+ *                             host synchronisation per chunk of primaries; inside a
+ *                             captured graph (G3PCF_F_GRAPH) the list passes are
+ *                             planned on the device instead)
  *   G3PCF_OPT_LIST_BYTES      device bytes for the pair lists (0: up to 40% of free
  *                             memory, at most 32 GB); more pairs than fit are
  *                             processed in several passes
+ *   G3PCF_OPT_GRAD_PRECISION  arithmetic of the pair stage for multipoles that are
+ *                             differentiated (forwards with G3PCF_F_KEEP_ALM, the
+ *                             backward and its recomputation): 0 = double-float
+ *                             (FP32 head + tail; V = M A in FP64), gradients within
+ *                             1e-7 of the FP64 reference; 1 = FP32, about 1e-6
+ *                             (faster).  Plain forwards always use FP32; the fused
+ *                             kernel (G3PCF_OPT_PAIR_KERNELS = 1) is FP32 only
  *   G3PCF_OPT_BASIS           multipoles of the pair-list forward: 0 = Chebyshev form
  *                             (FP32, the fast path); 1 = the paper's monomial power
  *                             sums sum w x^a y^b z^c, a + b + c <= lmax (Sec. 3.3.2),
@@ -268,7 +284,8 @@ enum {
     G3PCF_OPT_PAIR_KERNELS = 4,
     G3PCF_OPT_LIST_BYTES = 5,
     G3PCF_OPT_BASIS = 7,
-    G3PCF_OPT_X_REFINE = 8
+    G3PCF_OPT_X_REFINE = 8,
+    G3PCF_OPT_GRAD_PRECISION = 9
 };
 int g3pcf_set_option(g3pcf_plan_t plan, int option, int64_t value);
 

@@ -24,6 +24,7 @@ LOS_Z_PERIODIC, LOS_Z_OPEN, LOS_RADIAL_OPEN = 0, 1, 2
 OPT_CHUNK_ROWS, OPT_CELLS_PER_RMAX, OPT_KFLUSH, OPT_PAIR_KERNELS, OPT_LIST_BYTES = 1, 2, 3, 4, 5
 OPT_BASIS = 7
 OPT_X_REFINE = 8
+OPT_GRAD_PRECISION = 9
 F_POS_F64, F_CONTRACT_FP32, F_NO_SYNC, F_KEEP_ALM, F_GRAPH = 1, 2, 4, 8, 16
 ERRORS = {0: "OK", -1: "ERR_ARG", -2: "ERR_RANGE", -3: "ERR_RMAX", -4: "ERR_ALLOC",
           -5: "ERR_CUDA", -6: "ERR_TIMEOUT", -7: "ERR_STATE", -8: "ERR_UNSUPPORTED"}
@@ -251,7 +252,7 @@ class Plan:
 
     def set_option(self, option: int, value: int):
         """Tuning knob (OPT_CHUNK_ROWS, OPT_CELLS_PER_RMAX, OPT_KFLUSH, OPT_PAIR_KERNELS,
-        OPT_LIST_BYTES, OPT_BASIS, OPT_X_REFINE; 0 = automatic)."""
+        OPT_LIST_BYTES, OPT_BASIS, OPT_X_REFINE, OPT_GRAD_PRECISION; 0 = automatic)."""
         _check(lib().g3pcf_set_option(self._h, int(option), int(value)))
 
     def status(self):

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(ROOT, "_build", "obj")
 LIB = os.path.join(HERE, "libg3pcf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "index.cu", "pair.cu", "pairlist.cu", "contract.cu", "contract_tc.cu", "adjoint.cu", "noalloc.cu", "peak.cu", "monomial.cu"]
+SOURCES = ["api.cu", "index.cu", "pair.cu", "pairlist.cu", "contract.cu", "contract_tc.cu", "adjoint.cu", "noalloc.cu", "peak.cu", "monomial.cu", "precise.cu"]
 
 
 def nvcc() -> str:

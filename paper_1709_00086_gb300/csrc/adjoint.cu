@@ -4,7 +4,8 @@
 //
 // With G_m = dL/dzeta_m / 2 (the caller passes dL/d(Re zeta, Im zeta)),
 // M_m = G_m + G_m^H and A_i the primary's multipoles,
-//      V_i = M_m A_i                    (k_vgemm, per m block, FP32)
+//      V_i = M_m A_i                    (k_vgemm, per m block, FP32, or FP64
+//                                        for the double-float pair pass)
 //      dL/dw_i (as a primary) = Re(A_i^H V_i)   (fused into k_vgemm)
 //      H_i = w_i V_i                    (applied by the adjoint pair pass)
 // (per catalog c of a batched forward, M is built from that catalog's dL/dzeta_c)
@@ -32,13 +33,14 @@ struct MInfo {
     long long zoff[kMaxL + 1];  // complex offset of block m in zeta
 };
 
+template <class TM>
 __global__ void k_build_mreal(const double* dz, MInfo mi, int lmax, int64_t zsize, size_t mfloats,
-                              float* Mr) {
+                              TM* Mr) {
     const int m = blockIdx.y, cat = blockIdx.z;
     if (m > lmax) return;
     const int K = mi.K[m], W = mi.W[m];
     const double* Z = dz + 2 * ((int64_t)cat * zsize + mi.zoff[m]);
-    float* out = Mr + (size_t)cat * mfloats + mi.moff[m];
+    TM* out = Mr + (size_t)cat * mfloats + mi.moff[m];
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < W * W; e += gridDim.x * blockDim.x) {
         const int rr = e / W, cc = e % W;
         const int r = rr % K, c = cc % K;
@@ -52,7 +54,7 @@ __global__ void k_build_mreal(const double* dz, MInfo mi, int lmax, int64_t zsiz
             const bool rlo = rr < K, clo = cc < K;
             v = (rlo == clo) ? re : (rlo ? -im : im);
         }
-        out[e] = (float)v;
+        out[e] = (TM)v;
     }
 }
 
@@ -61,14 +63,17 @@ __global__ void k_build_mreal(const double* dz, MInfo mi, int lmax, int64_t zsiz
 // b covers rows row_lo + kRows b .. of catalog 0 below row_hi.  The row's
 // primary-weight term is added to dw[row], or, for rows of a chunk of
 // primaries (rorig non-null), to dw[rorig[rplist ? rplist[q0 + row] : q0 + row]].
+// TM = float: FP32 M, V and sums; TM = double: FP64 M, V and sums (the A rows
+// stay FP32, exact in FP64).
+template <class TM>
 __global__ void __launch_bounds__(kVThreads) k_vgemm(const float* __restrict__ A, int RLP, int RL,
                                                      const int4* __restrict__ blks, int64_t row_lo,
-                                                     int64_t row_hi, const float* __restrict__ Mall,
-                                                     size_t mfloats, MInfo mi, int lmax, float* V,
+                                                     int64_t row_hi, const TM* __restrict__ Mall,
+                                                     size_t mfloats, MInfo mi, int lmax, TM* V,
                                                      double* dw, const int* rplist, const int* rorig,
                                                      int64_t q0) {
     extern __shared__ float sA[];  // kRows x RL
-    __shared__ float red[kRows][kVThreads / 32];
+    __shared__ TM red[kRows][kVThreads / 32];
     int4 blk;
     if (blks) {
         blk = blks[blockIdx.x];
@@ -76,7 +81,7 @@ __global__ void __launch_bounds__(kVThreads) k_vgemm(const float* __restrict__ A
         const int64_t b0 = row_lo + (int64_t)blockIdx.x * kRows;
         blk = make_int4(0, (int)b0, (int)(row_hi - b0 < kRows ? row_hi - b0 : kRows), 0);
     }
-    const float* __restrict__ Mr = Mall + (size_t)blk.x * mfloats;
+    const TM* __restrict__ Mr = Mall + (size_t)blk.x * mfloats;
     const int64_t r0 = blk.y;
     const int64_t rows = r0 + blk.z;
     for (int k = threadIdx.x; k < kRows * RL; k += kVThreads) {
@@ -84,33 +89,33 @@ __global__ void __launch_bounds__(kVThreads) k_vgemm(const float* __restrict__ A
         sA[k] = (r0 + rr < rows) ? A[(r0 + rr) * RLP + c] : 0.f;
     }
     __syncthreads();
-    float dwp[kRows];
+    TM dwp[kRows];
 #pragma unroll
-    for (int r = 0; r < kRows; ++r) dwp[r] = 0.f;
+    for (int r = 0; r < kRows; ++r) dwp[r] = (TM)0;
     for (int col = threadIdx.x; col < RL; col += kVThreads) {
         int m = 0;
         while (m < lmax && col >= mi.col0[m + 1]) ++m;
         const int W = mi.W[m], c = col - mi.col0[m];
-        const float* Mrow = Mr + mi.moff[m] + (int64_t)c * W;
+        const TM* Mrow = Mr + mi.moff[m] + (int64_t)c * W;
         const float* As = sA + mi.col0[m];
-        float acc[kRows];
+        TM acc[kRows];
 #pragma unroll
-        for (int r = 0; r < kRows; ++r) acc[r] = 0.f;
+        for (int r = 0; r < kRows; ++r) acc[r] = (TM)0;
         for (int k = 0; k < W; ++k) {
-            const float mv = __ldg(Mrow + k);
+            const TM mv = __ldg(Mrow + k);
 #pragma unroll
-            for (int r = 0; r < kRows; ++r) acc[r] = fmaf(mv, As[r * RL + k], acc[r]);
+            for (int r = 0; r < kRows; ++r) acc[r] = fma(mv, (TM)As[r * RL + k], acc[r]);
         }
 #pragma unroll
         for (int r = 0; r < kRows; ++r) {
             if (r0 + r < rows) V[(r0 + r) * RLP + col] = acc[r];
-            dwp[r] = fmaf(sA[r * RL + col], acc[r], dwp[r]);
+            dwp[r] = fma((TM)sA[r * RL + col], acc[r], dwp[r]);
         }
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
-        float v = dwp[r];
+        TM v = dwp[r];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) red[r][wid] = v;
@@ -162,44 +167,79 @@ size_t adjoint_m_floats(int nbins, int lmax) {
 
 int adjoint_rows_per_block() { return kRows; }
 
-int launch_adjoint_prep(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, const float* A,
-                        int RLP, int RL, const int4* blks, int nblks, float* Mr, float* V, double* dw,
-                        cudaStream_t st) {
-    if (launch_adjoint_m(dzeta, nbins, lmax, ncat, zsize, Mr, st) != 0) return -1;
+template <class TM>
+int adjoint_m_t(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, TM* Mr, cudaStream_t st) {
+    const MInfo mi = make_info(nbins, lmax);
+    dim3 g1(64, lmax + 1, ncat);
+    k_build_mreal<TM><<<g1, 256, 0, st>>>(dzeta, mi, lmax, zsize, adjoint_m_floats(nbins, lmax), Mr);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <class TM>
+int adjoint_prep_t(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, const float* A, int RLP,
+                   int RL, const int4* blks, int nblks, TM* Mr, TM* V, double* dw, cudaStream_t st) {
+    if (adjoint_m_t<TM>(dzeta, nbins, lmax, ncat, zsize, Mr, st) != 0) return -1;
     if (nblks > 0) {
         const MInfo mi = make_info(nbins, lmax);
         const size_t smem = sizeof(float) * kRows * RL;
-        if (cudaFuncSetAttribute(k_vgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        if (cudaFuncSetAttribute(k_vgemm<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return -1;
-        k_vgemm<<<(unsigned)nblks, kVThreads, smem, st>>>(A, RLP, RL, blks, 0, 0, Mr,
-                                                         adjoint_m_floats(nbins, lmax), mi, lmax, V, dw,
-                                                         nullptr, nullptr, 0);
+        k_vgemm<TM><<<(unsigned)nblks, kVThreads, smem, st>>>(A, RLP, RL, blks, 0, 0, Mr,
+                                                             adjoint_m_floats(nbins, lmax), mi, lmax, V, dw,
+                                                             nullptr, nullptr, 0);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+template <class TM>
+int vgemm_rows_t(const float* A, int RLP, int RL, int64_t row_lo, int64_t row_hi, const TM* Mr, int nbins,
+                 int lmax, TM* V, double* dw, const int* plist, const int* orig, int64_t q0, cudaStream_t st) {
+    if (row_hi <= row_lo) return 0;
+    const MInfo mi = make_info(nbins, lmax);
+    const size_t smem = sizeof(float) * kRows * RL;
+    if (cudaFuncSetAttribute(k_vgemm<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return -1;
+    const int64_t nb = (row_hi - row_lo + kRows - 1) / kRows;
+    k_vgemm<TM><<<(unsigned)nb, kVThreads, smem, st>>>(A, RLP, RL, nullptr, row_lo, row_hi, Mr,
+                                                       adjoint_m_floats(nbins, lmax), mi, lmax, V, dw, plist,
+                                                       orig, q0);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+
+int launch_adjoint_prep(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, const float* A,
+                        int RLP, int RL, const int4* blks, int nblks, float* Mr, float* V, double* dw,
+                        cudaStream_t st) {
+    return adjoint_prep_t<float>(dzeta, nbins, lmax, ncat, zsize, A, RLP, RL, blks, nblks, Mr, V, dw, st);
+}
+
+int launch_adjoint_prep64(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, const float* A,
+                          int RLP, int RL, const int4* blks, int nblks, double* Mr, double* V, double* dw,
+                          cudaStream_t st) {
+    return adjoint_prep_t<double>(dzeta, nbins, lmax, ncat, zsize, A, RLP, RL, blks, nblks, Mr, V, dw, st);
+}
+
 int launch_adjoint_m(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, float* Mr,
                      cudaStream_t st) {
-    const MInfo mi = make_info(nbins, lmax);
-    dim3 g1(64, lmax + 1, ncat);
-    k_build_mreal<<<g1, 256, 0, st>>>(dzeta, mi, lmax, zsize, adjoint_m_floats(nbins, lmax), Mr);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return adjoint_m_t<float>(dzeta, nbins, lmax, ncat, zsize, Mr, st);
+}
+
+int launch_adjoint_m64(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, double* Mr,
+                       cudaStream_t st) {
+    return adjoint_m_t<double>(dzeta, nbins, lmax, ncat, zsize, Mr, st);
 }
 
 int launch_vgemm_rows(const float* A, int RLP, int RL, int64_t row_lo, int64_t row_hi, const float* Mr,
                       int nbins, int lmax, float* V, double* dw, const int* plist, const int* orig,
                       int64_t q0, cudaStream_t st) {
-    if (row_hi <= row_lo) return 0;
-    const MInfo mi = make_info(nbins, lmax);
-    const size_t smem = sizeof(float) * kRows * RL;
-    if (cudaFuncSetAttribute(k_vgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return -1;
-    const int64_t nb = (row_hi - row_lo + kRows - 1) / kRows;
-    k_vgemm<<<(unsigned)nb, kVThreads, smem, st>>>(A, RLP, RL, nullptr, row_lo, row_hi, Mr,
-                                                   adjoint_m_floats(nbins, lmax), mi, lmax, V, dw, plist,
-                                                   orig, q0);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return vgemm_rows_t<float>(A, RLP, RL, row_lo, row_hi, Mr, nbins, lmax, V, dw, plist, orig, q0, st);
+}
+
+int launch_vgemm_rows64(const float* A, int RLP, int RL, int64_t row_lo, int64_t row_hi, const double* Mr,
+                        int nbins, int lmax, double* V, double* dw, const int* plist, const int* orig,
+                        int64_t q0, cudaStream_t st) {
+    return vgemm_rows_t<double>(A, RLP, RL, row_lo, row_hi, Mr, nbins, lmax, V, dw, plist, orig, q0, st);
 }
 
 }  // namespace g3

@@ -83,12 +83,15 @@ struct g3pcf_plan_s {
     std::vector<float> colscale;
     std::vector<int4> colconv;     // Chebyshev-form columns (pair-list path)
     std::vector<float> colcoef;
+    std::vector<double> colcoef64;  // the same coefficients in FP64 (double-float path)
     std::vector<int4> slotconv;    // the transposed connection (pair-list adjoint)
     std::vector<float> slotcoef;
+    std::vector<double> slotcoef64;
     std::vector<int> monoexp, monoidx;  // monomial-basis tables (k_mono)
     std::vector<int4> monoconv;
     std::vector<double> monocoef;
     int opt_basis = 0;             // G3PCF_OPT_BASIS
+    int opt_grad = 0;              // G3PCF_OPT_GRAD_PRECISION (0 double-float, 1 FP32)
     std::vector<Tile> tiles;      // FP32 contraction tiles (edge T)
     std::vector<Tile> tiles_tc;   // tensor-core contraction tiles (edge T_tc)
     int T = 0, T_tc = 0;
@@ -99,6 +102,7 @@ struct g3pcf_plan_s {
     DevBuf counts, A, partials, d_tiles, d_segs, d_segfirst, d_colmap, d_colscale, d_catoff;
     DevBuf d_colconv, d_colcoef, d_bintab_s, d_slotconv, d_slotcoef, d_monoexp, d_monoconv, d_monoidx, d_monocoef;
     DevBuf d_ranges, d_tiles_tc, ops, d_cats, d_mreal, d_V, d_bintab, wrow, d_vblk;
+    DevBuf d_colcoef64, d_slotcoef64, d_mreal64, d_V64;
     int64_t opt_chunk = 0;   // G3PCF_OPT_CHUNK_ROWS
     // pinned staging for host -> device tables (capturable copies); offset
     // restarts at every forward
@@ -232,6 +236,12 @@ int upload_consts(g3pcf_plan_t P) {
         return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (constants)");
     CK(cudaMemcpy(P->d_slotconv.p, P->slotconv.data(), P->slotconv.size() * sizeof(int4), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->d_slotcoef.p, P->slotcoef.data(), P->slotcoef.size() * sizeof(float), cudaMemcpyHostToDevice));
+    if (P->d_colcoef64.ensure(P->colcoef64.size() * sizeof(double)) ||
+        P->d_slotcoef64.ensure(P->slotcoef64.size() * sizeof(double)))
+        return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (constants)");
+    CK(cudaMemcpy(P->d_colcoef64.p, P->colcoef64.data(), P->colcoef64.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->d_slotcoef64.p, P->slotcoef64.data(), P->slotcoef64.size() * sizeof(double),
+                  cudaMemcpyHostToDevice));
     if (P->d_monoexp.ensure(P->monoexp.size() * sizeof(int)) || P->d_monoconv.ensure(P->monoconv.size() * sizeof(int4)) ||
         P->d_monoidx.ensure(P->monoidx.size() * sizeof(int)) || P->d_monocoef.ensure(P->monocoef.size() * sizeof(double)))
         return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (constants)");
@@ -400,6 +410,7 @@ void compute_columns(g3pcf_plan_t P) {
     P->colscale.assign(P->RL, 0.f);
     P->colconv.assign(P->RL, int4{0, 0, 0, 0});
     P->colcoef.clear();
+    P->colcoef64.clear();
     // coefficient rows (times K_lm) per (l, m), shared by the bins and parts
     std::vector<int> coef_off((L + 1) * (L + 1), 0);
     for (int m = 0; m <= L; ++m)
@@ -409,7 +420,10 @@ void compute_columns(g3pcf_plan_t P) {
             double kl = std::exp(lnN + lnLead);
             if (m & 1) kl = -kl;
             coef_off[l * (L + 1) + m] = (int)P->colcoef.size();
-            for (double ck : cheb_coeffs(m, l - m)) P->colcoef.push_back((float)(ck * kl));
+            for (double ck : cheb_coeffs(m, l - m)) {
+                P->colcoef.push_back((float)(ck * kl));
+                P->colcoef64.push_back(ck * kl);
+            }
         }
     int col = 0;
     for (int m = 0; m <= L; ++m) {
@@ -436,6 +450,7 @@ void compute_columns(g3pcf_plan_t P) {
     const int NR = (L + 1) * (L + 1);
     P->slotconv.assign(NR, int4{0, 0, 0, 0});
     P->slotcoef.clear();
+    P->slotcoef64.clear();
     int colm = 0;
     for (int m = 0; m <= L; ++m) {
         const int K = B * (L + 1 - m);
@@ -450,6 +465,7 @@ void compute_columns(g3pcf_plan_t P) {
                     double kl = std::exp(lnN + lnLead);
                     if (m & 1) kl = -kl;
                     P->slotcoef.push_back((float)(cheb_coeffs(m, nn)[k] * kl));
+                    P->slotcoef64.push_back(cheb_coeffs(m, nn)[k] * kl);
                 }
             }
         colm += (m == 0) ? K : 2 * K;
@@ -601,8 +617,12 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode
     la.bin_tscale = pa.bin_tscale;
     la.g = pa.g;
     la.bins = pa.bins;
-    // multipoles that will be differentiated take the exact image separations
+    // multipoles that will be differentiated take the exact image separations and,
+    // unless the FP32 form is asked for, the double-float kernels (precise.cu)
     la.exact_img = (mode >= 1 || P->exact_alm) ? 1 : 0;
+    la.precise = (la.exact_img && P->opt_grad == 0) ? 1 : 0;
+    la.colcoef64 = P->d_colcoef64.as<double>();
+    la.slotcoef64 = P->d_slotcoef64.as<double>();
     la.monoexp = P->d_monoexp.as<int>();
     la.monoconv = P->d_monoconv.as<int4>();
     la.monoidx = P->d_monoidx.as<int>();
@@ -613,6 +633,7 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode
         la.dpos = pa.dpos;
         la.slotconv = P->d_slotconv.as<int4>();
         la.slotcoef = P->d_slotcoef.as<float>();
+        la.V64 = P->d_V64.as<double>();
     }
     la.need = P->l_need.as<int>();
     la.base = P->l_base.as<int>();
@@ -746,10 +767,15 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode
             // recompute: the chunk-local multipole rows of this pass, their V = M A and
             // primary-weight terms, then the adjoint pair pass over the same lists
             P->launches += 2;
-            if (launch_accum(P->lmax, la, P->nsm, st) != 0 ||
-                launch_vgemm_rows(la.A, la.RLP, la.RL, la.qa - la.q0, la.qb - la.q0, P->d_mreal.as<float>(),
-                                  P->nbins, P->lmax, P->d_V.as<float>(), pa.dw, la.plist, la.orig, la.q0,
-                                  st) != 0)
+            int vr = launch_accum(P->lmax, la, P->nsm, st);
+            if (vr == 0)
+                vr = la.precise ? launch_vgemm_rows64(la.A, la.RLP, la.RL, la.qa - la.q0, la.qb - la.q0,
+                                                      P->d_mreal64.as<double>(), P->nbins, P->lmax,
+                                                      P->d_V64.as<double>(), pa.dw, la.plist, la.orig, la.q0, st)
+                                : launch_vgemm_rows(la.A, la.RLP, la.RL, la.qa - la.q0, la.qb - la.q0,
+                                                    P->d_mreal.as<float>(), P->nbins, P->lmax, P->d_V.as<float>(),
+                                                    pa.dw, la.plist, la.orig, la.q0, st);
+            if (vr != 0)
                 return fail(G3PCF_ERR_CUDA, "adjoint recompute launch failed: %s", cudaGetErrorString(cudaGetLastError()));
             CK(cudaMemsetAsync(la.queue, 0, sizeof(int), st));
         }
@@ -1354,15 +1380,20 @@ int g3pcf_backward(g3pcf_plan_t P, const double* dzeta, double* dpos, double* dw
         // the multipoles did not fit: recompute them chunk by chunk (same chunks as the
         // forward) and run each chunk's adjoint on the lists that recomputed them
         const int64_t C = P->fixed_chunk;
-        if (ensure(P->d_mreal, sizeof(float) * adjoint_m_floats(P->nbins, P->lmax), "adjoint M") ||
-            ensure(P->d_V, sizeof(float) * (size_t)P->RLP * C, "adjoint V"))
+        const bool precise = P->opt_grad == 0;
+        if (precise ? (ensure(P->d_mreal64, sizeof(double) * adjoint_m_floats(P->nbins, P->lmax), "adjoint M") ||
+                       ensure(P->d_V64, sizeof(double) * (size_t)P->RLP * C, "adjoint V"))
+                    : (ensure(P->d_mreal, sizeof(float) * adjoint_m_floats(P->nbins, P->lmax), "adjoint M") ||
+                       ensure(P->d_V, sizeof(float) * (size_t)P->RLP * C, "adjoint V")))
             return G3PCF_ERR_ALLOC;
         int* d_status = P->small.as<int>();
         int* d_queue = d_status + 16;
         CK(cudaMemsetAsync(P->small.p, 0, 256, st));
         CK(cudaMemsetAsync(P->counts.p, 0, sizeof(unsigned long long) * P->nbins, st));
-        if (launch_adjoint_m(dzeta, P->nbins, P->lmax, 1, zsize_of(P->nbins, P->lmax), P->d_mreal.as<float>(),
-                             st) != 0)
+        if ((precise ? launch_adjoint_m64(dzeta, P->nbins, P->lmax, 1, zsize_of(P->nbins, P->lmax),
+                                          P->d_mreal64.as<double>(), st)
+                     : launch_adjoint_m(dzeta, P->nbins, P->lmax, 1, zsize_of(P->nbins, P->lmax),
+                                        P->d_mreal.as<float>(), st)) != 0)
             return fail(G3PCF_ERR_CUDA, "adjoint preparation launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         P->lev_used = 0;
         for (int64_t q0 = 0; q0 < rows; q0 += C) {
@@ -1408,8 +1439,12 @@ int g3pcf_backward(g3pcf_plan_t P, const double* dzeta, double* dpos, double* dw
         const int64_t r0 = ncat > 1 ? P->last_offs[c] : 0, r1 = ncat > 1 ? P->last_offs[c + 1] : rows;
         for (int64_t r = r0; r < r1; r += RB) blks.push_back(int4{c, (int)r, (int)std::min<int64_t>(RB, r1 - r), 0});
     }
-    if (ensure(P->d_mreal, sizeof(float) * adjoint_m_floats(P->nbins, P->lmax) * ncat, "adjoint M") ||
-        ensure(P->d_V, sizeof(float) * (size_t)P->RLP * rows, "adjoint V") ||
+    // the double-float pair pass (list path, G3PCF_OPT_GRAD_PRECISION 0) takes M and V in FP64
+    const bool precise = P->opt_grad == 0 && P->opt_pair != 1;
+    if ((precise ? (ensure(P->d_mreal64, sizeof(double) * adjoint_m_floats(P->nbins, P->lmax) * ncat, "adjoint M") ||
+                    ensure(P->d_V64, sizeof(double) * (size_t)P->RLP * rows, "adjoint V"))
+                 : (ensure(P->d_mreal, sizeof(float) * adjoint_m_floats(P->nbins, P->lmax) * ncat, "adjoint M") ||
+                    ensure(P->d_V, sizeof(float) * (size_t)P->RLP * rows, "adjoint V"))) ||
         ensure(P->d_vblk, sizeof(int4) * (blks.size() + 1), "adjoint blocks"))
         return G3PCF_ERR_ALLOC;
     CK(cudaMemcpyAsync(P->d_vblk.p, blks.data(), sizeof(int4) * blks.size(), cudaMemcpyHostToDevice, st));
@@ -1417,9 +1452,12 @@ int g3pcf_backward(g3pcf_plan_t P, const double* dzeta, double* dpos, double* dw
     int* d_queue = d_status + 16;
     CK(cudaMemsetAsync(P->small.p, 0, 256, st));
     CK(cudaMemsetAsync(P->counts.p, 0, sizeof(unsigned long long) * P->nbins * ncat, st));
-    if (launch_adjoint_prep(dzeta, P->nbins, P->lmax, ncat, zsize_of(P->nbins, P->lmax), P->A.as<float>(),
-                            P->RLP, P->RL, P->d_vblk.as<int4>(), (int)blks.size(), P->d_mreal.as<float>(),
-                            P->d_V.as<float>(), dw, st) != 0)
+    if ((precise ? launch_adjoint_prep64(dzeta, P->nbins, P->lmax, ncat, zsize_of(P->nbins, P->lmax),
+                                         P->A.as<float>(), P->RLP, P->RL, P->d_vblk.as<int4>(), (int)blks.size(),
+                                         P->d_mreal64.as<double>(), P->d_V64.as<double>(), dw, st)
+                 : launch_adjoint_prep(dzeta, P->nbins, P->lmax, ncat, zsize_of(P->nbins, P->lmax),
+                                       P->A.as<float>(), P->RLP, P->RL, P->d_vblk.as<int4>(), (int)blks.size(),
+                                       P->d_mreal.as<float>(), P->d_V.as<float>(), dw, st)) != 0)
         return fail(G3PCF_ERR_CUDA, "adjoint preparation launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     PairArgs pa{};
     pa.pts = P->pts.as<float4>();
@@ -1489,6 +1527,10 @@ int g3pcf_set_option(g3pcf_plan_t P, int option, int64_t value) {
         case G3PCF_OPT_BASIS:
             if (value < 0 || value > 1) return fail(G3PCF_ERR_ARG, "basis must be 0 (Chebyshev) or 1 (monomials)");
             P->opt_basis = (int)value;
+            return G3PCF_OK;
+        case G3PCF_OPT_GRAD_PRECISION:
+            if (value < 0 || value > 1) return fail(G3PCF_ERR_ARG, "gradient precision must be 0 or 1");
+            P->opt_grad = (int)value;
             return G3PCF_OK;
         case G3PCF_OPT_LIST_BYTES:
             if (value < 0) return fail(G3PCF_ERR_ARG, "list bytes must be >= 0");
@@ -1669,6 +1711,7 @@ int g3pcf_destroy(g3pcf_plan_t P) {
                       &P->small, &P->counts, &P->A, &P->partials, &P->d_tiles, &P->d_segs,
                       &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_colconv, &P->d_colcoef, &P->d_bintab_s, &P->d_slotconv, &P->d_slotcoef, &P->d_monoexp, &P->d_monoconv, &P->d_monoidx, &P->d_monocoef, &P->d_catoff, &P->d_ranges,
                       &P->d_tiles_tc, &P->ops, &P->d_cats, &P->d_mreal, &P->d_V, &P->d_bintab, &P->d_vblk,
+                      &P->d_colcoef64, &P->d_slotcoef64, &P->d_mreal64, &P->d_V64,
                       &P->wrow, &P->l_need, &P->l_base, &P->l_nch, &P->l_pool, &P->l_tag, &P->l_ord,
                       &P->l_gbase, &P->l_scantmp, &P->l_passq};
     for (DevBuf* b : bufs) b->release();

@@ -166,28 +166,7 @@ int contract_tile_dim_fp32() { return kT; }
 
 // Tiles of edge T over the upper triangle of every C_m (row-major in (ti, tj)).
 int make_tiles(int nbins, int lmax, int T, Tile* out, int max_tiles) {
-    int n = 0, col0 = 0, off = 0;
-    for (int m = 0; m <= lmax; ++m) {
-        const int K = nbins * (lmax + 1 - m);
-        const int W = (m == 0) ? K : 2 * K;
-        const int nt = (W + T - 1) / T;
-        for (int ti = 0; ti < nt; ++ti)
-            for (int tj = ti; tj < nt; ++tj) {
-                if (n >= max_tiles) return -1;
-                Tile& t = out[n++];
-                t.m = m;
-                t.r0 = ti * T;
-                t.c0 = tj * T;
-                t.rows = W - t.r0 < T ? W - t.r0 : T;
-                t.cols = W - t.c0 < T ? W - t.c0 : T;
-                t.col0 = col0;
-                t.width = W;
-                t.out_off = off;
-                off += T * T;
-            }
-        col0 += W;
-    }
-    return n;
+    return fill_tiles(nbins, lmax, T, out, max_tiles);
 }
 
 int launch_contract_fp32(const float* A, int RLP, const float* wrow, const Tile* tiles, int ntiles,

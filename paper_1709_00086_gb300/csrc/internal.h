@@ -189,6 +189,12 @@ struct ListArgs {
     const float* slotcoef;
     double* dw;
     double* dpos;
+    // double-float path (multipoles meant for differentiation): FP64 connection
+    // tables (same layout as colcoef / slotcoef) and the FP64 V rows
+    int precise;
+    const double* colcoef64;
+    const double* slotcoef64;
+    const double* V64;
     int* chunks;             // pool: 32 ints per chunk
     int* tag;                // pool: (rank among its bin's chunks) << 5 | bin, per chunk
     int* ord;                // pool: the primary's chunks listed by bin (stable), chunk | bin << 26
@@ -207,6 +213,10 @@ int launch_plan(const int* need, long long* gbase, long long* tmp, int qa, int q
 int launch_scan(const ListArgs& a, int nsm, cudaStream_t st);
 int launch_accum(int lmax, const ListArgs& a, int nsm, cudaStream_t st);
 int launch_adj(int lmax, const ListArgs& a, int nsm, cudaStream_t st);
+// precise.cu: the same two passes in double-float (a.precise selects them inside
+// launch_accum / launch_adj)
+int launch_accum_df(int lmax, const ListArgs& a, int nsm, cudaStream_t st);
+int launch_adj_df(int lmax, const ListArgs& a, int nsm, cudaStream_t st);
 // monomial.cu: the multipoles through the paper's monomial power sums (FP64)
 int mono_count(int lmax);
 int launch_mono(int lmax, const ListArgs& a, int nsm, cudaStream_t st);
@@ -218,7 +228,45 @@ struct Tile {          // one output tile of one m block of C_m = sum_i w_i v_i 
     int out_off;       // offset (floats) of this tile inside one segment's partials
 };
 struct Segment { int cat; int row0; int row1; };
+// Upper-triangle output tiles of every m block (T x T, ragged at the block
+// edge), in (m, row tile, column tile) order; returns the count or -1 when
+// more than max_tiles are needed.  Host and device code (the allocation-free
+// entry point fills its fixed table on the device).
+__host__ __device__ inline int fill_tiles(int nbins, int lmax, int T, Tile* out, int max_tiles) {
+    int n = 0, col0 = 0, off = 0;
+    for (int m = 0; m <= lmax; ++m) {
+        const int K = nbins * (lmax + 1 - m);
+        const int W = (m == 0) ? K : 2 * K;
+        const int nt = (W + T - 1) / T;
+        for (int ti = 0; ti < nt; ++ti)
+            for (int tj = ti; tj < nt; ++tj) {
+                if (n >= max_tiles) return -1;
+                Tile& t = out[n++];
+                t.m = m;
+                t.r0 = ti * T;
+                t.c0 = tj * T;
+                t.rows = W - t.r0 < T ? W - t.r0 : T;
+                t.cols = W - t.c0 < T ? W - t.c0 : T;
+                t.col0 = col0;
+                t.width = W;
+                t.out_off = off;
+                off += T * T;
+            }
+        col0 += W;
+    }
+    return n;
+}
 int make_tiles(int nbins, int lmax, int T, Tile* out, int max_tiles);
+// Number of tiles fill_tiles writes for (nbins, lmax, T).
+__host__ __device__ inline int count_tiles(int nbins, int lmax, int T) {
+    int n = 0;
+    for (int m = 0; m <= lmax; ++m) {
+        const int W = (m == 0 ? 1 : 2) * nbins * (lmax + 1 - m);
+        const int nt = (W + T - 1) / T;
+        n += nt * (nt + 1) / 2;
+    }
+    return n;
+}
 int contract_tile_dim_fp32();
 int launch_contract_fp32(const float* A, int RLP, const float* wrow, const Tile* tiles, int ntiles,
                          const Segment* segs, int nsegs, double* partials, int part_stride,
@@ -257,6 +305,15 @@ int launch_adjoint_m(const double* dzeta, int nbins, int lmax, int ncat, int64_t
 int launch_vgemm_rows(const float* A, int RLP, int RL, int64_t row_lo, int64_t row_hi, const float* Mr,
                       int nbins, int lmax, float* V, double* dw, const int* plist, const int* orig,
                       int64_t q0, cudaStream_t st);
+// FP64 forms of the three (M and V in FP64; for the double-float adjoint pass)
+int launch_adjoint_prep64(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, const float* A,
+                          int RLP, int RL, const int4* blks, int nblks, double* Mr, double* V, double* dw,
+                          cudaStream_t st);
+int launch_adjoint_m64(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, double* Mr,
+                       cudaStream_t st);
+int launch_vgemm_rows64(const float* A, int RLP, int RL, int64_t row_lo, int64_t row_hi, const double* Mr,
+                        int nbins, int lmax, double* V, double* dw, const int* plist, const int* orig,
+                        int64_t q0, cudaStream_t st);
 
 // ---- api.cu / noalloc.cu -----------------------------------------------------
 void set_last_error(const char* msg);

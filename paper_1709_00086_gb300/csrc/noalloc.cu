@@ -10,12 +10,18 @@
 // file-scope device arrays of fixed size that exist, on every GPU that loads
 // this library, until the process exits.
 //
-// The arrays are shared by all calls.  Each call overwrites every partial it
-// reads and every zeta entry it writes, so nothing has to start at zero, but
-// two calls whose work overlaps on the GPU (on different streams, or from
-// different host threads) race on the same arrays and must be ordered by the
-// caller.
+// The arrays are shared by all calls.  Each call rewrites its tile and segment
+// tables on the device (a one-thread kernel, so nothing is copied from host
+// memory), and overwrites every partial it reads and every zeta entry it
+// writes, so nothing has to start at zero; but two calls whose work overlaps
+// on the GPU (on different streams, or from different host threads) race on
+// the same arrays and must be ordered by the caller.  The device addresses of
+// the arrays are looked up once per device, by the first call made with that
+// device current, and kept until the process exits; a cudaDeviceReset()
+// invalidates them, so this entry point must not be used on a device after
+// that device has been reset.
 #include <cstdio>
+#include <mutex>
 
 #include "internal.h"
 
@@ -31,6 +37,22 @@ static __device__ __align__(256) Tile g_tiles[kNoAllocMaxTiles];
 static __device__ __align__(256) Segment g_segs[kNoAllocMaxSegs];
 static __device__ __align__(256) int g_segfirst[2];
 
+// Writes the tile table and the segments of one call straight into the fixed
+// arrays (device code may name them), so that no table is copied from host
+// memory.  One thread: the tables hold at most a few hundred entries.
+__global__ void k_fill_tables(int nbins, int lmax, int T, int64_t np, int64_t seg, int nsegs) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    fill_tiles(nbins, lmax, T, g_tiles, kNoAllocMaxTiles);
+    for (int s = 0; s < nsegs; ++s) {
+        const int64_t r0 = (int64_t)s * seg;
+        g_segs[s].cat = 0;
+        g_segs[s].row0 = (int)r0;
+        g_segs[s].row1 = (int)(r0 + seg < np ? r0 + seg : np);
+    }
+    g_segfirst[0] = 0;
+    g_segfirst[1] = nsegs;
+}
+
 struct SymbolAddrs {
     int device = -1;
     double* partials = nullptr;
@@ -39,25 +61,31 @@ struct SymbolAddrs {
     int* segfirst = nullptr;
 };
 
-// Host-side addresses of the arrays, resolved once per device.  The array
-// names are host stand-ins in host code, not device addresses; only the
-// addresses returned by cudaGetSymbolAddress may be passed to kernels.
+// Host-side addresses of the arrays, looked up once per device (with that
+// device current) and kept for the life of the process.  In host code the
+// array names are host stand-ins, not device addresses; only the addresses
+// returned by cudaGetSymbolAddress are passed to kernels.  The mutex makes
+// concurrent first calls from several host threads safe.
 SymbolAddrs g_addrs[64];
+std::mutex g_addrs_mu;
 
-int resolve(int dev, SymbolAddrs*& out) {
+int resolve(int dev, SymbolAddrs& out) {
     if (dev < 0 || dev >= 64) return -1;
+    std::lock_guard<std::mutex> lock(g_addrs_mu);
     SymbolAddrs& s = g_addrs[dev];
     if (s.device != dev) {
-        if (cudaGetSymbolAddress((void**)&s.partials, g_partials) != cudaSuccess ||
-            cudaGetSymbolAddress((void**)&s.tiles, g_tiles) != cudaSuccess ||
-            cudaGetSymbolAddress((void**)&s.segs, g_segs) != cudaSuccess ||
-            cudaGetSymbolAddress((void**)&s.segfirst, g_segfirst) != cudaSuccess) {
+        SymbolAddrs t;
+        if (cudaGetSymbolAddress((void**)&t.partials, g_partials) != cudaSuccess ||
+            cudaGetSymbolAddress((void**)&t.tiles, g_tiles) != cudaSuccess ||
+            cudaGetSymbolAddress((void**)&t.segs, g_segs) != cudaSuccess ||
+            cudaGetSymbolAddress((void**)&t.segfirst, g_segfirst) != cudaSuccess) {
             cudaGetLastError();
             return -1;
         }
-        s.device = dev;
+        t.device = dev;
+        s = t;
     }
-    out = &s;
+    out = s;
     return 0;
 }
 
@@ -66,10 +94,10 @@ int resolve(int dev, SymbolAddrs*& out) {
 int noalloc_zeta_from_alm(int nbins, int lmax, const float* alm, int64_t ld, const float* w,
                           int64_t np, double* zeta, cudaStream_t st, char* err, size_t errlen) {
     const int T = contract_tile_dim_fp32();
-    Tile tiles[kNoAllocMaxTiles];  // host stack tables: no heap use either
-    const int ntiles = make_tiles(nbins, lmax, T, tiles, kNoAllocMaxTiles);
+    // the table's size only (the table itself is written on the device)
+    const int ntiles = count_tiles(nbins, lmax, T);
     const int RL = nbins * (lmax + 1) * (lmax + 1);
-    if (ntiles < 0) {
+    if (ntiles > kNoAllocMaxTiles) {
         snprintf(err, errlen, "nbins*(lmax+1) too large for the static tile table (%d tiles max)",
                  kNoAllocMaxTiles);
         return G3PCF_ERR_ARG;
@@ -87,36 +115,21 @@ int noalloc_zeta_from_alm(int nbins, int lmax, const float* alm, int64_t ld, con
     int nsegs_max = (int)(kNoAllocPartialDoubles / part_stride);
     if (nsegs_max > kNoAllocMaxSegs) nsegs_max = kNoAllocMaxSegs;
     // segments of primaries: at least 4096 rows each, at most nsegs_max of them
-    Segment segs[kNoAllocMaxSegs];
+    int64_t seg = 4096;
     int nsegs = 0;
     if (np > 0) {
-        int64_t seg = (np + nsegs_max - 1) / nsegs_max;
+        seg = (np + nsegs_max - 1) / nsegs_max;
         if (seg < 4096) seg = 4096;
-        for (int64_t s = 0; s < np && nsegs < nsegs_max; s += seg) {
-            Segment& sg = segs[nsegs++];
-            sg.cat = 0;
-            sg.row0 = (int)s;
-            sg.row1 = (int)(s + seg < np ? s + seg : np);
-        }
+        nsegs = (int)((np + seg - 1) / seg);
     }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         snprintf(err, errlen, "cudaGetDevice failed");
         return G3PCF_ERR_CUDA;
     }
-    SymbolAddrs* sa = nullptr;
+    SymbolAddrs sa;
     if (resolve(dev, sa) != 0) {
         snprintf(err, errlen, "cudaGetSymbolAddress failed for the static scratch arrays");
-        return G3PCF_ERR_CUDA;
-    }
-    const int segfirst[2] = {0, nsegs};
-    // Small tables go to the static arrays by stream-ordered copies from
-    // pageable host memory (staged by the driver; no device allocation).
-    if (cudaMemcpyAsync(sa->tiles, tiles, sizeof(Tile) * ntiles, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(sa->segfirst, segfirst, sizeof(segfirst), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        (nsegs > 0 && cudaMemcpyAsync(sa->segs, segs, sizeof(Segment) * nsegs,
-                                      cudaMemcpyHostToDevice, st) != cudaSuccess)) {
-        snprintf(err, errlen, "copy of the tile tables failed: %s", cudaGetErrorString(cudaGetLastError()));
         return G3PCF_ERR_CUDA;
     }
     if (nsegs == 0) {
@@ -127,9 +140,11 @@ int noalloc_zeta_from_alm(int nbins, int lmax, const float* alm, int64_t ld, con
         }
         return G3PCF_OK;
     }
-    if (launch_contract_fp32(alm, (int)ld, w, sa->tiles, ntiles, sa->segs, nsegs, sa->partials,
+    k_fill_tables<<<1, 1, 0, st>>>(nbins, lmax, T, np, seg, nsegs);
+    if (cudaGetLastError() != cudaSuccess ||
+        launch_contract_fp32(alm, (int)ld, w, sa.tiles, ntiles, sa.segs, nsegs, sa.partials,
                              (int)part_stride, st) != 0 ||
-        launch_reduce(sa->partials, (int)part_stride, sa->segfirst, 1, nbins, lmax, sa->tiles, T,
+        launch_reduce(sa.partials, (int)part_stride, sa.segfirst, 1, nbins, lmax, sa.tiles, T,
                       zeta, st) != 0) {
         snprintf(err, errlen, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         return G3PCF_ERR_CUDA;

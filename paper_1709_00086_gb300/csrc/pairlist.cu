@@ -895,6 +895,7 @@ int launch_plan(const int* need, long long* gbase, long long* tmp, int qa, int q
 
 int launch_adj(int lmax, const ListArgs& a, int nsm, cudaStream_t st) {
     if (!a.qrange && a.qb <= a.qa) return 0;
+    if (a.precise) return launch_adj_df(lmax, a, nsm, st);
     switch (lmax) {
         case 0: return launch_adj_t<0>(a, nsm, st);
         case 1: return launch_adj_t<1>(a, nsm, st);
@@ -913,6 +914,7 @@ int launch_adj(int lmax, const ListArgs& a, int nsm, cudaStream_t st) {
 
 int launch_accum(int lmax, const ListArgs& a, int nsm, cudaStream_t st) {
     if (!a.qrange && a.qb <= a.qa) return 0;
+    if (a.precise) return launch_accum_df(lmax, a, nsm, st);
     switch (lmax) {
         case 0: return launch_accum_t<0>(a, nsm, st);
         case 1: return launch_accum_t<1>(a, nsm, st);

@@ -89,7 +89,42 @@ def test_batched_64_catalogs():
         assert _hermitian(zb[k].cpu().numpy(), cats[k].nbins, cats[k].lmax) < 1e-12
 
 
-def test_differentiation_500k_forward_and_adjoint():
+def _nearest(cat, k, seed):
+    """The k galaxies nearest (periodic distance) to a seeded random galaxy: their
+    rmax neighbourhoods overlap, so the oracle's reference gradient at them needs
+    the multipoles of about 1.8 x (points within rmax) primaries only."""
+    rng = np.random.default_rng(seed)
+    c = cat.pos[rng.integers(cat.n)].astype(np.float64)
+    d = cat.pos.astype(np.float64) - c
+    d -= cat.box * np.round(d / cat.box)
+    return np.sort(np.argsort((d * d).sum(1))[:k])
+
+
+def test_differentiation_500k_gradient_at_32_galaxies():
+    # the differentiation workload in full (500,000 primaries, lmax = 6): the
+    # adjoint of a seeded Hermitian dL/dzeta, element by element at 32 galaxies
+    # against the oracle's reference gradient (orc_grad_sel, pinned to orc_grad,
+    # which is pinned to FP64 central differences)
+    cat = catalogs.differentiation()
+    plan = g3.Plan(**cat.params())
+    pos, w = to_dev(cat, torch)
+    plan.compute(pos, w, keep_alm=True, fp32_contraction=True)
+    rng = np.random.default_rng(6)
+    G = rng.normal(size=plan.zsize) + 1j * rng.normal(size=plan.zsize)
+    G = np.concatenate([(b + b.conj().T).ravel() for b in oracle.zeta_blocks(G, cat.nbins, cat.lmax)])
+    dz = torch.from_numpy(np.stack([2 * G.real, 2 * G.imag], axis=1)).cuda()
+    dpos, dw = plan.backward(dz)
+    sel = _nearest(cat, 32, seed=6)
+    rpos, rw = oracle.grad_sel(cat.pos, cat.w, G, cat.box, cat.nbins, cat.rmin, cat.rmax, cat.lmax, sel)
+    assert maxrel(dw.cpu().numpy()[sel], rw) < 1e-6
+    assert maxrel(dpos.cpu().numpy()[sel], rpos) < 1e-6
+
+
+def test_differentiation_500k_autograd_loss():
+    # the workload's loss L = sum |zeta - zeta_t|^2 (zeta_t from seed 5) through
+    # autograd: finite, and translation invariant (position gradients sum to ~0;
+    # autograd hands them back in the positions' dtype, FP32, whose rounding of
+    # 500,000 terms leaves a sum near 4e-6 of the largest component)
     cat = catalogs.differentiation()
     tgt = catalogs.differentiation(seed=5)
     plan = g3.Plan(**cat.params())
@@ -101,9 +136,8 @@ def test_differentiation_500k_forward_and_adjoint():
     loss = ((z - torch.view_as_real(zt)) ** 2).sum()
     gpos, gw = torch.autograd.grad(loss, [pos, w])
     assert torch.isfinite(gpos).all() and torch.isfinite(gw).all()
-    # translation invariance of the periodic loss: position gradients sum to ~0
     s = gpos.double().sum(0).abs().max().item()
-    assert s < 1e-3 * gpos.double().abs().max().item()
+    assert s < 2e-5 * gpos.double().abs().max().item()
 
 
 def test_large_radial_50m():
