@@ -195,14 +195,14 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def run_batch(args):
+def measure_batch(steps: int, warmup: int) -> dict:
     """The batched workload (64 catalogs, sizes log-uniform in [1e3, 1e6], periodic L = 600,
     Rmax = 150, 12 bins, lmax = 8): one compute_batch per step, replayed from a captured CUDA
     graph, against the same call uncaptured."""
     import torch
     import paper_1709_00086_gb300 as g3
     from paper_1709_00086_gb300 import catalogs
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", torch.cuda.current_device())
     cats = catalogs.batched(64, seed=3)
     plan = g3.Plan(**cats[0].params())
     pos = torch.from_numpy(np.concatenate([c.pos for c in cats])).to(dev)
@@ -213,11 +213,11 @@ def run_batch(args):
     stream = torch.cuda.current_stream()
     res = {}
     for graph in (True, False):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             plan.compute_batch(pos, w, offs, graph=graph, out=zb, counts_out=cb)
         torch.cuda.synchronize()
         ms = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -227,16 +227,161 @@ def run_batch(args):
             ms.append(e0.elapsed_time(e1))
         plan.status()
         res[graph] = float(np.mean(ms))
+    st = plan.stats()
     pairs = float(cb.sum().item())
-    out = {"metric": METRIC, "value": pairs / (res[True] / 1e3), "unit": "pairs/s", "n_gpus": 1,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": res[True], "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "batched: 64 uniform catalogs, sizes log-uniform in [1e3, 1e6] (%d points), "
-                                  "periodic L=600, Rmax=150, 12 bins, lmax=8, LOS=z" % int(offs[-1]),
-                      "form": "split-BF16 tensor-core contraction, CUDA-graph replay",
-                      "pairs_per_step": pairs, "parallelism": "single GPU"},
-           "uncaptured": {"ms_per_step": res[False], "value": pairs / (res[False] / 1e3)}}
+    # the project autotuner on the largest catalog (whose pairs dominate), through its
+    # on-disk cache, then the graph replay again with the tuned grid
+    import tempfile
+    big = max(range(len(cats)), key=lambda k: cats[k].n)
+    sl = slice(int(offs[big]), int(offs[big + 1]))
+    t0 = time.perf_counter()
+    tune = plan.autotune_cached(pos[sl], w[sl], os.path.join(tempfile.gettempdir(), "g3pcf_tune.txt"))
+    tune["seconds"] = time.perf_counter() - t0
+    for _ in range(warmup):
+        plan.compute_batch(pos, w, offs, graph=True, out=zb, counts_out=cb)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.compute_batch(pos, w, offs, graph=True, out=zb, counts_out=cb, sync=False)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    plan.status()
+    tuned_ms = float(np.mean(ms))
+    out = {"workload": "batched: 64 uniform catalogs, sizes log-uniform in [1e3, 1e6] (%d points), "
+                       "periodic L=600, Rmax=150, 12 bins, lmax=8, LOS=z" % int(offs[-1]),
+           "pairs_per_step": pairs, "graph_ms_per_step": res[True], "graph_pairs_per_s": pairs / (res[True] / 1e3),
+           "uncaptured_ms_per_step": res[False], "uncaptured_pairs_per_s": pairs / (res[False] / 1e3),
+           "contract_ms": st["contract_ms"], "pair_ms": st["pair_ms"],
+           "zeta_tflops": zeta_flops_per_primary(12, 8) * int(offs[-1]) / (st["contract_ms"] / 1e3) / 1e12,
+           "tuned": {"settings": tune, "graph_ms_per_step": tuned_ms,
+                     "graph_pairs_per_s": pairs / (tuned_ms / 1e3),
+                     "vs_default": res[True] / tuned_ms}}
+    del plan, pos, w, zb, cb
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batch(args):
+    """--workload batch64: the batched workload as the JSON line's own value."""
+    b = measure_batch(args.steps, args.warmup)
+    out = {"metric": METRIC, "value": b["graph_pairs_per_s"], "unit": "pairs/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["graph_ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": b["workload"], "form": "split-BF16 tensor-core contraction, CUDA-graph replay",
+                      "pairs_per_step": b["pairs_per_step"], "parallelism": "single GPU"},
+           "uncaptured": {"ms_per_step": b["uncaptured_ms_per_step"], "value": b["uncaptured_pairs_per_s"]},
+           "tuned": b["tuned"]}
     print(json.dumps(out), flush=True)
+
+
+def measure_forward(cat, steps: int, warmup: int) -> dict:
+    """Plain forwards of one catalog, split-BF16 tensor-core and plain-FP32 contraction."""
+    import torch
+    import paper_1709_00086_gb300 as g3
+    dev = torch.device("cuda", torch.cuda.current_device())
+    plan = g3.Plan(**cat.params())
+    pos = torch.from_numpy(cat.pos).to(dev)
+    w = torch.from_numpy(cat.w).to(dev)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for fp32 in (False, True):
+        for _ in range(warmup):
+            plan.compute(pos, w, fp32_contraction=fp32, with_counts=False)
+        ms, st = [], []
+        for _ in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.compute(pos, w, fp32_contraction=fp32, with_counts=False, sync=False)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            st.append(plan.stats())
+        plan.status()
+        t = float(np.mean(ms))
+        con = float(np.mean([x["contract_ms"] for x in st]))
+        pairs = st[-1]["pairs"]
+        res["fp32" if fp32 else "tc"] = {
+            "ms_per_step": t, "pairs_per_s": pairs / (t / 1e3), "contract_ms": con,
+            "contract_share": con / t, "pair_ms": float(np.mean([x["pair_ms"] for x in st])),
+            "zeta_tflops": zeta_flops_per_primary(cat.nbins, cat.lmax) * st[-1]["primaries"] / (con / 1e3) / 1e12}
+    res["pairs_per_step"] = pairs
+    del plan, pos, w
+    torch.cuda.empty_cache()
+    return res
+
+
+def measure_adjoint(dev, stream) -> dict:
+    """The differentiation workload (clustered N = 500,000, L = 800, Rmax = 120, 8 bins,
+    lmax = 6): forward with multipoles kept, then g3pcf_backward, in the default
+    double-float gradient arithmetic and in the FP32 form."""
+    import torch
+    import paper_1709_00086_gb300 as g3
+    from paper_1709_00086_gb300 import catalogs as cats
+    dcat = cats.differentiation()
+    dpos = torch.from_numpy(dcat.pos).to(dev)
+    dwt = torch.from_numpy(dcat.w).to(dev)
+    out = {"workload": "clustered N=500,000, periodic L=800, Rmax=120, 8 bins, lmax=6"}
+    for prec, key in ((0, "double_float"), (1, "fp32")):
+        dplan = g3.Plan(**dcat.params())
+        dplan.set_option(g3.OPT_GRAD_PRECISION, prec)
+        rng = np.random.default_rng(5)
+        dz = torch.from_numpy(rng.normal(size=(dplan.zsize, 2))).to(dev)
+        fwd_ms, bwd_ms = [], []
+        for k in range(3):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            dplan.compute(dpos, dwt, keep_alm=True, with_counts=False, fp32_contraction=True)
+            e1.record(stream)
+            dplan.backward(dz)
+            e2.record(stream)
+            e2.synchronize()
+            if k > 0:
+                fwd_ms.append(e0.elapsed_time(e1))
+                bwd_ms.append(e1.elapsed_time(e2))
+        dpairs = dplan.stats()["pairs"]
+        out["pairs"] = dpairs
+        out[key] = {"forward_ms": float(np.mean(fwd_ms)), "backward_ms": float(np.mean(bwd_ms)),
+                    "backward_pairs_per_s": dpairs / (float(np.mean(bwd_ms)) / 1e3)}
+        del dplan
+    out["forward_ms"] = out["double_float"]["forward_ms"]
+    out["backward_ms"] = out["double_float"]["backward_ms"]
+    del dpos, dwt
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_large(dev) -> dict:
+    """One forward of the large radial workload (N = 5e7 clustered, open L = 3000, radial LOS,
+    Rmax = 200, 10 bins, lmax = 10), after one untimed forward."""
+    import torch
+    import paper_1709_00086_gb300 as g3
+    from paper_1709_00086_gb300 import catalogs as cats
+    cat = cats.large_radial()
+    plan = g3.Plan(**cat.params())
+    pos = torch.from_numpy(cat.pos).to(dev)
+    w = torch.from_numpy(cat.w).to(dev)
+    stream = torch.cuda.current_stream()
+    plan.compute(pos, w, with_counts=False)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.compute(pos, w, with_counts=False, sync=False)
+    e1.record(stream)
+    e1.synchronize()
+    plan.status()
+    st = plan.stats()
+    ms = e0.elapsed_time(e1)
+    out = {"workload": "clustered N=5e7, open cube L=3000, radial LOS from the centre, Rmax=200, 10 bins, lmax=10",
+           "forward_ms": ms, "pairs": st["pairs"], "pairs_per_s": st["pairs"] / (ms / 1e3),
+           "pair_ms": st["pair_ms"], "contract_ms": st["contract_ms"], "list_passes": st["list_passes"]}
+    del plan, pos, w
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_ours(args):
@@ -332,35 +477,20 @@ def run_ours(args):
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_val = ws * pairs / (float(np.mean(e2e_ms)) / 1e3)
 
-    # the adjoint (differentiation workload: clustered N = 500,000, L = 800, Rmax = 120,
-    # 8 bins, lmax = 6): forward with multipoles kept, then g3pcf_backward
+    # the other measured workloads (one GPU only): the plain 20,000-point catalog, the
+    # batched 64 catalogs, the differentiation workload's adjoint and, on request, the
+    # 50-million-point radial catalog
     adj = None
-    if not args.no_adjoint:
-        from paper_1709_00086_gb300 import catalogs as cats
-        dcat = cats.differentiation()
-        dplan = g3.Plan(**dcat.params())
-        dpos = torch.from_numpy(dcat.pos).to(dev)
-        dwt = torch.from_numpy(dcat.w).to(dev)
-        rng = np.random.default_rng(5)
-        dz = torch.from_numpy(rng.normal(size=(dplan.zsize, 2))).to(dev)
-        fwd_ms, bwd_ms = [], []
-        for k in range(3):
-            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-            e0.record(stream)
-            dplan.compute(dpos, dwt, keep_alm=True, with_counts=False, fp32_contraction=True)
-            e1.record(stream)
-            dplan.backward(dz)
-            e2.record(stream)
-            e2.synchronize()
-            if k > 0:
-                fwd_ms.append(e0.elapsed_time(e1))
-                bwd_ms.append(e1.elapsed_time(e2))
-        dpairs = dplan.stats()["pairs"]
-        adj = {"workload": "clustered N=500,000, periodic L=800, Rmax=120, 8 bins, lmax=6",
-               "pairs": dpairs, "forward_ms": float(np.mean(fwd_ms)),
-               "backward_ms": float(np.mean(bwd_ms)),
-               "backward_pairs_per_s": dpairs / (float(np.mean(bwd_ms)) / 1e3)}
-        del dplan, dpos, dwt
+    other = {}
+    if ws == 1:
+        if not args.no_adjoint:
+            adj = measure_adjoint(dev, stream)
+        if not args.no_other:
+            from paper_1709_00086_gb300 import catalogs as cats
+            other["plain_uniform_20k"] = measure_forward(cats.plain_uniform(), max(3, args.steps), args.warmup)
+            other["batched_64"] = measure_batch(2, 1)
+        if args.large:
+            other["large_radial_50m"] = measure_large(dev)
 
     if rank != 0:
         return
@@ -405,6 +535,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(hpos.numel() * 4 + hw.numel() * 4),
                 "d2h_bytes_per_step": int(hz.numel() * 8)},
         "adjoint": adj,
+        "other_workloads": other,
         "clocks": clocks,
         "gpu_launches": int(st_tc[-1]["launches"]) * args.steps,
     }
@@ -431,6 +562,8 @@ def main():
     ap.add_argument("--ref-primaries", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing")
+    ap.add_argument("--no-other", action="store_true", help="skip the 20k and batched workloads")
+    ap.add_argument("--large", action="store_true", help="also time one forward of the 50M radial workload")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

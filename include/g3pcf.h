@@ -167,13 +167,26 @@ int g3pcf_backward(g3pcf_plan_t plan, const double* dzeta, double* dpos, double*
 int g3pcf_alm(g3pcf_plan_t plan, const int64_t* primaries, int64_t np, double* out);
 
 /* Autotuner (a project-written search, not in the paper): times the pair stage
- * on a bounded sample (the first min(n, 8192) points as primaries, all n as
- * secondaries) for cell resolutions around the density heuristic (and, when
- * the plan uses the fused pair kernel, two flush sizes), and keeps the fastest
- * on the plan (as if set with g3pcf_set_option).
- * pos/w as for g3pcf_compute_ex (flags: G3PCF_F_POS_F64 only).  chosen (HOST,
- * may be NULL) receives {cells per rmax, kflush, pair-stage microseconds}.
+ * on a bounded sample (the first min(n, 32768) points as primaries, all n as
+ * secondaries; best of two timed runs after one that sizes the workspace) over
+ * the cell resolution around the density heuristic (s - 1, s, s + 1) and, for
+ * the pair lists, the x refinement of the cells (4, 8, 16), or, for the fused
+ * kernel, two flush sizes; keeps the fastest on the plan (as if set with
+ * g3pcf_set_option).  For a batch, tune on its largest catalog (its pairs
+ * dominate the step).  pos/w as for g3pcf_compute_ex (flags: G3PCF_F_POS_F64
+ * only).  cache_path (may be NULL): a text file of earlier results, one line
+ * per key (nbins, lmax, LOS mode, kernel choice, SM count and the expected
+ * neighbours per point n (4/3) pi rmax^3 / box^3 in quarter-octave buckets); a
+ * hit applies the stored settings without timing anything, a miss tunes and
+ * appends a line (an unreadable or unwritable file only disables the cache).
+ * chosen (HOST, may be NULL): {cells per rmax, x refinement, kflush,
+ * pair-stage microseconds of the sample, 1 if taken from the cache}.
  * Allocates a temporary zeta buffer; synchronises the plan's stream. */
+int g3pcf_autotune_cached(g3pcf_plan_t plan, const void* pos, const float* w, int64_t n, int flags,
+                          const char* cache_path, int64_t* chosen);
+
+/* The same without a cache; chosen (HOST, may be NULL) receives {cells per
+ * rmax, kflush, pair-stage microseconds}. */
 int g3pcf_autotune(g3pcf_plan_t plan, const void* pos, const float* w, int64_t n, int flags,
                    int64_t* chosen);
 
@@ -235,6 +248,24 @@ int g3pcf_zeta_from_alm_noalloc(int nbins, int lmax, const float* alm, int64_t l
  * G3PCF_ERR_CUDA if the launch fails. */
 int g3pcf_isotropic(int nbins, int lmax, int ncat, const double* zeta, double* out, void* stream);
 
+/* Linear combination of zeta blocks: out = sum_c coef[c] zeta_c.  The paper's
+ * Sec. 6 corrects the measured 3PCF with random catalogs, whose own noise is
+ * averaged down by using many of them; with a batch of D - R_k catalogs (data
+ * plus the k-th random catalog at negative weight) and of the randoms R_k from
+ * one g3pcf_compute_batch, coef = 1/N_R on the first N_R blocks gives the mean
+ * zeta of the D - R field, and on the last N_R blocks the mean zeta of the
+ * randoms.  The sum runs over catalogs in index order (reruns are bit-identical).
+ *   zeta: device, ncat x g3pcf_zeta_size(nbins, lmax) complex FP64 (caller-owned).
+ *   coef: HOST, ncat finite doubles (copied into the launch).
+ *   out:  device, one zeta block (caller-owned; must not overlap zeta).
+ *   stream: cudaStream_t or NULL.  Asynchronous; allocates nothing.
+ * Errors: G3PCF_ERR_ARG for nbins / lmax out of range, ncat outside
+ * [1, G3PCF_MAX_COMBINE], a null pointer or a non-finite coefficient;
+ * G3PCF_ERR_CUDA if the launch fails. */
+#define G3PCF_MAX_COMBINE 256
+int g3pcf_zeta_combine(int nbins, int lmax, int ncat, const double* zeta, const double* coef, double* out,
+                       void* stream);
+
 /* Diagnostic: measured FP32 FMA throughput of the current device (TFLOP/s,
  * one FMA = 2 flop), best of 5 timed launches of an FMA-chain kernel that fills
  * every SM.  The denominator of the pair stage's roofline.  stream may be NULL.
@@ -276,6 +307,16 @@ int g3pcf_fp32_peak(double* tflops, void* stream);
  *                             (FP32, the fast path); 1 = the paper's monomial power
  *                             sums sum w x^a y^b z^c, a + b + c <= lmax (Sec. 3.3.2),
  *                             accumulated and converted in FP64 -- a slow cross-check
+ *   G3PCF_OPT_TEST_FAIL_ALLOC test hook for the allocation-failure path: with value
+ *                             k >= 1 the k-th workspace growth of this plan from now
+ *                             on fails once with G3PCF_ERR_ALLOC (host side, before
+ *                             anything is launched with that buffer); 0 = off
+ *   G3PCF_OPT_TEST_TC_TIMEOUT test hook for the bounded-wait path of the tensor-core
+ *                             contraction: 1 = the MMA thread's first wait for its
+ *                             operands is a single non-blocking test, so it gives up
+ *                             before the copies land; the kernel then flags
+ *                             G3PCF_ERR_TIMEOUT, waits (bounded) for its own copies,
+ *                             frees its tensor memory and returns; 0 = off
  * Returns G3PCF_ERR_ARG for unknown options or values out of range. */
 enum {
     G3PCF_OPT_CHUNK_ROWS = 1,
@@ -285,7 +326,9 @@ enum {
     G3PCF_OPT_LIST_BYTES = 5,
     G3PCF_OPT_BASIS = 7,
     G3PCF_OPT_X_REFINE = 8,
-    G3PCF_OPT_GRAD_PRECISION = 9
+    G3PCF_OPT_GRAD_PRECISION = 9,
+    G3PCF_OPT_TEST_FAIL_ALLOC = 10,
+    G3PCF_OPT_TEST_TC_TIMEOUT = 11
 };
 int g3pcf_set_option(g3pcf_plan_t plan, int option, int64_t value);
 

@@ -25,6 +25,7 @@ OPT_CHUNK_ROWS, OPT_CELLS_PER_RMAX, OPT_KFLUSH, OPT_PAIR_KERNELS, OPT_LIST_BYTES
 OPT_BASIS = 7
 OPT_X_REFINE = 8
 OPT_GRAD_PRECISION = 9
+OPT_TEST_FAIL_ALLOC, OPT_TEST_TC_TIMEOUT = 10, 11
 F_POS_F64, F_CONTRACT_FP32, F_NO_SYNC, F_KEEP_ALM, F_GRAPH = 1, 2, 4, 8, 16
 ERRORS = {0: "OK", -1: "ERR_ARG", -2: "ERR_RANGE", -3: "ERR_RMAX", -4: "ERR_ALLOC",
           -5: "ERR_CUDA", -6: "ERR_TIMEOUT", -7: "ERR_STATE", -8: "ERR_UNSUPPORTED"}
@@ -64,8 +65,12 @@ def lib():
         L.g3pcf_destroy.argtypes = [P]
         L.g3pcf_autotune.argtypes = [P, P, P, I64, I, P]
         L.g3pcf_autotune.restype = I
+        L.g3pcf_autotune_cached.argtypes = [P, P, P, I64, I, ctypes.c_char_p, P]
+        L.g3pcf_autotune_cached.restype = I
         L.g3pcf_isotropic.argtypes = [I, I, I, P, P, P]
         L.g3pcf_isotropic.restype = I
+        L.g3pcf_zeta_combine.argtypes = [I, I, I, P, P, P, P]
+        L.g3pcf_zeta_combine.restype = I
         L.g3pcf_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), P]
         L.g3pcf_fp32_peak.restype = I
         L.g3pcf_set_option.argtypes = [P, I, I64]
@@ -106,6 +111,24 @@ def isotropic(z, nbins: int, lmax: int):
     stream = torch.cuda.current_stream(zz.device).cuda_stream
     _check(lib().g3pcf_isotropic(nbins, lmax, ncat, _ptr(zz), _ptr(out), stream))
     return out[0] if single else out
+
+
+def zeta_combine(zb, coef, nbins: int, lmax: int):
+    """sum_c coef[c] zeta_c of a batch of zeta blocks (g3pcf_zeta_combine): zb is
+    (ncat, zsize) complex or (ncat, zsize, 2) float64 on a CUDA device; returns a
+    complex (zsize,) tensor on that device."""
+    import torch
+    zr = torch.view_as_real(zb) if zb.is_complex() else zb
+    zr = zr.contiguous()
+    c = np.ascontiguousarray(coef, dtype=np.float64)
+    ncat = zr.shape[0]
+    if c.size != ncat:
+        raise ValueError("one coefficient per catalog")
+    out = torch.empty((zr.shape[1], 2), dtype=torch.float64, device=zr.device)
+    _check(lib().g3pcf_zeta_combine(int(nbins), int(lmax), int(ncat), _ptr(zr),
+                                    c.ctypes.data_as(ctypes.c_void_p), _ptr(out),
+                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return torch.view_as_complex(out)
 
 
 def zeta_size(nbins: int, lmax: int) -> int:
@@ -249,6 +272,22 @@ class Plan:
         _check(lib().g3pcf_autotune(self._h, _ptr(pos), _ptr(w), pos.shape[0], flags,
                                     out.ctypes.data_as(ctypes.c_void_p)))
         return {"cells_per_rmax": int(out[0]), "kflush": int(out[1]), "pair_us": int(out[2])}
+
+    def autotune_cached(self, pos, w, cache_path=None) -> dict:
+        """Tune cell resolution and x refinement (pair lists) or flush size (fused
+        kernel) on a sample of this data, through the on-disk cache cache_path
+        (see g3pcf_autotune_cached)."""
+        import torch
+        pos = pos.contiguous()
+        w = w.contiguous()
+        flags = F_POS_F64 if pos.dtype == torch.float64 else 0
+        out = np.zeros(5, dtype=np.int64)
+        self._stream()
+        _check(lib().g3pcf_autotune_cached(self._h, _ptr(pos), _ptr(w), pos.shape[0], flags,
+                                           None if cache_path is None else str(cache_path).encode(),
+                                           out.ctypes.data_as(ctypes.c_void_p)))
+        return {"cells_per_rmax": int(out[0]), "x_refine": int(out[1]), "kflush": int(out[2]),
+                "pair_us": int(out[3]), "from_cache": bool(out[4])}
 
     def set_option(self, option: int, value: int):
         """Tuning knob (OPT_CHUNK_ROWS, OPT_CELLS_PER_RMAX, OPT_KFLUSH, OPT_PAIR_KERNELS,

@@ -155,6 +155,27 @@ def data_minus_randoms(data: Catalog, nrand_factor: int = 2, seed: int = 0) -> C
                    name="%s-minus-%dR" % (data.name, nrand_factor))
 
 
+def random_catalogs(data: Catalog, n_randoms: int, nrand_factor: int = 2, seed: int = 0):
+    """n_randoms random catalogs for the random-catalog correction of Sec. 6.  R_k
+    holds nrand_factor x n uniform points in the data's box (drawn from seed (seed, k))
+    with the equal positive weight alpha = sum(w_D) / n_R, so that its total weight
+    is the data's; D - R_k is the data followed by R_k at weight -alpha.  Returns
+    ([D - R_0, ...], [R_0, ...]) with the data's parameters."""
+    n_r = nrand_factor * data.n
+    alpha = float(np.sum(data.w, dtype=np.float64)) / max(n_r, 1)
+    dr, rr = [], []
+    for k in range(n_randoms):
+        rng = np.random.default_rng([seed, k])
+        rpos = uniform_positions(rng, n_r, data.box, data.pos.dtype.type)
+        rr.append(Catalog(rpos, np.full(n_r, alpha, dtype=np.float32), data.box, data.nbins, data.rmin,
+                          data.rmax, data.lmax, data.los_mode, name="R%d" % k))
+        dr.append(Catalog(np.concatenate([data.pos, rpos]),
+                          np.concatenate([data.w, np.full(n_r, -alpha, dtype=np.float32)]), data.box,
+                          data.nbins, data.rmin, data.rmax, data.lmax, data.los_mode,
+                          name="%s-minus-R%d" % (data.name, k)))
+    return dr, rr
+
+
 def small_case(kind: str, n: int, seed: int, box: float, nbins: int, rmin: float, rmax: float,
                lmax: int, los_mode: int = 0, dtype=np.float32, weight_kind="uniform_0.5_1.5"):
     """A small catalog with an explicit recipe, for parity tests."""

@@ -92,6 +92,8 @@ struct g3pcf_plan_s {
     std::vector<double> monocoef;
     int opt_basis = 0;             // G3PCF_OPT_BASIS
     int opt_grad = 0;              // G3PCF_OPT_GRAD_PRECISION (0 double-float, 1 FP32)
+    int test_fail_alloc = 0;       // G3PCF_OPT_TEST_FAIL_ALLOC countdown (0: off)
+    int test_tc_timeout = 0;       // G3PCF_OPT_TEST_TC_TIMEOUT
     std::vector<Tile> tiles;      // FP32 contraction tiles (edge T)
     std::vector<Tile> tiles_tc;   // tensor-core contraction tiles (edge T_tc)
     int T = 0, T_tc = 0;
@@ -539,7 +541,10 @@ struct CallSpec {
     int flags;
 };
 
-int ensure(DevBuf& b, size_t bytes, const char* what) {
+int ensure(g3pcf_plan_t P, DevBuf& b, size_t bytes, const char* what) {
+    // test hook (G3PCF_OPT_TEST_FAIL_ALLOC): the k-th workspace growth fails once
+    if (P->test_fail_alloc > 0 && !(bytes <= b.bytes && b.p) && --P->test_fail_alloc == 0)
+        return fail(G3PCF_ERR_ALLOC, "injected allocation failure (%s, %zu bytes)", what, bytes);
     if (b.ensure(bytes)) return fail(G3PCF_ERR_ALLOC, "cudaMalloc of %zu bytes (%s) failed", bytes, what);
     return 0;
 }
@@ -579,9 +584,9 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode
     const int qa = pa.q0, qb = pa.nprim;
     const int64_t nq = (int64_t)qb - qa;
     if (nq <= 0) return G3PCF_OK;
-    if (ensure(P->l_need, 4 * (size_t)qb, "pair-list bounds") ||
-        ensure(P->l_base, 4 * (size_t)qb, "pair-list bounds") ||
-        ensure(P->l_nch, 4 * (size_t)qb, "pair-list bounds"))
+    if (ensure(P, P->l_need, 4 * (size_t)qb, "pair-list bounds") ||
+        ensure(P, P->l_base, 4 * (size_t)qb, "pair-list bounds") ||
+        ensure(P, P->l_nch, 4 * (size_t)qb, "pair-list bounds"))
         return G3PCF_ERR_ALLOC;
     if ((size_t)nq > P->h_list_cap) {
         if (P->h_need) cudaFreeHost(P->h_need);
@@ -717,9 +722,9 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode
     if (cap < most)
         return fail(G3PCF_ERR_ALLOC, "pair lists of one primary (%lld chunks) exceed the list budget (%lld)",
                     (long long)most, (long long)cap);
-    if (cap > 0 && (ensure(P->l_pool, 128 * (size_t)cap, "pair lists") ||
-                    ensure(P->l_tag, 4 * (size_t)cap, "pair lists") ||
-                    ensure(P->l_ord, 4 * (size_t)cap, "pair lists")))
+    if (cap > 0 && (ensure(P, P->l_pool, 128 * (size_t)cap, "pair lists") ||
+                    ensure(P, P->l_tag, 4 * (size_t)cap, "pair lists") ||
+                    ensure(P, P->l_ord, 4 * (size_t)cap, "pair lists")))
         return G3PCF_ERR_ALLOC;
     la.chunks = P->l_pool.as<int>();
     la.tag = P->l_tag.as<int>();
@@ -728,9 +733,9 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode
         int64_t slack = 0, stride = 0;
         int npass = 0;
         graph_plan_sizes(cap, total, most, P->nbins, slack, stride, npass);
-        if (ensure(P->l_gbase, 8 * (size_t)nq, "pair-list plan") ||
-            ensure(P->l_scantmp, plan_scan_tmp_bytes(nq), "pair-list plan") ||
-            ensure(P->l_passq, 4 * (size_t)(npass + 1), "pair-list plan"))
+        if (ensure(P, P->l_gbase, 8 * (size_t)nq, "pair-list plan") ||
+            ensure(P, P->l_scantmp, plan_scan_tmp_bytes(nq), "pair-list plan") ||
+            ensure(P, P->l_passq, 4 * (size_t)(npass + 1), "pair-list plan"))
             return G3PCF_ERR_ALLOC;
         P->gl_events += 4 * npass;
         if (int r = ensure_events(P, P->gl_events)) return r;
@@ -812,11 +817,11 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
     P->cev_used = 0;
     CK(cudaEventRecord(P->ev[0], st));
     // zero outputs and counters
-    if (ensure(P->small, 256, "status")) return G3PCF_ERR_ALLOC;
+    if (ensure(P, P->small, 256, "status")) return G3PCF_ERR_ALLOC;
     int* d_status = P->small.as<int>();
     int* d_queue = d_status + 16;
     CK(cudaMemsetAsync(P->small.p, 0, 256, st));
-    if (ensure(P->counts, sizeof(unsigned long long) * B * c.ncat + 8, "counts")) return G3PCF_ERR_ALLOC;
+    if (ensure(P, P->counts, sizeof(unsigned long long) * B * c.ncat + 8, "counts")) return G3PCF_ERR_ALLOC;
     CK(cudaMemsetAsync(P->counts.p, 0, sizeof(unsigned long long) * B * c.ncat, st));
     CK(cudaMemsetAsync(c.zeta, 0, sizeof(double) * 2 * zs * c.ncat, st));
     // density for the grid: pair-weighted over catalogs
@@ -838,14 +843,14 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
         // ---- workspace
         const size_t hist_ints = radix_hist_ints(n);
         const size_t off_ints = (hist_ints > (size_t)n ? hist_ints : (size_t)n) + 1;
-        if (ensure(P->key_a, 4 * n, "keys") || ensure(P->key_b, 4 * n, "keys") ||
-            ensure(P->val_a, 4 * n, "vals") || ensure(P->val_b, 4 * n, "vals") ||
-            ensure(P->hist, 4 * hist_ints, "hist") || ensure(P->hist_off, 4 * off_ints, "hist") ||
-            ensure(P->scan_tmp, 4 * (scan_tmp_ints(off_ints) + 16), "scan") ||
-            ensure(P->pts, 16 * n, "points") || ensure(P->orig, 4 * n, "orig") ||
-            ensure(P->cstart, 4 * (ncells + 1), "cells") || ensure(P->plist, 4 * n, "plist"))
+        if (ensure(P, P->key_a, 4 * n, "keys") || ensure(P, P->key_b, 4 * n, "keys") ||
+            ensure(P, P->val_a, 4 * n, "vals") || ensure(P, P->val_b, 4 * n, "vals") ||
+            ensure(P, P->hist, 4 * hist_ints, "hist") || ensure(P, P->hist_off, 4 * off_ints, "hist") ||
+            ensure(P, P->scan_tmp, 4 * (scan_tmp_ints(off_ints) + 16), "scan") ||
+            ensure(P, P->pts, 16 * n, "points") || ensure(P, P->orig, 4 * n, "orig") ||
+            ensure(P, P->cstart, 4 * (ncells + 1), "cells") || ensure(P, P->plist, 4 * n, "plist"))
             return G3PCF_ERR_ALLOC;
-        if (c.pos_f64 && ensure(P->pts64, 24 * n, "points64")) return G3PCF_ERR_ALLOC;
+        if (c.pos_f64 && ensure(P, P->pts64, 24 * n, "points64")) return G3PCF_ERR_ALLOC;
         IndexBuffers ib{};
         ib.key_a = P->key_a.as<unsigned>();
         ib.key_b = P->key_b.as<unsigned>();
@@ -870,7 +875,7 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
         PrimRanges pr{};
         const PrimRanges* prp = nullptr;
         if (c.ncat > 1) {
-            if (ensure(P->d_catoff, 8 * (c.ncat + 1), "offsets")) return G3PCF_ERR_ALLOC;
+            if (ensure(P, P->d_catoff, 8 * (c.ncat + 1), "offsets")) return G3PCF_ERR_ALLOC;
             UP(P->d_catoff.p, c.offs.data(), 8 * (c.ncat + 1));
             d_catoff = P->d_catoff.as<int64_t>();
             // processing order: catalogs by decreasing size (heaviest first)
@@ -888,7 +893,7 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
                 rs[2 * c.ncat + k] = o;
                 o += rs[c.ncat + k];
             }
-            if (ensure(P->d_ranges, 4 * rs.size(), "ranges")) return G3PCF_ERR_ALLOC;
+            if (ensure(P, P->d_ranges, 4 * rs.size(), "ranges")) return G3PCF_ERR_ALLOC;
             UP(P->d_ranges.p, rs.data(), 4 * rs.size());
             pr.start = P->d_ranges.as<int>();
             pr.len = pr.start + c.ncat;
@@ -931,8 +936,8 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
         P->fixed_chunk = C;
         const int64_t nchunks = chunked ? (rows_all + C - 1) / C : 1;
         const int64_t rows_cap = chunked ? C : rows_all;
-        if (ensure(P->A, sizeof(float) * (size_t)P->RLP * (rows_cap > 0 ? rows_cap : 1), "multipoles") ||
-            ensure(P->wrow, sizeof(float) * (size_t)(rows_cap > 0 ? rows_cap : 1), "row weights"))
+        if (ensure(P, P->A, sizeof(float) * (size_t)P->RLP * (rows_cap > 0 ? rows_cap : 1), "multipoles") ||
+            ensure(P, P->wrow, sizeof(float) * (size_t)(rows_cap > 0 ? rows_cap : 1), "row weights"))
             return G3PCF_ERR_ALLOC;
         const std::vector<Tile>& tl = use_tc ? P->tiles_tc : P->tiles;
         const int T = use_tc ? P->T_tc : P->T;
@@ -990,12 +995,12 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
                 max_cats = std::max(max_cats, ccats[ch].size());
                 max_pad = std::max(max_pad, cpad[ch]);
             }
-            if (ensure(P->d_segs, sizeof(Segment) * max_segs, "segments") ||
-                ensure(P->d_segfirst, 4 * (c.ncat + 1), "segments") ||
-                ensure(P->partials, sizeof(double) * (size_t)part_stride * total_segs, "partials"))
+            if (ensure(P, P->d_segs, sizeof(Segment) * max_segs, "segments") ||
+                ensure(P, P->d_segfirst, 4 * (c.ncat + 1), "segments") ||
+                ensure(P, P->partials, sizeof(double) * (size_t)part_stride * total_segs, "partials"))
                 return G3PCF_ERR_ALLOC;
-            if (use_tc && (ensure(P->d_cats, 4 * max_cats, "catalog table") ||
-                           ensure(P->ops, (size_t)4 * P->RL * (max_pad > 0 ? max_pad : 1) * 2,
+            if (use_tc && (ensure(P, P->d_cats, 4 * max_cats, "catalog table") ||
+                           ensure(P, P->ops, (size_t)4 * P->RL * (max_pad > 0 ? max_pad : 1) * 2,
                                   "tensor-core operands")))
                 return G3PCF_ERR_ALLOC;
             UP(P->d_segfirst.p, segfirst.data(), 4 * (c.ncat + 1));
@@ -1065,7 +1070,8 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
                         return fail(G3PCF_ERR_CUDA, "operand split launch failed: %s", cudaGetErrorString(cudaGetLastError()));
                     const int rc = launch_contract_tc(P->ops.p, cpad[ch], P->RL, d_tl, ntiles,
                                                       P->d_segs.as<Segment>(), nsegs, part, part_stride,
-                                                      d_status + kNegWeightSlot, d_status, st);
+                                                      d_status + kNegWeightSlot, d_status, st,
+                                                      P->test_tc_timeout);
                     if (rc == -2) return fail(G3PCF_ERR_CUDA, "cuTensorMapEncodeTiled unavailable or failed");
                     if (rc != 0)
                         return fail(G3PCF_ERR_CUDA, "tensor-core contraction launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -1381,10 +1387,10 @@ int g3pcf_backward(g3pcf_plan_t P, const double* dzeta, double* dpos, double* dw
         // forward) and run each chunk's adjoint on the lists that recomputed them
         const int64_t C = P->fixed_chunk;
         const bool precise = P->opt_grad == 0;
-        if (precise ? (ensure(P->d_mreal64, sizeof(double) * adjoint_m_floats(P->nbins, P->lmax), "adjoint M") ||
-                       ensure(P->d_V64, sizeof(double) * (size_t)P->RLP * C, "adjoint V"))
-                    : (ensure(P->d_mreal, sizeof(float) * adjoint_m_floats(P->nbins, P->lmax), "adjoint M") ||
-                       ensure(P->d_V, sizeof(float) * (size_t)P->RLP * C, "adjoint V")))
+        if (precise ? (ensure(P, P->d_mreal64, sizeof(double) * adjoint_m_floats(P->nbins, P->lmax), "adjoint M") ||
+                       ensure(P, P->d_V64, sizeof(double) * (size_t)P->RLP * C, "adjoint V"))
+                    : (ensure(P, P->d_mreal, sizeof(float) * adjoint_m_floats(P->nbins, P->lmax), "adjoint M") ||
+                       ensure(P, P->d_V, sizeof(float) * (size_t)P->RLP * C, "adjoint V")))
             return G3PCF_ERR_ALLOC;
         int* d_status = P->small.as<int>();
         int* d_queue = d_status + 16;
@@ -1441,11 +1447,11 @@ int g3pcf_backward(g3pcf_plan_t P, const double* dzeta, double* dpos, double* dw
     }
     // the double-float pair pass (list path, G3PCF_OPT_GRAD_PRECISION 0) takes M and V in FP64
     const bool precise = P->opt_grad == 0 && P->opt_pair != 1;
-    if ((precise ? (ensure(P->d_mreal64, sizeof(double) * adjoint_m_floats(P->nbins, P->lmax) * ncat, "adjoint M") ||
-                    ensure(P->d_V64, sizeof(double) * (size_t)P->RLP * rows, "adjoint V"))
-                 : (ensure(P->d_mreal, sizeof(float) * adjoint_m_floats(P->nbins, P->lmax) * ncat, "adjoint M") ||
-                    ensure(P->d_V, sizeof(float) * (size_t)P->RLP * rows, "adjoint V"))) ||
-        ensure(P->d_vblk, sizeof(int4) * (blks.size() + 1), "adjoint blocks"))
+    if ((precise ? (ensure(P, P->d_mreal64, sizeof(double) * adjoint_m_floats(P->nbins, P->lmax) * ncat, "adjoint M") ||
+                    ensure(P, P->d_V64, sizeof(double) * (size_t)P->RLP * rows, "adjoint V"))
+                 : (ensure(P, P->d_mreal, sizeof(float) * adjoint_m_floats(P->nbins, P->lmax) * ncat, "adjoint M") ||
+                    ensure(P, P->d_V, sizeof(float) * (size_t)P->RLP * rows, "adjoint V"))) ||
+        ensure(P, P->d_vblk, sizeof(int4) * (blks.size() + 1), "adjoint blocks"))
         return G3PCF_ERR_ALLOC;
     CK(cudaMemcpyAsync(P->d_vblk.p, blks.data(), sizeof(int4) * blks.size(), cudaMemcpyHostToDevice, st));
     int* d_status = P->small.as<int>();
@@ -1528,6 +1534,14 @@ int g3pcf_set_option(g3pcf_plan_t P, int option, int64_t value) {
             if (value < 0 || value > 1) return fail(G3PCF_ERR_ARG, "basis must be 0 (Chebyshev) or 1 (monomials)");
             P->opt_basis = (int)value;
             return G3PCF_OK;
+        case G3PCF_OPT_TEST_FAIL_ALLOC:
+            if (value < 0 || value > 1000000) return fail(G3PCF_ERR_ARG, "allocation-failure countdown out of range");
+            P->test_fail_alloc = (int)value;
+            return G3PCF_OK;
+        case G3PCF_OPT_TEST_TC_TIMEOUT:
+            if (value < 0 || value > 1) return fail(G3PCF_ERR_ARG, "tensor-core timeout test must be 0 or 1");
+            P->test_tc_timeout = (int)value;
+            return G3PCF_OK;
         case G3PCF_OPT_GRAD_PRECISION:
             if (value < 0 || value > 1) return fail(G3PCF_ERR_ARG, "gradient precision must be 0 or 1");
             P->opt_grad = (int)value;
@@ -1542,21 +1556,79 @@ int g3pcf_set_option(g3pcf_plan_t P, int option, int64_t value) {
     }
 }
 
-int g3pcf_autotune(g3pcf_plan_t P, const void* pos, const float* w, int64_t n, int flags,
-                   int64_t* chosen) {
+namespace {
+
+// Tune-cache key: plan shape, line-of-sight mode, kernel choice, SM count and
+// the expected neighbours per point (n V / L^3) in quarter-octave buckets.
+std::string tune_key(g3pcf_plan_t P, int64_t n) {
+    const double V = 4.0 / 3.0 * M_PI * P->rmax * P->rmax * P->rmax;
+    const double nb = (double)n * V / (P->box * P->box * P->box);
+    const int bucket = (int)std::lround(4.0 * std::log2(nb > 1e-30 ? nb : 1e-30));
+    char k[160];
+    snprintf(k, sizeof(k), "g3pcf-tune-v1 nbins=%d lmax=%d los=%d pairk=%d sm=%d nbr4=%d", P->nbins, P->lmax,
+             P->los_mode, P->opt_pair == 1 ? 1 : 0, P->nsm, bucket);
+    return k;
+}
+
+// A cache line is "<key> | <cells> <xref> <kflush> <microseconds>".
+bool tune_lookup(const char* path, const std::string& key, int v[4]) {
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        const char* bar = std::strstr(line, " | ");
+        if (!bar || (size_t)(bar - line) != key.size() || std::strncmp(line, key.c_str(), key.size()) != 0) continue;
+        int a[4];
+        if (std::sscanf(bar + 3, "%d %d %d %d", &a[0], &a[1], &a[2], &a[3]) == 4 && a[0] >= 1 && a[0] <= 8 &&
+            a[1] >= 1 && a[1] <= 16 && a[2] >= 2 && a[2] <= 16) {
+            for (int t = 0; t < 4; ++t) v[t] = a[t];
+            found = true;  // the last matching line wins
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void tune_store(const char* path, const std::string& key, const int v[4]) {
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;  // an unwritable cache only costs a re-tune
+    std::fprintf(f, "%s | %d %d %d %d\n", key.c_str(), v[0], v[1], v[2], v[3]);
+    std::fclose(f);
+}
+
+}  // namespace
+
+int g3pcf_autotune_cached(g3pcf_plan_t P, const void* pos, const float* w, int64_t n, int flags,
+                          const char* cache_path, int64_t* chosen) {
     g_err.clear();
     if (int r = check_plan(P)) return r;
     if (n <= 0 || !pos || !w) return fail(G3PCF_ERR_ARG, "autotune needs n > 0 points");
     if (n >= G3PCF_MAX_POINTS) return fail(G3PCF_ERR_ARG, "n must be < 2^27");
     if (flags & ~G3PCF_F_POS_F64) return fail(G3PCF_ERR_ARG, "autotune accepts G3PCF_F_POS_F64 only");
     if (int r = setup_device(P)) return r;
+    const std::string key = tune_key(P, n);
+    int hit[4];
+    if (cache_path && *cache_path && tune_lookup(cache_path, key, hit)) {
+        P->opt_cells = hit[0];
+        P->opt_xref = hit[1];
+        P->kflush = hit[2];
+        if (chosen) {
+            chosen[0] = hit[0];
+            chosen[1] = hit[1];
+            chosen[2] = hit[2];
+            chosen[3] = hit[3];
+            chosen[4] = 1;
+        }
+        return G3PCF_OK;
+    }
     const int64_t zs = zsize_of(P->nbins, P->lmax);
     double* ztmp = nullptr;
     if (cudaMalloc(&ztmp, sizeof(double) * 2 * zs) != cudaSuccess) {
         cudaGetLastError();
         return fail(G3PCF_ERR_ALLOC, "autotune scratch allocation failed");
     }
-    // heuristic resolution and the largest flush size that fits
+    // the density heuristic's resolution, and the largest flush size that fits
     const double density = (double)n / (P->box * P->box * P->box);
     int s0 = (int)std::floor(P->rmax / std::cbrt(48.0 / density));
     s0 = s0 < 1 ? 1 : (s0 > 8 ? 8 : s0);
@@ -1566,45 +1638,52 @@ int g3pcf_autotune(g3pcf_plan_t P, const void* pos, const float* w, int64_t n, i
             kmax = kf;
             break;
         }
-    const int64_t saved_cells = P->opt_cells, saved_chunk = P->opt_chunk;
-    const int saved_kf = P->kflush;
+    const int saved_cells = P->opt_cells, saved_xref = P->opt_xref, saved_kf = P->kflush;
+    const int64_t saved_chunk = P->opt_chunk;
     double best = 1e300;
-    int best_s = s0, best_kf = kmax;
+    int best_s = s0, best_x = 8, best_kf = saved_kf;
     int rc = G3PCF_OK;
-    // the flush size matters to the fused kernel only (G3PCF_OPT_PAIR_KERNELS = 1)
+    // pair lists (the default): cell resolution x x refinement; the fused kernel
+    // (G3PCF_OPT_PAIR_KERNELS = 1): cell resolution x flush size
     const bool fused = P->opt_pair == 1;
-    const int kf_alt = fused ? (kmax > 6 ? kmax - 4 : kmax) : saved_kf;
-    for (int s = s0 - 1; s <= s0 + 2 && rc == G3PCF_OK; ++s) {
+    std::vector<std::pair<int, int>> second;
+    if (fused) {
+        second = {{8, kmax}, {8, kmax > 6 ? kmax - 4 : kmax}};
+    } else {
+        second = {{4, saved_kf}, {8, saved_kf}, {16, saved_kf}};
+    }
+    for (int s = s0 - 1; s <= s0 + 1 && rc == G3PCF_OK; ++s) {
         if (s < 1 || s > 8) continue;
-        for (int kf : {fused ? kmax : saved_kf, kf_alt}) {
+        for (const auto& xk : second) {
             P->opt_cells = s;
-            P->kflush = kf;
+            P->opt_xref = xk.first;
+            P->kflush = xk.second;
             CallSpec c;
             c.pos = pos;
             c.w = w;
             c.n = n;
-            c.n_primary = n < 8192 ? n : 8192;  // a bounded sample of primaries
+            c.n_primary = n < 32768 ? n : 32768;  // a bounded sample of primaries
             c.pos_f64 = (flags & G3PCF_F_POS_F64) ? 1 : 0;
             c.ncat = 1;
             c.offs = {0, n};
             c.zeta = ztmp;
             c.counts = nullptr;
             c.flags = G3PCF_F_CONTRACT_FP32;
-            double t = 0;
-            for (int rep = 0; rep < 2 && rc == G3PCF_OK; ++rep) {
+            double t = 1e300;
+            for (int rep = 0; rep < 3 && rc == G3PCF_OK; ++rep) {
                 rc = run_forward(P, c);
-                if (rc == G3PCF_OK && rep == 1) {
+                if (rc == G3PCF_OK && rep >= 1) {  // the first run sizes the workspace
                     float ms = 0.f;
                     cudaEventElapsedTime(&ms, P->ev[1], P->ev[2]);
-                    t = ms;
+                    t = std::min(t, (double)ms);
                 }
             }
             if (rc == G3PCF_OK && t < best) {
                 best = t;
                 best_s = s;
-                best_kf = kf;
+                best_x = xk.first;
+                best_kf = xk.second;
             }
-            if (kf == kf_alt) break;
         }
     }
     cudaFree(ztmp);
@@ -1612,18 +1691,33 @@ int g3pcf_autotune(g3pcf_plan_t P, const void* pos, const float* w, int64_t n, i
     P->have_alm = false;
     P->opt_chunk = saved_chunk;
     if (rc != G3PCF_OK) {
-        P->opt_cells = (int)saved_cells;
+        P->opt_cells = saved_cells;
+        P->opt_xref = saved_xref;
         P->kflush = saved_kf;
         return rc;
     }
     P->opt_cells = best_s;
+    P->opt_xref = best_x;
     P->kflush = best_kf;
+    const int v[4] = {best_s, best_x, best_kf, (int)std::min(best * 1000.0, 2e9)};
+    if (cache_path && *cache_path) tune_store(cache_path, key, v);
     if (chosen) {
-        chosen[0] = best_s;
-        chosen[1] = best_kf;
-        chosen[2] = (int64_t)(best * 1000.0);
+        for (int t = 0; t < 4; ++t) chosen[t] = v[t];
+        chosen[4] = 0;
     }
     return G3PCF_OK;
+}
+
+int g3pcf_autotune(g3pcf_plan_t P, const void* pos, const float* w, int64_t n, int flags,
+                   int64_t* chosen) {
+    int64_t c5[5] = {0, 0, 0, 0, 0};
+    const int rc = g3pcf_autotune_cached(P, pos, w, n, flags, nullptr, c5);
+    if (rc == G3PCF_OK && chosen) {
+        chosen[0] = c5[0];
+        chosen[1] = c5[2];
+        chosen[2] = c5[3];
+    }
+    return rc;
 }
 
 int g3pcf_status(g3pcf_plan_t P) {
@@ -1699,6 +1793,21 @@ int g3pcf_isotropic(int nbins, int lmax, int ncat, const double* zeta, double* o
     if (!zeta || !out) return fail(G3PCF_ERR_ARG, "isotropic: null pointer");
     if (launch_isotropic(zeta, nbins, lmax, ncat, out, static_cast<cudaStream_t>(stream)) != 0)
         return fail(G3PCF_ERR_CUDA, "isotropic launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return G3PCF_OK;
+}
+
+int g3pcf_zeta_combine(int nbins, int lmax, int ncat, const double* zeta, const double* coef, double* out,
+                       void* stream) {
+    g_err.clear();
+    if (nbins < 1 || nbins > G3PCF_MAX_NBINS || lmax < 0 || lmax > G3PCF_MAX_LMAX)
+        return fail(G3PCF_ERR_ARG, "combine: nbins in [1, %d], lmax in [0, %d]", G3PCF_MAX_NBINS, G3PCF_MAX_LMAX);
+    if (ncat < 1 || ncat > G3PCF_MAX_COMBINE)
+        return fail(G3PCF_ERR_ARG, "combine: ncat must be in [1, %d]", G3PCF_MAX_COMBINE);
+    if (!zeta || !coef || !out) return fail(G3PCF_ERR_ARG, "combine: null pointer");
+    for (int c = 0; c < ncat; ++c)
+        if (!std::isfinite(coef[c])) return fail(G3PCF_ERR_ARG, "combine: coefficient %d is not finite", c);
+    if (launch_combine(zeta, zsize_of(nbins, lmax), ncat, coef, out, static_cast<cudaStream_t>(stream)) != 0)
+        return fail(G3PCF_ERR_CUDA, "combine launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     return G3PCF_OK;
 }
 

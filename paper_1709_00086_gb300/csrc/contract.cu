@@ -160,7 +160,29 @@ __global__ void k_isotropic(const double* zeta, BlockInfo bi, int nbins, int lma
     out[e] = acc;
 }
 
+// out[e] = sum_c coef[c] zeta_c[e] over the 2 zsize doubles of a zeta block,
+// catalogs in index order (fixed summation order: reruns are bit-identical).
+__global__ void k_combine(const double* zeta, int64_t n2, int ncat, CombineCoef cf, double* out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n2; e += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < ncat; ++c) acc = fma(cf.c[c], zeta[(int64_t)c * n2 + e], acc);
+        out[e] = acc;
+    }
+}
+
 }  // namespace
+
+int launch_combine(const double* zeta, int64_t zsize, int ncat, const double* coef, double* out, cudaStream_t st) {
+    if (ncat < 1 || ncat > kMaxCombine) return -1;
+    CombineCoef cf{};
+    for (int c = 0; c < ncat; ++c) cf.c[c] = coef[c];
+    const int64_t n2 = 2 * zsize;
+    int64_t blocks = (n2 + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    k_combine<<<(unsigned)blocks, 256, 0, st>>>(zeta, n2, ncat, cf, out);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
 
 int contract_tile_dim_fp32() { return kT; }
 

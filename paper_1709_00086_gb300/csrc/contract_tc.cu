@@ -53,6 +53,18 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
                  : "memory");
 }
 
+// One non-blocking test of the phase (the error-path test's shortened first wait).
+__device__ __forceinline__ bool mbar_test(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait for the phase with the given parity; false on expiry.
 __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
     for (unsigned it = 0; it < kSpinLimit; ++it) {
@@ -120,6 +132,7 @@ struct TcArgs {
     int part_stride;
     const int* negw;       // 0: the right operands are the left ones (sqrt(w) A both sides)
     int* status;
+    int test_timeout;      // 1: the MMA thread's first wait is one non-blocking test (error-path test)
 };
 
 constexpr int kSubKB = 32;          // k-blocks per FP32 accumulation run (2048 primaries)
@@ -216,7 +229,9 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
                     break;
                 }
                 const int s = kb % kStages;
-                if (!mbar_wait(full0 + 8 * s, (kb / kStages) & 1)) {
+                const bool landed = (kb == 0 && a.test_timeout) ? mbar_test(full0, 0)
+                                                                : mbar_wait(full0 + 8 * s, (kb / kStages) & 1);
+                if (!landed) {
                     ok = false;
                     break;
                 }
@@ -417,7 +432,7 @@ int launch_split(const float* A, int RLP, int RL, const float* w, const int4* ca
 
 int launch_contract_tc(const void* ops, int64_t P_pad, int RL, const Tile* tiles, int ntiles,
                        const Segment* segs, int nsegs, double* partials, int part_stride,
-                       const int* negw, int* status, cudaStream_t st) {
+                       const int* negw, int* status, cudaStream_t st, int test_timeout) {
     if (ntiles <= 0 || nsegs <= 0) return 0;
     const __nv_bfloat16* base = static_cast<const __nv_bfloat16*>(ops);
     const int64_t n1 = (int64_t)RL * P_pad;
@@ -428,7 +443,7 @@ int launch_contract_tc(const void* ops, int64_t P_pad, int RL, const Tile* tiles
     if (cudaFuncSetAttribute(k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
         cudaSuccess)
         return -1;
-    TcArgs a{tiles, segs, partials, part_stride, negw, status};
+    TcArgs a{tiles, segs, partials, part_stride, negw, status, test_timeout};
     dim3 grid(ntiles, nsegs);
     k_contract_tc<<<grid, kTcWarps * 32, smem, st>>>(m[0], m[1], m[2], m[3], a);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;

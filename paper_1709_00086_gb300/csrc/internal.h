@@ -277,6 +277,10 @@ int launch_reduce(const double* partials, int part_stride, const int* seg_first,
                   int colmajor = 0);
 int pair_nrp(int lmax);
 int launch_isotropic(const double* zeta, int nbins, int lmax, int ncat, double* out, cudaStream_t st);
+// out = sum_c coef[c] zeta_c (coef: host, passed by value; ncat <= kMaxCombine)
+constexpr int kMaxCombine = 256;
+struct CombineCoef { double c[kMaxCombine]; };
+int launch_combine(const double* zeta, int64_t zsize, int ncat, const double* coef, double* out, cudaStream_t st);
 // contract_tc.cu: split-BF16 tcgen05 contraction
 int contract_tile_dim_tc();
 int contract_tc_kblock();
@@ -287,7 +291,7 @@ int launch_split(const float* A, int RLP, int RL, const float* w, const int4* ca
                  int64_t P_pad, const int* negw, void* ops, cudaStream_t st);
 int launch_contract_tc(const void* ops, int64_t P_pad, int RL, const Tile* tiles, int ntiles,
                        const Segment* segs, int nsegs, double* partials, int part_stride,
-                       const int* negw, int* status, cudaStream_t st);
+                       const int* negw, int* status, cudaStream_t st, int test_timeout = 0);
 
 // ---- adjoint.cu ----------------------------------------------------------------
 size_t adjoint_m_floats(int nbins, int lmax);

@@ -93,7 +93,11 @@ def test_set_option_validation():
     p.set_option(g3.OPT_X_REFINE, 16)
     p.set_option(g3.OPT_GRAD_PRECISION, 1)
     p.set_option(g3.OPT_GRAD_PRECISION, 0)
-    for opt, val in [(g3.OPT_GRAD_PRECISION, 2), (g3.OPT_GRAD_PRECISION, -1), (g3.OPT_CHUNK_ROWS, -1), (g3.OPT_CELLS_PER_RMAX, 9), (g3.OPT_KFLUSH, 1),
+    p.set_option(g3.OPT_TEST_FAIL_ALLOC, 3)
+    p.set_option(g3.OPT_TEST_FAIL_ALLOC, 0)
+    p.set_option(g3.OPT_TEST_TC_TIMEOUT, 1)
+    p.set_option(g3.OPT_TEST_TC_TIMEOUT, 0)
+    for opt, val in [(g3.OPT_TEST_FAIL_ALLOC, -1), (g3.OPT_TEST_TC_TIMEOUT, 2), (g3.OPT_GRAD_PRECISION, 2), (g3.OPT_GRAD_PRECISION, -1), (g3.OPT_CHUNK_ROWS, -1), (g3.OPT_CELLS_PER_RMAX, 9), (g3.OPT_KFLUSH, 1),
                      (g3.OPT_X_REFINE, 17), (g3.OPT_X_REFINE, -1),
                      (g3.OPT_KFLUSH, 17), (g3.OPT_PAIR_KERNELS, 3), (g3.OPT_PAIR_KERNELS, -1),
                      (g3.OPT_LIST_BYTES, -1), (g3.OPT_LIST_BYTES, 1000), (g3.OPT_BASIS, 2), (99, 1)]:
@@ -101,6 +105,21 @@ def test_set_option_validation():
             p.set_option(opt, val)
         assert ei.value.name == "ERR_ARG"
     p.close()
+
+
+def test_zeta_combine_argument_errors_before_device_work():
+    lib = g3.lib()
+    dummy = ctypes.c_void_p(16)
+    coef = (ctypes.c_double * 2)(0.5, 0.5)
+    bad = (ctypes.c_double * 2)(0.5, float("nan"))
+    assert lib.g3pcf_zeta_combine(0, 2, 2, dummy, coef, dummy, None) == -1     # nbins < 1
+    assert lib.g3pcf_zeta_combine(4, 11, 2, dummy, coef, dummy, None) == -1    # lmax > 10
+    assert lib.g3pcf_zeta_combine(4, 2, 0, dummy, coef, dummy, None) == -1     # ncat < 1
+    assert lib.g3pcf_zeta_combine(4, 2, 257, dummy, coef, dummy, None) == -1   # ncat > max
+    assert lib.g3pcf_zeta_combine(4, 2, 2, None, coef, dummy, None) == -1      # null zeta
+    assert lib.g3pcf_zeta_combine(4, 2, 2, dummy, None, dummy, None) == -1     # null coef
+    assert lib.g3pcf_zeta_combine(4, 2, 2, dummy, bad, dummy, None) == -1      # non-finite
+    assert "finite" in lib.g3pcf_last_error().decode()
 
 
 def test_isotropic_argument_errors_before_device_work():

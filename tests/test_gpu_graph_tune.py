@@ -91,6 +91,36 @@ def test_autotune_choices_and_result():
     assert maxrel(z.cpu().numpy(), zo) < 1e-4
 
 
+def test_autotune_cache_round_trip_and_tuned_parity(tmp_path):
+    # the first tune times the sweep and appends its winner to the cache; a new
+    # plan with the same shape and density reads it back without timing; a
+    # tuned forward (and a batch over the tuned grid) still matches the oracle
+    cat = catalogs.clustered_2m(n=60000, seed=23, box=700.0)
+    cache = tmp_path / "tune.txt"
+    pos, w = to_dev(cat, torch)
+    p1 = g3.Plan(**cat.params())
+    t1 = p1.autotune_cached(pos, w, cache)
+    assert not t1["from_cache"] and t1["pair_us"] > 0
+    assert 1 <= t1["cells_per_rmax"] <= 8 and t1["x_refine"] in (4, 8, 16)
+    lines = cache.read_text().strip().splitlines()
+    assert len(lines) == 1 and "nbins=10 lmax=10" in lines[0]
+    p2 = g3.Plan(**cat.params())
+    t2 = p2.autotune_cached(pos, w, cache)
+    assert t2["from_cache"] and (t2["cells_per_rmax"], t2["x_refine"]) == (t1["cells_per_rmax"], t1["x_refine"])
+    assert len(cache.read_text().strip().splitlines()) == 1
+    z, c = p2.compute(pos, w, n_primary=300, fp32_contraction=True)
+    zo, co = oracle_zeta(cat, n_primary=300)
+    np.testing.assert_array_equal(c.cpu().numpy(), co)
+    assert maxrel(z.cpu().numpy(), zo) < 1e-5
+    # every x refinement and resolution the tuner may pick gives the same counts
+    for s, x in ((max(1, t1["cells_per_rmax"] - 1), 4), (t1["cells_per_rmax"] + 1, 16)):
+        p3 = g3.Plan(**cat.params())
+        p3.set_option(g3.OPT_CELLS_PER_RMAX, min(s, 8))
+        p3.set_option(g3.OPT_X_REFINE, x)
+        _, c3 = p3.compute(pos, w, n_primary=300, fp32_contraction=True)
+        np.testing.assert_array_equal(c3.cpu().numpy(), co)
+
+
 def test_graph_replay_with_denser_data_falls_back():
     # capture on a catalog of scattered points, then overwrite the buffers with
     # a tightly clustered catalog of the same size: its lists outgrow the pool
