@@ -530,7 +530,14 @@ def run_ours(args):
                                     "(nominal 2 x 128 lanes x %d SMs x %.0f MHz = %.1f)" % (n_sm, clk_max, nominal),
                      "flops_per_pair": pair_flops(L),
                      "executed_flops_per_pair": accum_exec_flops(L),
-                     "executed_tflops": executed},
+                     "executed_tflops": executed,
+                     "frac_executed": executed / fp32_peak,
+                     # the whole pair stage (candidate scan + accumulate), algorithmic and executed
+                     "pair_stage": {"ms": pair_ms,
+                                    "achieved": pairs * pair_flops(L) / (pair_ms / 1e3) / 1e12,
+                                    "frac": pairs * pair_flops(L) / (pair_ms / 1e3) / 1e12 / fp32_peak,
+                                    "frac_executed": pairs * accum_exec_flops(L) / (pair_ms / 1e3) / 1e12
+                                                     / fp32_peak}},
         "e2e": {"value": e2e_val, "unit": "pairs/s",
                 "h2d_bytes_per_step": int(hpos.numel() * 4 + hw.numel() * 4),
                 "d2h_bytes_per_step": int(hz.numel() * 8)},
