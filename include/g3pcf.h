@@ -313,10 +313,10 @@ int g3pcf_fp32_peak(double* tflops, void* stream);
  *                             anything is launched with that buffer); 0 = off
  *   G3PCF_OPT_TEST_TC_TIMEOUT test hook for the bounded-wait path of the tensor-core
  *                             contraction: 1 = the MMA thread's first wait for its
- *                             operands is a single non-blocking test, so it gives up
- *                             before the copies land; the kernel then flags
- *                             G3PCF_ERR_TIMEOUT, waits (bounded) for its own copies,
- *                             frees its tensor memory and returns; 0 = off
+ *                             operands gives up at once, as if its bound had expired;
+ *                             the kernel then flags G3PCF_ERR_TIMEOUT, waits (bounded)
+ *                             for its own copies, frees its tensor memory and
+ *                             returns; 0 = off
  * Returns G3PCF_ERR_ARG for unknown options or values out of range. */
 enum {
     G3PCF_OPT_CHUNK_ROWS = 1,

@@ -96,6 +96,7 @@ struct g3pcf_plan_s {
     int test_tc_timeout = 0;       // G3PCF_OPT_TEST_TC_TIMEOUT
     std::vector<Tile> tiles;      // FP32 contraction tiles (edge T)
     std::vector<Tile> tiles_tc;   // tensor-core contraction tiles (edge T_tc)
+    std::vector<TcStrip> strips_tc;  // their strips (one or two tiles of a row panel)
     int T = 0, T_tc = 0;
     int kflush = 16;
     // device buffers
@@ -103,7 +104,7 @@ struct g3pcf_plan_s {
     DevBuf small;       // status, queue
     DevBuf counts, A, partials, d_tiles, d_segs, d_segfirst, d_colmap, d_colscale, d_catoff;
     DevBuf d_colconv, d_colcoef, d_bintab_s, d_slotconv, d_slotcoef, d_monoexp, d_monoconv, d_monoidx, d_monocoef;
-    DevBuf d_ranges, d_tiles_tc, ops, d_cats, d_mreal, d_V, d_bintab, wrow, d_vblk;
+    DevBuf d_ranges, d_tiles_tc, d_cats, d_mreal, d_V, d_bintab, wrow, d_vblk, d_strips_tc, d_items;
     DevBuf d_colcoef64, d_slotcoef64, d_mreal64, d_V64;
     int64_t opt_chunk = 0;   // G3PCF_OPT_CHUNK_ROWS
     // pinned staging for host -> device tables (capturable copies); offset
@@ -221,6 +222,10 @@ int upload_consts(g3pcf_plan_t P) {
         P->d_tiles_tc.ensure(P->tiles_tc.size() * sizeof(Tile)))
         return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (constants)");
     CK(cudaMemcpy(P->d_tiles_tc.p, P->tiles_tc.data(), P->tiles_tc.size() * sizeof(Tile),
+                  cudaMemcpyHostToDevice));
+    if (P->d_strips_tc.ensure(P->strips_tc.size() * sizeof(TcStrip)))
+        return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (constants)");
+    CK(cudaMemcpy(P->d_strips_tc.p, P->strips_tc.data(), P->strips_tc.size() * sizeof(TcStrip),
                   cudaMemcpyHostToDevice));
     if (P->d_bintab.ensure(P->bintab.size()) || P->d_bintab_s.ensure(P->bintab_s.size()))
         return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (bin table)");
@@ -926,7 +931,7 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
                 CK(cudaMemGetInfo(&fr, &tot));
                 double budget = 0.4 * (double)fr;
                 if (budget > 48e9) budget = 48e9;
-                const double per_row = 4.0 * P->RLP + 4.0 + (use_tc ? 8.0 * P->RL : 0.0);
+                const double per_row = 4.0 * P->RLP + 4.0;
                 C = (int64_t)(budget / per_row) / KB * KB;
                 if (C < KB) C = KB;
             }
@@ -946,6 +951,12 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
         const int part_stride = ntiles * T * T;
         // segments of every chunk (partial slots are global across chunks)
         std::vector<std::vector<Segment>> csegs(nchunks);
+        // tensor-core work units per virtual segment: a two-tile strip takes one
+        // segment per CTA, a one-tile strip two
+        double tc_units = 0.0;
+        for (const TcStrip& sp : P->strips_tc) tc_units += sp.ntile == 2 ? 1.0 : 0.5;
+        if (tc_units <= 0.0) tc_units = 1.0;
+        const int64_t rows_tot = chunked ? std::min<int64_t>(C, rows_all) : rows_all;
         std::vector<int> segfirst(c.ncat + 1, 0);
         std::vector<std::vector<int>> ccats(nchunks);
         std::vector<int64_t> cpad(nchunks, 0);
@@ -959,16 +970,24 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
                 const int64_t r1 = chunked ? q1 - q0 : ((c.ncat > 1) ? c.offs[k + 1] : c.n_primary);
                 const int64_t len = r1 - r0;
                 if (use_tc) {
-                    // padded primary coordinates: every catalog starts on a k-block
+                    // padded primary coordinates: every catalog starts on a k-block; an
+                    // even number V of virtual segments per catalog, about
+                    // nsm * (catalog share of the primaries) / (work units per segment)
                     const int64_t plen = (len + KB - 1) / KB * KB;
                     ccats[ch].insert(ccats[ch].end(), {(int)cpad[ch], (int)r0, (int)len, 0});
-                    int64_t seg = (plen / 8 + KB - 1) / KB * KB;
-                    if (seg < 64 * KB) seg = 64 * KB;
-                    for (int64_t s0 = 0; s0 < plen; s0 += seg) {
+                    const double share = rows_tot > 0 ? (double)plen / (double)rows_tot : 1.0;
+                    int64_t V = 2 * (int64_t)std::llround(share * P->nsm / (2.0 * tc_units));
+                    // at least one full FP32 accumulation run (2048 primaries) per segment
+                    const int64_t vmax = 2 * (plen / (2 * 2048));
+                    if (V > vmax) V = vmax;
+                    if (V < 2) V = 2;
+                    const int64_t seg = ((plen + V - 1) / V + KB - 1) / KB * KB;
+                    for (int64_t v = 0; v < V; ++v) {
                         Segment sg;
                         sg.cat = k;
+                        const int64_t s0 = std::min(plen, v * seg), s1 = std::min(plen, (v + 1) * seg);
                         sg.row0 = (int)(cpad[ch] + s0);
-                        sg.row1 = (int)(cpad[ch] + (s0 + seg < plen ? s0 + seg : plen));
+                        sg.row1 = (int)(cpad[ch] + s1);
                         csegs[ch].push_back(sg);
                     }
                     cpad[ch] += plen;
@@ -989,20 +1008,15 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
         segfirst[c.ncat] = total_segs;
         if (total_segs > 0) {
             size_t max_segs = 0, max_cats = 1;
-            int64_t max_pad = 0;
             for (int64_t ch = 0; ch < nchunks; ++ch) {
                 max_segs = std::max(max_segs, csegs[ch].size());
                 max_cats = std::max(max_cats, ccats[ch].size());
-                max_pad = std::max(max_pad, cpad[ch]);
             }
             if (ensure(P, P->d_segs, sizeof(Segment) * max_segs, "segments") ||
                 ensure(P, P->d_segfirst, 4 * (c.ncat + 1), "segments") ||
                 ensure(P, P->partials, sizeof(double) * (size_t)part_stride * total_segs, "partials"))
                 return G3PCF_ERR_ALLOC;
-            if (use_tc && (ensure(P, P->d_cats, 4 * max_cats, "catalog table") ||
-                           ensure(P, P->ops, (size_t)4 * P->RL * (max_pad > 0 ? max_pad : 1) * 2,
-                                  "tensor-core operands")))
-                return G3PCF_ERR_ALLOC;
+            if (use_tc && ensure(P, P->d_cats, 4 * max_cats, "catalog table")) return G3PCF_ERR_ALLOC;
             UP(P->d_segfirst.p, segfirst.data(), 4 * (c.ncat + 1));
         }
         // per-chunk stage events (created outside a capture; a capture that finds
@@ -1063,13 +1077,30 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
                 UP(P->d_segs.p, segs.data(), sizeof(Segment) * nsegs);
                 if (use_tc) {
                     UP(P->d_cats.p, ccats[ch].data(), 4 * ccats[ch].size());
-                    P->launches += 2;
-                    if (launch_split(P->A.as<float>(), P->RLP, P->RL, P->wrow.as<float>(), P->d_cats.as<int4>(),
-                                     (int)(ccats[ch].size() / 4), cpad[ch], d_status + kNegWeightSlot, P->ops.p,
-                                     st) != 0)
-                        return fail(G3PCF_ERR_CUDA, "operand split launch failed: %s", cudaGetErrorString(cudaGetLastError()));
-                    const int rc = launch_contract_tc(P->ops.p, cpad[ch], P->RL, d_tl, ntiles,
-                                                      P->d_segs.as<Segment>(), nsegs, part, part_stride,
+                    P->launches += 1;
+                    // work items: every strip over every virtual segment of every
+                    // catalog (one-tile strips two segments at a time)
+                    std::vector<TcItem> items;
+                    for (int s0 = 0; s0 < nsegs;) {
+                        int s1 = s0;
+                        while (s1 < nsegs && segs[s1].cat == segs[s0].cat) ++s1;
+                        for (int k = 0; k < (int)P->strips_tc.size(); ++k) {
+                            const int step = P->strips_tc[k].ntile == 2 ? 1 : 2;
+                            for (int v = s0; v < s1; v += step)
+                                items.push_back(TcItem{k, v, std::min(step, s1 - v), 0});
+                        }
+                        s0 = s1;
+                    }
+                    if (ensure(P, P->d_items, sizeof(TcItem) * items.size(), "tensor-core work items"))
+                        return G3PCF_ERR_ALLOC;
+                    UP(P->d_items.p, items.data(), sizeof(TcItem) * items.size());
+                    // the rows of A written by this pass: the map reads zeros past them, so
+                    // the padding primaries of the last k-block never meet stale memory
+                    const int64_t rows_written = chunked ? q1 - q0 : rows_all;
+                    const int rc = launch_contract_tc(P->A.as<float>(), P->RLP, P->RL, rows_written, P->wrow.as<float>(),
+                                                      P->d_cats.as<int4>(), d_tl, P->d_strips_tc.as<TcStrip>(),
+                                                      P->d_items.as<TcItem>(), (int)items.size(),
+                                                      P->d_segs.as<Segment>(), part, part_stride,
                                                       d_status + kNegWeightSlot, d_status, st,
                                                       P->test_tc_timeout);
                     if (rc == -2) return fail(G3PCF_ERR_CUDA, "cuTensorMapEncodeTiled unavailable or failed");
@@ -1264,6 +1295,9 @@ int g3pcf_plan(g3pcf_plan_t* out, int nbins, double rmin, double rmax, int lmax,
         return fail(G3PCF_ERR_ARG, "too many contraction tiles");
     }
     P->tiles_tc.resize(nt);
+    P->strips_tc.resize(nt);
+    const int nstrip = make_strips(P->tiles_tc.data(), nt, P->strips_tc.data(), nt);
+    P->strips_tc.resize(nstrip > 0 ? nstrip : 0);
     *out = P;
     return G3PCF_OK;
 }
@@ -1819,7 +1853,8 @@ int g3pcf_destroy(g3pcf_plan_t P) {
                       &P->scan_tmp, &P->pts, &P->pts64, &P->orig, &P->cstart, &P->plist,
                       &P->small, &P->counts, &P->A, &P->partials, &P->d_tiles, &P->d_segs,
                       &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_colconv, &P->d_colcoef, &P->d_bintab_s, &P->d_slotconv, &P->d_slotcoef, &P->d_monoexp, &P->d_monoconv, &P->d_monoidx, &P->d_monocoef, &P->d_catoff, &P->d_ranges,
-                      &P->d_tiles_tc, &P->ops, &P->d_cats, &P->d_mreal, &P->d_V, &P->d_bintab, &P->d_vblk,
+                      &P->d_tiles_tc, &P->d_cats, &P->d_mreal, &P->d_V, &P->d_bintab, &P->d_vblk,
+                      &P->d_strips_tc, &P->d_items,
                       &P->d_colcoef64, &P->d_slotcoef64, &P->d_mreal64, &P->d_V64,
                       &P->wrow, &P->l_need, &P->l_base, &P->l_nch, &P->l_pool, &P->l_tag, &P->l_ord,
                       &P->l_gbase, &P->l_scantmp, &P->l_passq};

@@ -12,15 +12,29 @@
 // dropped).  With no negative weight L = R = sqrt(w) (.) A, so one hi / lo
 // pair serves both sides; otherwise L = A (unweighted) and R = w (.) A.
 //
-// Data flow.  k_split writes the operands K-major (primaries contiguous)
-// as bf16 [column][primary].  k_contract_tc: one CTA per (128 x 128 output
-// tile, segment of primaries); one thread issues TMA tile loads (128B
-// swizzle, 3-stage mbarrier ring) and the tcgen05.mma instructions, the
-// accumulator lives in 128 TMEM columns, and four warps read it back with
-// tcgen05.ld and write FP64 partials (one per (segment, tile)) that the FP64
-// reduction adds in a fixed order.  Every wait is bounded: on expiry the
-// kernel records a timeout in the status word, drains its own copies (again
-// bounded), frees its TMEM and returns.
+// Data flow.  The operands are formed inside the kernel from the FP32
+// multipole rows A (no separate split pass, no operand buffer): one CTA per
+// work item = (strip, range of primaries).  A strip is one or two 128 x 128
+// output tiles side by side in one row panel of an m block, computed as one
+// M = 128, N = 128 or 256 MMA, so the row panel is formed once for both
+// tiles; when the strip starts on the diagonal of the symmetric form its row
+// panel is the first column panel.  The primaries of every catalog are cut
+// into an even number of equal "virtual segments"; a two-tile strip takes one
+// per CTA and a one-tile strip two, so that every CTA does the same MMA work
+// (its partial goes to the first slot and the second is zeroed).
+//   warps 5-12 (converters): per k-block of 64 primaries, read the rows of A
+//     (coalesced 128-byte pieces of each row), scale them by sqrt(w) (or by 1
+//     and w), split into bf16 hi and lo and store them K-major in the 128-byte
+//     swizzled shared-memory layout of the MMA descriptors; only the columns of
+//     the strip's m block are read (the rest of a panel is zero); a ring of 2
+//     to 7 stages, handed to the MMA thread through mbarriers;
+//   warp 4 (one thread): tcgen05.mma into an N-column TMEM accumulator,
+//     double-buffered per run of kSubKB k-blocks;
+//   warps 0-3 (drain): tcgen05.ld of each finished run, added to the FP64
+//     partials (one per (virtual segment, tile)) that the FP64 reduction adds
+//     in a fixed order.
+// Every wait is bounded: on expiry the kernel records a timeout in the status
+// word, all warps stop at an agreed point, the TMEM is freed and it returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -35,9 +49,19 @@ namespace {
 
 constexpr int kTT = 128;          // output tile edge (M = N = 128)
 constexpr int kKB = 64;           // primaries per k-block (one 128-byte swizzle row of bf16)
-constexpr int kStages = 3;
-constexpr int kOpBytes = kTT * kKB * 2;          // one operand tile: 16 KB
-constexpr int kStageBytes = 4 * kOpBytes;        // L_hi, L_lo, R_hi, R_lo
+constexpr int kOpBytes = kTT * kKB * 2;          // one operand box (128 rows x 64 primaries): 16 KB
+// stage buffers: 2 to 6 operand boxes per stage (R hi / lo of one or two panels,
+// L hi / lo unless shared with R), as many stages as fit
+constexpr int kBufBytes = 13 * kOpBytes;         // 208 KB: operand stages + FP32 staging slots
+constexpr int kMaxStages = 7;
+// FP32 staging of one unit (one panel of one k-block): rows of A for the 64
+// primaries, 132 columns from the panel's first column rounded down to a
+// multiple of 4 (a TMA box must start on a 16-byte boundary)
+constexpr int kStgCols = kTT + 4;
+constexpr int kStgBytes = kKB * kStgCols * 4;    // 33,792 bytes
+
+constexpr int kMaxStg = 4;
+static_assert(kBufBytes + 1024 + 1024 <= 227 * 1024, "stage buffers and barriers fit in shared memory");
 constexpr unsigned kSpinLimit = 1u << 26;        // bounded waits
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -51,18 +75,6 @@ __device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
 __device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                  : "memory");
-}
-
-// One non-blocking test of the phase (the error-path test's shortened first wait).
-__device__ __forceinline__ bool mbar_test(unsigned bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
 }
 
 // Bounded wait for the phase with the given parity; false on expiry.
@@ -126,17 +138,28 @@ __device__ __forceinline__ void mma_commit(unsigned bar) {
 }
 
 struct TcArgs {
+    const float* A;        // multipole rows (FP32), row pitch RLP (also read through the tensor map)
+    int RLP;
+    const float* wrow;     // weight of every A row
+    const int4* cats;      // per catalog {padded start, first A row, length, 0}
     const Tile* tiles;
-    const Segment* segs;   // row ranges in padded primary coordinates (multiples of kKB)
-    double* partials;      // per (segment, tile): 128 x 128 doubles, column-major [c][r]
+    const TcStrip* strips;
+    const TcItem* items;
+    const Segment* segs;   // virtual segments in padded primary coordinates (multiples of kKB)
+    double* partials;      // per (virtual segment, tile): 128 x 128 doubles, column-major [c][r]
     int part_stride;
-    const int* negw;       // 0: the right operands are the left ones (sqrt(w) A both sides)
+    const int* negw;       // 0: both operand sides are sqrt(w) A (no negative weight)
     int* status;
-    int test_timeout;      // 1: the MMA thread's first wait is one non-blocking test (error-path test)
+    int test_timeout;      // 1: the MMA thread's first wait gives up at once (error-path test)
 };
 
 constexpr int kSubKB = 32;          // k-blocks per FP32 accumulation run (2048 primaries)
-constexpr int kTcWarps = 5;         // warps 0-3: TMEM drain (lanes 0-127); warp 4: TMA + MMA
+constexpr int kDrainWarps = 4;      // warps 0-3: TMEM drain (lanes 0-127)
+constexpr int kMmaWarp = 4;         // warp 4: MMA issue
+constexpr int kTmaWarp = 5;         // warp 5: TMA loads of the FP32 rows
+constexpr int kCvtWarps = 16;       // warps 6-21: operand formation
+constexpr int kCvtThreads = kCvtWarps * 32;
+constexpr int kTcWarps = kDrainWarps + 2 + kCvtWarps;
 
 __device__ __forceinline__ void tmem_ld32(unsigned taddr, unsigned (&r)[32]) {
     asm volatile(
@@ -152,37 +175,95 @@ __device__ __forceinline__ void tmem_ld32(unsigned taddr, unsigned (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// One CTA = one (tile, segment).  The segment's k-blocks are accumulated in
-// runs of kSubKB into one of two TMEM buffers (columns [0,128) and
-// [128,256)); while the MMA warp fills one buffer the drain warps add the
-// other into the FP64 partial, which bounds every FP32 accumulation run to
+// Bounded wait that also gives up when another warp has flagged an abort.
+__device__ __forceinline__ bool mbar_wait_or_abort(unsigned bar, unsigned parity, volatile int* abort_flag) {
+    for (unsigned it = 0; it < kSpinLimit; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (*abort_flag) return false;
+    }
+    return false;
+}
+
+// Barrier 1 over the converter warps with an OR of a predicate: every converter
+// thread gets the same answer, so they stop (or go on) together.
+__device__ __forceinline__ bool cvt_barrier_any(bool pred) {
+    unsigned r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((unsigned)pred), "r"(kCvtThreads)
+        : "memory");
+    return r != 0;
+}
+
+// One CTA = one work item (strip, virtual segments).  The k-blocks are
+// accumulated in runs of kSubKB into one of two TMEM buffers (columns [0, N)
+// and [N, 2N)); while the MMA warp fills one buffer the drain warps add the
+// other into the FP64 partials, which bounds every FP32 accumulation run to
 // 3 * kSubKB * 4 MMA steps whatever the segment length.
+//   units: the panels of every k-block in order (u = nb kb + b; panel b < nt
+//   is the b-th column panel, b = nt the row panel when it is not shared);
+//   the TMA thread stages unit u in slot u % S, the converters turn it into
+//   the operand boxes of stage kb % O, the MMA thread consumes the stage.
 __global__ void __launch_bounds__(kTcWarps * 32, 1)
-    k_contract_tc(const __grid_constant__ CUtensorMap mLh, const __grid_constant__ CUtensorMap mLl,
-                  const __grid_constant__ CUtensorMap mRh, const __grid_constant__ CUtensorMap mRl,
-                  TcArgs a) {
+    k_contract_tc(const __grid_constant__ CUtensorMap mA, TcArgs a) {
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
-    __shared__ __align__(8) unsigned long long bars[2 * kStages + 4];
+    __shared__ __align__(8) unsigned long long bars[2 * kMaxStages + 2 * kMaxStg + 4];
     __shared__ unsigned tmem_slot;
     __shared__ int abort_flag;
+    __shared__ __align__(16) float meta_sl[2][kKB];  // per k-block: scale of each primary on the row (L) side
+    __shared__ __align__(16) float meta_sr[2][kKB];  // ... on the column (R) side
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const Tile t = a.tiles[blockIdx.x];
-    const Segment sg = a.segs[blockIdx.y];
-    const int kb0 = sg.row0 / kKB;
-    const int nkb = (sg.row1 - sg.row0 + kKB - 1) / kKB;
+    const TcItem it = a.items[blockIdx.x];
+    const TcStrip sp = a.strips[it.strip];
+    const Segment sg0 = a.segs[it.vseg0];
+    const int row0 = sg0.row0, row1 = a.segs[it.vseg0 + it.nvseg - 1].row1;
+    const int kb0 = row0 / kKB;
+    const int nkb = (row1 - row0 + kKB - 1) / kKB;
     const int nsub = (nkb + kSubKB - 1) / kSubKB;
+    const int nt = sp.ntile;   // tiles side by side: N = 128 nt
+    const int N = kTT * nt;
     const unsigned raw = smem_u32(tc_smem_raw);
     const unsigned sbase = (raw + 1023u) & ~1023u;  // 1024-byte aligned stage buffers
-    const unsigned full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[kStages]),
-                   ready0 = smem_u32(&bars[2 * kStages]), drained0 = smem_u32(&bars[2 * kStages + 2]);
+    unsigned char* sgen = tc_smem_raw + (sbase - raw);
+    // no negative weight: both sides are sqrt(w) A; a strip that starts on the
+    // diagonal then finds its row panel as the first column panel
+    const bool sym = *a.negw == 0;
+    const bool lshare = sym && sp.xrow == sp.xcol;
+    const int nb = lshare ? nt : nt + 1;               // units (panels) per k-block
+    const unsigned stage_bytes = (unsigned)(2 * nb) * kOpBytes;
+    // staging slots first (up to two k-blocks of copies in flight), then as many
+    // operand stages as fit (>= 1 for every strip shape)
+    int S = (int)((kBufBytes - stage_bytes) / kStgBytes);
+    S = S < kMaxStg ? S : kMaxStg;
+    int O = (int)((kBufBytes - S * kStgBytes) / stage_bytes);
+    O = O < kMaxStages ? O : kMaxStages;
+    const unsigned stg0 = (unsigned)O * stage_bytes;   // staging after the operand stages
+    const unsigned ofull0 = smem_u32(&bars[0]), oempty0 = smem_u32(&bars[kMaxStages]);
+    const unsigned sfull0 = smem_u32(&bars[2 * kMaxStages]), sempty0 = smem_u32(&bars[2 * kMaxStages + kMaxStg]);
+    const unsigned ready0 = smem_u32(&bars[2 * kMaxStages + 2 * kMaxStg]);
+    const unsigned drained0 = ready0 + 16;
+    const int nunits = nkb * nb;
+    const int4 cat = a.cats[sg0.cat];
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
+        for (int s = 0; s < kMaxStages; ++s) {
+            mbar_init(ofull0 + 8 * s, kCvtWarps);  // one arrival per converter warp
+            mbar_init(oempty0 + 8 * s, 1);         // the MMA thread's commit
+        }
+        for (int s = 0; s < kMaxStg; ++s) {
+            mbar_init(sfull0 + 8 * s, 1);          // TMA bytes
+            mbar_init(sempty0 + 8 * s, kCvtWarps);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(ready0 + 8 * b, 1);
-            mbar_init(drained0 + 8 * b, 4);  // one arrival per drain warp
+            mbar_init(drained0 + 8 * b, kDrainWarps);
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -190,7 +271,7 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_slot)),
-                     "r"(2 * kTT)
+                     "r"(2 * N)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -198,28 +279,40 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = tmem_slot;
+    auto unit_col = [&](int b) { return b == nt ? sp.xrow : sp.xcol + kTT * b; };
 
-    if (warp == 4) {
-        if (lane == 0 && nkb > 0) {
-            const int xrow = t.col0 + t.r0;  // first operand row (A column) of the tile's rows
-            const int xcol = t.col0 + t.c0;  // ... of the tile's columns
-            const unsigned idesc = make_idesc(kTT, kTT);
-            const bool sym = *a.negw == 0;   // no negative weight: R = L = split(sqrt(w) A)
-            const CUtensorMap* mrh = sym ? &mLh : &mRh;
-            const CUtensorMap* mrl = sym ? &mLl : &mRl;
-            bool ok = true;
+    if (warp == kTmaWarp) {
+        if (lane == 0 && nunits > 0) {
             int issued = 0;
-            auto issue_load = [&](int kb) {
-                const int s = kb % kStages;
-                const unsigned st = sbase + s * kStageBytes;
-                const int x = (kb0 + kb) * kKB;
-                mbar_expect_tx(full0 + 8 * s, kStageBytes);
-                tma_load_2d(st + 0 * kOpBytes, &mLh, x, xrow, full0 + 8 * s);
-                tma_load_2d(st + 1 * kOpBytes, &mLl, x, xrow, full0 + 8 * s);
-                tma_load_2d(st + 2 * kOpBytes, mrh, x, xcol, full0 + 8 * s);
-                tma_load_2d(st + 3 * kOpBytes, mrl, x, xcol, full0 + 8 * s);
-            };
-            for (; issued < kStages && issued < nkb; ++issued) issue_load(issued);
+            bool ok = true;
+            for (int u = 0; u < nunits; ++u) {
+                const int slot = u % S;
+                if (u >= S && !mbar_wait_or_abort(sempty0 + 8 * slot, ((u / S) - 1) & 1, &abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                const int kb = u / nb, b = u - kb * nb;
+                const int xp = unit_col(b);
+                const int y = cat.y + (kb0 + kb) * kKB - cat.x;  // A row of the k-block's first primary
+                mbar_expect_tx(sfull0 + 8 * slot, kStgBytes);
+                tma_load_2d(sbase + stg0 + slot * kStgBytes, &mA, xp & ~3, y, sfull0 + 8 * slot);
+                ++issued;
+            }
+            if (!ok && !abort_flag) {
+                abort_flag = 1;
+                atomicOr(a.status, kStatusTimeout);
+            }
+            if (abort_flag) {
+                // this CTA's copies still in flight (the latest one of every slot;
+                // earlier ones were consumed) land before it exits (bounded)
+                for (int u = issued > S ? issued - S : 0; u < issued; ++u)
+                    mbar_wait(sfull0 + 8 * (u % S), (u / S) & 1);
+            }
+        }
+    } else if (warp == kMmaWarp) {
+        if (lane == 0 && nkb > 0) {
+            const unsigned idesc = make_idesc(kTT, N);
+            bool ok = true;
             for (int kb = 0; kb < nkb && ok; ++kb) {
                 const int sub = kb / kSubKB, buf = sub & 1;
                 const bool first = (kb % kSubKB) == 0;
@@ -228,17 +321,20 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
                     ok = false;
                     break;
                 }
-                const int s = kb % kStages;
-                const bool landed = (kb == 0 && a.test_timeout) ? mbar_test(full0, 0)
-                                                                : mbar_wait(full0 + 8 * s, (kb / kStages) & 1);
-                if (!landed) {
+                const int o = kb % O;
+                // error-path test: the first wait gives up at once, as if its bound had expired
+                const bool formed = (kb == 0 && a.test_timeout)
+                                        ? false
+                                        : mbar_wait_or_abort(ofull0 + 8 * o, (kb / O) & 1, &abort_flag);
+                if (!formed) {
                     ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const unsigned st = sbase + s * kStageBytes;
-                const unsigned Lh = st, Ll = st + kOpBytes, Rh = st + 2 * kOpBytes, Rl = st + 3 * kOpBytes;
-                const unsigned d = tmem + (unsigned)(buf * kTT);
+                const unsigned st = sbase + o * stage_bytes;
+                const unsigned Rh = st, Rl = st + nt * kOpBytes;
+                const unsigned Lh = lshare ? Rh : st + 2 * nt * kOpBytes, Ll = lshare ? Rl : Lh + kOpBytes;
+                const unsigned d = tmem + (unsigned)(buf * N);
 #pragma unroll
                 for (int k = 0; k < kKB / 16; ++k) {
                     const unsigned off = k * 32;  // 16 bf16 along K inside the swizzled row
@@ -247,35 +343,112 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
                     mma_bf16(d, make_desc(Lh + off), make_desc(Rl + off), idesc, 1u);
                     mma_bf16(d, make_desc(Ll + off), make_desc(Rh + off), idesc, 1u);
                 }
-                mma_commit(empty0 + 8 * s);  // frees stage s when these MMAs have read it
+                mma_commit(oempty0 + 8 * o);  // frees the operand stage when these MMAs have read it
                 if (last) mma_commit(ready0 + 8 * buf);
-                if (kb >= 1 && issued < nkb) {
-                    // refill the stage freed by the previous k-block
-                    const int ps = issued % kStages;
-                    if (!mbar_wait(empty0 + 8 * ps, ((issued / kStages) - 1) & 1)) {
-                        ok = false;
-                        break;
-                    }
-                    issue_load(issued);
-                    ++issued;
-                }
             }
             if (!ok) {
-                abort_flag = 1;
-                __threadfence_block();
-                atomicOr(a.status, kStatusTimeout);
-                // drain this CTA's own copies still in flight (bounded), then
-                // release the drain warps
-                for (int kb = 0; kb < issued; ++kb)
-                    mbar_wait(full0 + 8 * (kb % kStages), (kb / kStages) & 1);
+                if (!abort_flag) {
+                    abort_flag = 1;
+                    atomicOr(a.status, kStatusTimeout);
+                }
+                // release the drain warps (the commits complete when every MMA
+                // already issued has finished)
                 mma_commit(ready0);
                 mma_commit(ready0 + 8);
             }
         }
+    } else if (warp > kTmaWarp) {
+        // converters: unit u (staged FP32 rows of one panel) -> bf16 hi / lo of
+        // the scaled rows, K-major in the swizzled layout of operand stage
+        // kb % O.  Thread ct takes panel row r = ct % 128 (A column xp + r) and
+        // primaries [16 q, 16 q + 16) of the k-block, q = ct / 128: a warp reads
+        // 32 consecutive words of one staged row (distinct banks), and its
+        // 16-byte stores (one chunk of 8 primaries per lane) cover every bank
+        // group four times.  No per-element test: a primary past its catalog
+        // has scale 0, columns past the m block only feed discarded rows of the
+        // tile, and the box reads zeros past the ends of A.
+        const int ct = threadIdx.x - (kTmaWarp + 1) * 32;
+        const int r = ct & (kTT - 1);
+        const int q = ct >> 7;
+        const unsigned swz = (unsigned)((r >> 3) * 1024 + (r & 7) * 128);
+        for (int u = 0; u < nunits; ++u) {
+            const int kb = u / nb, b = u - kb * nb;
+            const int o = kb % O, mb = kb & 1, slot = u % S;
+            if (b == 0 && ct < kKB) {  // the k-block's scales (both sides); 0 past the catalog
+                const int k = (kb0 + kb) * kKB + ct - cat.x;
+                const float w = (k >= 0 && k < cat.z) ? __ldg(a.wrow + cat.y + k) : 0.f;
+                meta_sl[mb][ct] = sym ? sqrtf(w) : ((k >= 0 && k < cat.z) ? 1.f : 0.f);
+                meta_sr[mb][ct] = sym ? sqrtf(w) : w;
+            }
+            bool ok = mbar_wait_or_abort(sfull0 + 8 * slot, (u / S) & 1, &abort_flag);
+            if (cvt_barrier_any(!ok || abort_flag != 0)) {
+                if (!ok && !abort_flag) {
+                    abort_flag = 1;
+                    atomicOr(a.status, kStatusTimeout);
+                }
+                break;
+            }
+            const int xp = unit_col(b);
+            const float* stg = reinterpret_cast<const float*>(sgen + stg0 + slot * kStgBytes) +
+                               (16 * q) * kStgCols + (xp & 3) + r;
+            float cur[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) cur[i] = stg[i * kStgCols];
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sempty0 + 8 * slot) : "memory");
+            const bool isL = b == nt;
+            const float4* sc4 = reinterpret_cast<const float4*>((isL ? meta_sl[mb] : meta_sr[mb]) + 16 * q);
+            unsigned h[8], l[8];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {  // 16-byte chunk c: 8 primaries
+                const float4 s0 = sc4[2 * c], s1 = sc4[2 * c + 1];
+                const float2 sc2[4] = {make_float2(s0.x, s0.y), make_float2(s0.z, s0.w), make_float2(s1.x, s1.y),
+                                       make_float2(s1.z, s1.w)};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int i0 = 8 * c + 2 * e;
+                    const float2 y = __fmul2_rn(make_float2(cur[i0], cur[i0 + 1]), sc2[e]);
+                    const __nv_bfloat162 hp = __floats2bfloat162_rn(y.x, y.y);
+                    const unsigned hu = *reinterpret_cast<const unsigned*>(&hp);
+                    const float2 hf = make_float2(__uint_as_float(hu << 16), __uint_as_float(hu & 0xffff0000u));
+                    const float2 dd = __fadd2_rn(y, make_float2(-hf.x, -hf.y));
+                    const __nv_bfloat162 lp = __floats2bfloat162_rn(dd.x, dd.y);
+                    h[4 * c + e] = hu;
+                    l[4 * c + e] = *reinterpret_cast<const unsigned*>(&lp);
+                }
+            }
+            // the operand stage must have been read by the MMAs of k-block kb - O
+            if (b == 0 && kb >= O) {
+                ok = mbar_wait_or_abort(oempty0 + 8 * o, ((kb / O) - 1) & 1, &abort_flag);
+                if (cvt_barrier_any(!ok || abort_flag != 0)) {
+                    if (!ok && !abort_flag) {
+                        abort_flag = 1;
+                        atomicOr(a.status, kStatusTimeout);
+                    }
+                    break;
+                }
+            }
+            const unsigned st = o * stage_bytes;
+            unsigned char* hib = sgen + st + (isL ? 2 * nt : b) * kOpBytes + swz;
+            unsigned char* lob = sgen + st + (isL ? 2 * nt + 1 : nt + b) * kOpBytes + swz;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const unsigned chunk = (unsigned)(((2 * q + c) ^ (r & 7)) << 4);
+                *reinterpret_cast<uint4*>(hib + chunk) = make_uint4(h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]);
+                *reinterpret_cast<uint4*>(lob + chunk) = make_uint4(l[4 * c], l[4 * c + 1], l[4 * c + 2], l[4 * c + 3]);
+            }
+            if (b == nb - 1) {
+                // the MMA reads shared memory through the async proxy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ofull0 + 8 * o) : "memory");
+            }
+        }
     } else {
-        // drain warps: TMEM lane (= output row) warp*32 + lane
+        // drain warps: TMEM lane (= output row) warp*32 + lane; column c of the
+        // accumulator is column c % 128 of the strip's tile c / 128
         const int row = warp * 32 + lane;
-        double* out = a.partials + (int64_t)blockIdx.y * a.part_stride + t.out_off;
+        double* outs = a.partials + (int64_t)it.vseg0 * a.part_stride;
         for (int sub = 0; sub < nsub; ++sub) {
             const int buf = sub & 1;
             const bool ok = mbar_wait(ready0 + 8 * buf, (sub >> 1) & 1);
@@ -285,15 +458,18 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
                 break;
             }
 #pragma unroll 1
-            for (int c0 = 0; c0 < kTT; c0 += 32) {
-                unsigned r[32];
-                tmem_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(buf * kTT + c0), r);
+            for (int c0 = 0; c0 < N; c0 += 32) {
+                unsigned rr[32];
+                tmem_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(buf * N + c0), rr);
+                const Tile t = a.tiles[sp.tile0 + c0 / kTT];
+                const int cc = c0 % kTT;
+                double* out = outs + t.out_off;
                 if (row < t.rows) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        if (c0 + j < t.cols) {
-                            double* o = out + (int64_t)(c0 + j) * kTT + row;  // column-major
-                            const double v = (double)__uint_as_float(r[j]);
+                        if (cc + j < t.cols) {
+                            double* o = out + (int64_t)(cc + j) * kTT + row;  // column-major
+                            const double v = (double)__uint_as_float(rr[j]);
                             *o = (sub == 0) ? v : *o + v;
                         }
                     }
@@ -303,90 +479,21 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(drained0 + 8 * buf) : "memory");
         }
-        if (nsub == 0 && row < t.rows)
-            for (int c = 0; c < t.cols; ++c) out[(int64_t)c * kTT + row] = 0.0;
+        // an empty range writes zeros; the second virtual segment of a one-tile
+        // strip's item is zeroed (its primaries are in the first slot's sum)
+        for (int p = 0; p < nt; ++p) {
+            const Tile t = a.tiles[sp.tile0 + p];
+            for (int v = (nsub == 0 ? 0 : 1); v < it.nvseg; ++v) {
+                double* out = a.partials + (int64_t)(it.vseg0 + v) * a.part_stride + t.out_off;
+                for (int c = 0; c < kTT; ++c) out[(int64_t)c * kTT + row] = 0.0;
+            }
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTT)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * N)
                      : "memory");
-}
-
-// A (rows x RLP, FP32) -> K-major bf16 operands [col][pr] for the split
-// product.  pr is the padded primary position: catalog c occupies
-// [cats[c].x, cats[c].x + cats[c].z) with its rows starting at cats[c].y,
-// and every catalog starts on a multiple of kKB; the gaps are written as 0.
-// One block per kSplitP = 64 padded primaries sweeps all columns in tiles of
-// 32 (rows read as 128-byte lines, each column written as one 128-byte line
-// of bf16 pairs per operand).
-// With no negative weight (*negw == 0) both sides of w_i a a^T are sqrt(w_i) a,
-// so only its hi / lo pair is written (Lh, Ll; the contraction reads them for
-// both sides); otherwise L = A and R = w A as four arrays.
-constexpr int kSplitP = 64;
-
-__global__ void __launch_bounds__(256) k_split(const float* __restrict__ A, int RLP, int RL,
-                                               const float* __restrict__ w, const int4* __restrict__ cats,
-                                               int ncat, int64_t P_pad, const int* __restrict__ negw,
-                                               __nv_bfloat16* Lh, __nv_bfloat16* Ll, __nv_bfloat16* Rh,
-                                               __nv_bfloat16* Rl) {
-    __shared__ float tl[kSplitP][33];
-    __shared__ float tw[kSplitP];
-    __shared__ int trow[kSplitP];
-    const bool sym = *negw == 0;
-    const int64_t p0 = (int64_t)blockIdx.x * kSplitP;  // padded primary positions
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-    if (threadIdx.x < kSplitP) {
-        const int64_t pr = p0 + threadIdx.x;
-        int lo = 0, hi = ncat - 1;  // last catalog starting at or before pr
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (cats[mid].x <= pr) lo = mid; else hi = mid - 1;
-        }
-        const int4 ct = cats[lo];
-        const int64_t k = pr - ct.x;
-        const int r = (pr < P_pad && k >= 0 && k < ct.z) ? (int)(ct.y + k) : -1;
-        trow[threadIdx.x] = r;
-        const float wr = r >= 0 ? w[r] : 0.f;
-        tw[threadIdx.x] = sym ? sqrtf(wr) : wr;
-    }
-    __syncthreads();
-    for (int c0 = 0; c0 < RL; c0 += 32) {
-        for (int k = ty; k < kSplitP; k += 8) {  // primary k, columns c0 .. c0 + 31
-            const int r = trow[k];
-            const int c = c0 + tx;
-            tl[k][tx] = (r >= 0 && c < RL) ? A[(int64_t)r * RLP + c] : 0.f;
-        }
-        __syncthreads();
-        for (int k = ty; k < 32; k += 8) {  // column c0 + k, primaries 2 tx and 2 tx + 1
-            const int c = c0 + k;
-            const int64_t pr = p0 + 2 * tx;
-            if (c < RL && pr < P_pad && sym) {
-                const float y0 = tl[2 * tx][k] * tw[2 * tx], y1 = tl[2 * tx + 1][k] * tw[2 * tx + 1];
-                const __nv_bfloat16 yh0 = __float2bfloat16_rn(y0), yh1 = __float2bfloat16_rn(y1);
-                const int64_t o = (int64_t)c * P_pad + pr;
-                *reinterpret_cast<__nv_bfloat162*>(Lh + o) = __halves2bfloat162(yh0, yh1);
-                *reinterpret_cast<__nv_bfloat162*>(Ll + o) =
-                    __halves2bfloat162(__float2bfloat16_rn(y0 - __bfloat162float(yh0)),
-                                       __float2bfloat16_rn(y1 - __bfloat162float(yh1)));
-            } else if (c < RL && pr < P_pad) {
-                const float x0 = tl[2 * tx][k], x1 = tl[2 * tx + 1][k];
-                const float y0 = x0 * tw[2 * tx], y1 = x1 * tw[2 * tx + 1];
-                const __nv_bfloat16 xh0 = __float2bfloat16_rn(x0), xh1 = __float2bfloat16_rn(x1);
-                const __nv_bfloat16 yh0 = __float2bfloat16_rn(y0), yh1 = __float2bfloat16_rn(y1);
-                const int64_t o = (int64_t)c * P_pad + pr;
-                *reinterpret_cast<__nv_bfloat162*>(Lh + o) = __halves2bfloat162(xh0, xh1);
-                *reinterpret_cast<__nv_bfloat162*>(Ll + o) =
-                    __halves2bfloat162(__float2bfloat16_rn(x0 - __bfloat162float(xh0)),
-                                       __float2bfloat16_rn(x1 - __bfloat162float(xh1)));
-                *reinterpret_cast<__nv_bfloat162*>(Rh + o) = __halves2bfloat162(yh0, yh1);
-                *reinterpret_cast<__nv_bfloat162*>(Rl + o) =
-                    __halves2bfloat162(__float2bfloat16_rn(y0 - __bfloat162float(yh0)),
-                                       __float2bfloat16_rn(y1 - __bfloat162float(yh1)));
-            }
-        }
-        __syncthreads();
-    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -402,15 +509,17 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-int make_map(CUtensorMap* m, void* base, int64_t P_pad, int RL) {
+// FP32 rows of A as a 2-D tensor: RL columns (inner) x rows, row pitch RLP
+// floats; boxes of kStgCols x kKB, no swizzle, zeros outside.
+int make_map_a(CUtensorMap* m, const float* A, int RLP, int RL, int64_t rows) {
     auto fn = encode_fn();
     if (!fn) return -1;
-    cuuint64_t dims[2] = {(cuuint64_t)P_pad, (cuuint64_t)RL};
-    cuuint64_t strides[1] = {(cuuint64_t)P_pad * 2};
-    cuuint32_t box[2] = {kKB, kTT};
+    cuuint64_t dims[2] = {(cuuint64_t)RL, (cuuint64_t)(rows > 0 ? rows : 1)};
+    cuuint64_t strides[1] = {(cuuint64_t)RLP * 4};
+    cuuint32_t box[2] = {kStgCols, kKB};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : -1;
 }
@@ -418,34 +527,40 @@ int make_map(CUtensorMap* m, void* base, int64_t P_pad, int RL) {
 }  // namespace
 
 int contract_tile_dim_tc() { return kTT; }
-int contract_tc_kblock() { return kKB; }
 
-int launch_split(const float* A, int RLP, int RL, const float* w, const int4* cats, int ncat,
-                 int64_t P_pad, const int* negw, void* ops, cudaStream_t st) {
-    if (P_pad <= 0) return 0;
-    __nv_bfloat16* base = static_cast<__nv_bfloat16*>(ops);
-    const int64_t n1 = (int64_t)RL * P_pad;
-    k_split<<<(unsigned)((P_pad + kSplitP - 1) / kSplitP), 256, 0, st>>>(A, RLP, RL, w, cats, ncat, P_pad, negw,
-                                                                         base, base + n1, base + 2 * n1, base + 3 * n1);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+// Strips of the tile list (tiles in (m, row tile, column tile) order, column
+// tiles from the diagonal): consecutive tiles of one row panel, two at a time.
+int make_strips(const Tile* tiles, int ntiles, TcStrip* out, int max_strips) {
+    int n = 0;
+    for (int k = 0; k < ntiles;) {
+        const bool pair = k + 1 < ntiles && tiles[k + 1].m == tiles[k].m && tiles[k + 1].r0 == tiles[k].r0 &&
+                          tiles[k + 1].c0 == tiles[k].c0 + kTT;
+        if (n >= max_strips) return -1;
+        out[n].tile0 = k;
+        out[n].ntile = pair ? 2 : 1;
+        out[n].xrow = tiles[k].col0 + tiles[k].r0;
+        out[n].xcol = tiles[k].col0 + tiles[k].c0;
+        ++n;
+        k += pair ? 2 : 1;
+    }
+    return n;
 }
 
-int launch_contract_tc(const void* ops, int64_t P_pad, int RL, const Tile* tiles, int ntiles,
-                       const Segment* segs, int nsegs, double* partials, int part_stride,
-                       const int* negw, int* status, cudaStream_t st, int test_timeout) {
-    if (ntiles <= 0 || nsegs <= 0) return 0;
-    const __nv_bfloat16* base = static_cast<const __nv_bfloat16*>(ops);
-    const int64_t n1 = (int64_t)RL * P_pad;
-    CUtensorMap m[4];
-    for (int k = 0; k < 4; ++k)
-        if (make_map(&m[k], const_cast<__nv_bfloat16*>(base + k * n1), P_pad, RL) != 0) return -2;
-    const int smem = kStages * kStageBytes + 1024;
+int contract_tc_kblock() { return kKB; }
+
+int launch_contract_tc(const float* A, int RLP, int RL, int64_t arows, const float* wrow, const int4* cats,
+                       const Tile* tiles, const TcStrip* strips, const TcItem* items, int nitems,
+                       const Segment* segs, double* partials, int part_stride, const int* negw, int* status,
+                       cudaStream_t st, int test_timeout) {
+    if (nitems <= 0) return 0;
+    CUtensorMap m;
+    if (make_map_a(&m, A, RLP, RL, arows) != 0) return -2;
+    const int smem = kBufBytes + 1024;
     if (cudaFuncSetAttribute(k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
         cudaSuccess)
         return -1;
-    TcArgs a{tiles, segs, partials, part_stride, negw, status, test_timeout};
-    dim3 grid(ntiles, nsegs);
-    k_contract_tc<<<grid, kTcWarps * 32, smem, st>>>(m[0], m[1], m[2], m[3], a);
+    TcArgs a{A, RLP, wrow, cats, tiles, strips, items, segs, partials, part_stride, negw, status, test_timeout};
+    k_contract_tc<<<(unsigned)nitems, kTcWarps * 32, smem, st>>>(m, a);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -285,13 +285,22 @@ int launch_combine(const double* zeta, int64_t zsize, int ncat, const double* co
 int contract_tile_dim_tc();
 int contract_tc_kblock();
 // negw: the status block's negative-weight flag (kNegWeightSlot), read on the
-// device: 0 -> both operand sides are hi/lo of sqrt(w) A (two arrays written);
-// else the left side is hi/lo of A and the right side hi/lo of w A (four).
-int launch_split(const float* A, int RLP, int RL, const float* w, const int4* cats, int ncat,
-                 int64_t P_pad, const int* negw, void* ops, cudaStream_t st);
-int launch_contract_tc(const void* ops, int64_t P_pad, int RL, const Tile* tiles, int ntiles,
-                       const Segment* segs, int nsegs, double* partials, int part_stride,
-                       const int* negw, int* status, cudaStream_t st, int test_timeout = 0);
+// device: 0 -> both operand sides are hi/lo of sqrt(w) A; else the left side is
+// hi/lo of A and the right side hi/lo of w A.  The operands are formed inside
+// the kernel from the FP32 rows A (row pitch RLP) and the row weights wrow;
+// cats: per catalog {padded start, first A row, length, 0}.
+// A strip: ntile (1 or 2) output tiles side by side in one row panel, tiles
+// tile0.. of the tile list; xrow / xcol = A column of its first row / column.
+struct TcStrip { int tile0; int ntile; int xrow; int xcol; };
+// A work item of the tensor-core contraction: a strip and nvseg (1 or 2)
+// consecutive virtual segments from vseg0 (partials go to slot vseg0).
+struct TcItem { int strip; int vseg0; int nvseg; int pad; };
+int make_strips(const Tile* tiles, int ntiles, TcStrip* out, int max_strips);
+// arows: rows of A in the buffer (the tensor map's extent; rows beyond read as 0)
+int launch_contract_tc(const float* A, int RLP, int RL, int64_t arows, const float* wrow, const int4* cats,
+                       const Tile* tiles, const TcStrip* strips, const TcItem* items, int nitems,
+                       const Segment* segs, double* partials, int part_stride, const int* negw, int* status,
+                       cudaStream_t st, int test_timeout = 0);
 
 // ---- adjoint.cu ----------------------------------------------------------------
 size_t adjoint_m_floats(int nbins, int lmax);

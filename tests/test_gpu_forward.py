@@ -206,7 +206,12 @@ def test_chunked_passes_match_single_pass(tc):
     plan.set_option(g3.OPT_CHUNK_ROWS, 6400)
     z2, c2 = plan.compute(pos, w, fp32_contraction=not tc)
     assert torch.equal(c1, c2)
-    assert maxrel(z2.cpu().numpy(), z1.cpu().numpy()) < 1e-6
+    # the FP32 form adds the same FP32 partial sums in both cases (1e-6); the
+    # tensor-core form's FP32 accumulation runs in tensor memory follow the
+    # segments, which differ between the two, so its sums round differently at
+    # the 1e-6 level (both stay within 1e-4 of the FP64 oracle; a chunking
+    # mistake would show at order one)
+    assert maxrel(z2.cpu().numpy(), z1.cpu().numpy()) < (1e-5 if tc else 1e-6)
     with pytest.raises(g3.G3PCFError) as ei:
         plan.alm([0])
     assert ei.value.name == "ERR_STATE"
