@@ -315,20 +315,22 @@ def measure_forward(cat, steps: int, warmup: int) -> dict:
     return res
 
 
-def measure_adjoint(dev, stream) -> dict:
+def measure_adjoint(dev, stream, n: int = 0, list_bytes: int = 0) -> dict:
     """The differentiation workload (clustered N = 500,000, L = 800, Rmax = 120, 8 bins,
     lmax = 6): forward with multipoles kept, then g3pcf_backward, in the default
     double-float gradient arithmetic and in the FP32 form."""
     import torch
     import paper_1709_00086_gb300 as g3
     from paper_1709_00086_gb300 import catalogs as cats
-    dcat = cats.differentiation()
+    dcat = cats.differentiation(n=n) if n > 0 else cats.differentiation()
     dpos = torch.from_numpy(dcat.pos).to(dev)
     dwt = torch.from_numpy(dcat.w).to(dev)
-    out = {"workload": "clustered N=500,000, periodic L=800, Rmax=120, 8 bins, lmax=6"}
+    out = {"workload": "clustered N=%d, periodic L=800, Rmax=120, 8 bins, lmax=6" % dcat.n}
     for prec, key in ((0, "double_float"), (1, "fp32")):
         dplan = g3.Plan(**dcat.params())
         dplan.set_option(g3.OPT_GRAD_PRECISION, prec)
+        if list_bytes > 0:
+            dplan.set_option(g3.OPT_LIST_BYTES, list_bytes)
         rng = np.random.default_rng(5)
         dz = torch.from_numpy(rng.normal(size=(dplan.zsize, 2))).to(dev)
         fwd_ms, bwd_ms = [], []
@@ -395,6 +397,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     cat = make_catalog(args)
     plan = g3.Plan(**cat.params())
+    if args.list_bytes > 0:  # cap the pair-list pool (small-footprint profiling runs)
+        plan.set_option(g3.OPT_LIST_BYTES, args.list_bytes)
     pos = torch.from_numpy(cat.pos).to(dev)
     w = torch.from_numpy(cat.w).to(dev)
     stream = torch.cuda.current_stream()
@@ -484,7 +488,7 @@ def run_ours(args):
     other = {}
     if ws == 1:
         if not args.no_adjoint:
-            adj = measure_adjoint(dev, stream)
+            adj = measure_adjoint(dev, stream, args.adjoint_n, args.list_bytes)
         if not args.no_other:
             from paper_1709_00086_gb300 import catalogs as cats
             other["plain_uniform_20k"] = measure_forward(cats.plain_uniform(), max(3, args.steps), args.warmup)
@@ -570,6 +574,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing")
     ap.add_argument("--no-other", action="store_true", help="skip the 20k and batched workloads")
+    ap.add_argument("--list-bytes", type=int, default=0, help="pair-list pool of the main plan in bytes (0: automatic)")
+    ap.add_argument("--adjoint-n", type=int, default=0, help="override N of the differentiation workload (profiling cases)")
     ap.add_argument("--large", action="store_true", help="also time one forward of the 50M radial workload")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -4,8 +4,9 @@
 //
 // With G_m = dL/dzeta_m / 2 (the caller passes dL/d(Re zeta, Im zeta)),
 // M_m = G_m + G_m^H and A_i the primary's multipoles,
-//      V_i = M_m A_i                    (k_vgemm, per m block, FP32, or FP64
-//                                        for the double-float pair pass)
+//      V_i = M_m A_i                    (k_vgemm, per m block, FP32; k_vgemm_df
+//                                        in double-float for the double-float
+//                                        pair pass)
 //      dL/dw_i (as a primary) = Re(A_i^H V_i)   (fused into k_vgemm)
 //      H_i = w_i V_i                    (applied by the adjoint pair pass)
 // (per catalog c of a batched forward, M is built from that catalog's dL/dzeta_c)
@@ -33,6 +34,17 @@ struct MInfo {
     long long zoff[kMaxL + 1];  // complex offset of block m in zeta
 };
 
+// M entries as stored: FP32, or head + tail FP32 pairs for the double-float path
+template <class TM>
+__device__ __forceinline__ TM m_entry(double v);
+template <>
+__device__ __forceinline__ float m_entry<float>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ float2 m_entry<float2>(double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+
 template <class TM>
 __global__ void k_build_mreal(const double* dz, MInfo mi, int lmax, int64_t zsize, size_t mfloats,
                               TM* Mr) {
@@ -54,7 +66,7 @@ __global__ void k_build_mreal(const double* dz, MInfo mi, int lmax, int64_t zsiz
             const bool rlo = rr < K, clo = cc < K;
             v = (rlo == clo) ? re : (rlo ? -im : im);
         }
-        out[e] = (TM)v;
+        out[e] = m_entry<TM>(v);
     }
 }
 
@@ -63,8 +75,7 @@ __global__ void k_build_mreal(const double* dz, MInfo mi, int lmax, int64_t zsiz
 // b covers rows row_lo + kRows b .. of catalog 0 below row_hi.  The row's
 // primary-weight term is added to dw[row], or, for rows of a chunk of
 // primaries (rorig non-null), to dw[rorig[rplist ? rplist[q0 + row] : q0 + row]].
-// TM = float: FP32 M, V and sums; TM = double: FP64 M, V and sums (the A rows
-// stay FP32, exact in FP64).
+// FP32 M, V and sums.
 template <class TM>
 __global__ void __launch_bounds__(kVThreads) k_vgemm(const float* __restrict__ A, int RLP, int RL,
                                                      const int4* __restrict__ blks, int64_t row_lo,
@@ -134,6 +145,103 @@ __global__ void __launch_bounds__(kVThreads) k_vgemm(const float* __restrict__ A
     }
 }
 
+// The same product in double-float: M as head + tail pairs, the FP32 A entries
+// exact, each product M_h a formed exactly (a multiply and an FMA), the running
+// sum's head updated by an error-free two-sum and every rounding error, the
+// product's low part and M_l a gathered in the tail; V stored renormalised as
+// head + tail.  ~10 FP32 operations per multiply-add instead of one FP64 FMA,
+// which runs at 1/58 of the FP32 rate on this part.  The primary-weight term
+// Re(A^H V) sums in FP64 (one term per column).
+__global__ void __launch_bounds__(kVThreads) k_vgemm_df(const float* __restrict__ A, int RLP, int RL,
+                                                        const int4* __restrict__ blks, int64_t row_lo,
+                                                        int64_t row_hi, const float2* __restrict__ Mall,
+                                                        size_t mfloats, MInfo mi, int lmax, float2* V,
+                                                        double* dw, const int* rplist, const int* rorig,
+                                                        int64_t q0) {
+    extern __shared__ float sA[];  // kRows x RL
+    __shared__ double red[kRows][kVThreads / 32];
+    int4 blk;
+    if (blks) {
+        blk = blks[blockIdx.x];
+    } else {
+        const int64_t b0 = row_lo + (int64_t)blockIdx.x * kRows;
+        blk = make_int4(0, (int)b0, (int)(row_hi - b0 < kRows ? row_hi - b0 : kRows), 0);
+    }
+    const float2* __restrict__ Mr = Mall + (size_t)blk.x * mfloats;
+    const int64_t r0 = blk.y;
+    const int64_t rows = r0 + blk.z;
+    for (int k = threadIdx.x; k < kRows * RL; k += kVThreads) {
+        const int rr = k / RL, c = k % RL;
+        sA[k] = (r0 + rr < rows) ? A[(r0 + rr) * RLP + c] : 0.f;
+    }
+    __syncthreads();
+    double dwp[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) dwp[r] = 0.0;
+    for (int col = threadIdx.x; col < RL; col += kVThreads) {
+        int m = 0;
+        while (m < lmax && col >= mi.col0[m + 1]) ++m;
+        const int W = mi.W[m], c = col - mi.col0[m];
+        const float2* Mrow = Mr + mi.moff[m] + (int64_t)c * W;
+        const float* As = sA + mi.col0[m];
+        float sh[kRows], sl[kRows];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) sh[r] = sl[r] = 0.f;
+        for (int k = 0; k < W; ++k) {
+            const float2 mv = __ldg(Mrow + k);
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+                const float x = As[r * RL + k];
+                const float p = __fmul_rn(mv.x, x);
+                const float pe = __fmaf_rn(mv.x, x, -p);
+                const float s = __fadd_rn(sh[r], p);
+                const float bb = __fsub_rn(s, sh[r]);
+                const float err = __fadd_rn(__fsub_rn(sh[r], __fsub_rn(s, bb)), __fsub_rn(p, bb));
+                sh[r] = s;
+                sl[r] = __fmaf_rn(mv.y, x, __fadd_rn(sl[r], __fadd_rn(err, pe)));
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const float h = __fadd_rn(sh[r], sl[r]);
+            const float l = __fsub_rn(sl[r], __fsub_rn(h, sh[r]));
+            if (r0 + r < rows) V[(r0 + r) * RLP + col] = make_float2(h, l);
+            dwp[r] = fma((double)sA[r * RL + col], (double)h + (double)l, dwp[r]);
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        double v = dwp[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[r][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kRows && r0 + threadIdx.x < rows) {
+        double s = 0.0;
+        for (int k = 0; k < kVThreads / 32; ++k) s += red[threadIdx.x][k];
+        const int64_t row = r0 + threadIdx.x;
+        int64_t idx = row;
+        if (rorig) {
+            const int64_t q = q0 + row;
+            idx = rorig[rplist ? rplist[q] : q];
+        }
+        dw[idx] += s;
+    }
+}
+
+template <class TM>
+struct VgemmKernel;
+template <>
+struct VgemmKernel<float> {
+    static constexpr auto fn = k_vgemm<float>;
+};
+template <>
+struct VgemmKernel<float2> {
+    static constexpr auto fn = k_vgemm_df;
+};
+
 MInfo make_info(int nbins, int lmax) {
     MInfo mi{};
     int col = 0, moff = 0;
@@ -182,12 +290,12 @@ int adjoint_prep_t(const double* dzeta, int nbins, int lmax, int ncat, int64_t z
     if (nblks > 0) {
         const MInfo mi = make_info(nbins, lmax);
         const size_t smem = sizeof(float) * kRows * RL;
-        if (cudaFuncSetAttribute(k_vgemm<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        if (cudaFuncSetAttribute(VgemmKernel<TM>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return -1;
-        k_vgemm<TM><<<(unsigned)nblks, kVThreads, smem, st>>>(A, RLP, RL, blks, 0, 0, Mr,
-                                                             adjoint_m_floats(nbins, lmax), mi, lmax, V, dw,
-                                                             nullptr, nullptr, 0);
+        VgemmKernel<TM>::fn<<<(unsigned)nblks, kVThreads, smem, st>>>(A, RLP, RL, blks, 0, 0, Mr,
+                                                                      adjoint_m_floats(nbins, lmax), mi, lmax, V,
+                                                                      dw, nullptr, nullptr, 0);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -198,12 +306,13 @@ int vgemm_rows_t(const float* A, int RLP, int RL, int64_t row_lo, int64_t row_hi
     if (row_hi <= row_lo) return 0;
     const MInfo mi = make_info(nbins, lmax);
     const size_t smem = sizeof(float) * kRows * RL;
-    if (cudaFuncSetAttribute(k_vgemm<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(VgemmKernel<TM>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
         return -1;
     const int64_t nb = (row_hi - row_lo + kRows - 1) / kRows;
-    k_vgemm<TM><<<(unsigned)nb, kVThreads, smem, st>>>(A, RLP, RL, nullptr, row_lo, row_hi, Mr,
-                                                       adjoint_m_floats(nbins, lmax), mi, lmax, V, dw, plist,
-                                                       orig, q0);
+    VgemmKernel<TM>::fn<<<(unsigned)nb, kVThreads, smem, st>>>(A, RLP, RL, nullptr, row_lo, row_hi, Mr,
+                                                                adjoint_m_floats(nbins, lmax), mi, lmax, V, dw,
+                                                                plist, orig, q0);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -214,10 +323,10 @@ int launch_adjoint_prep(const double* dzeta, int nbins, int lmax, int ncat, int6
     return adjoint_prep_t<float>(dzeta, nbins, lmax, ncat, zsize, A, RLP, RL, blks, nblks, Mr, V, dw, st);
 }
 
-int launch_adjoint_prep64(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, const float* A,
-                          int RLP, int RL, const int4* blks, int nblks, double* Mr, double* V, double* dw,
-                          cudaStream_t st) {
-    return adjoint_prep_t<double>(dzeta, nbins, lmax, ncat, zsize, A, RLP, RL, blks, nblks, Mr, V, dw, st);
+int launch_adjoint_prep_df(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, const float* A,
+                           int RLP, int RL, const int4* blks, int nblks, float2* Mr, float2* V, double* dw,
+                           cudaStream_t st) {
+    return adjoint_prep_t<float2>(dzeta, nbins, lmax, ncat, zsize, A, RLP, RL, blks, nblks, Mr, V, dw, st);
 }
 
 int launch_adjoint_m(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, float* Mr,
@@ -225,9 +334,9 @@ int launch_adjoint_m(const double* dzeta, int nbins, int lmax, int ncat, int64_t
     return adjoint_m_t<float>(dzeta, nbins, lmax, ncat, zsize, Mr, st);
 }
 
-int launch_adjoint_m64(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, double* Mr,
-                       cudaStream_t st) {
-    return adjoint_m_t<double>(dzeta, nbins, lmax, ncat, zsize, Mr, st);
+int launch_adjoint_m_df(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, float2* Mr,
+                        cudaStream_t st) {
+    return adjoint_m_t<float2>(dzeta, nbins, lmax, ncat, zsize, Mr, st);
 }
 
 int launch_vgemm_rows(const float* A, int RLP, int RL, int64_t row_lo, int64_t row_hi, const float* Mr,
@@ -236,10 +345,10 @@ int launch_vgemm_rows(const float* A, int RLP, int RL, int64_t row_lo, int64_t r
     return vgemm_rows_t<float>(A, RLP, RL, row_lo, row_hi, Mr, nbins, lmax, V, dw, plist, orig, q0, st);
 }
 
-int launch_vgemm_rows64(const float* A, int RLP, int RL, int64_t row_lo, int64_t row_hi, const double* Mr,
-                        int nbins, int lmax, double* V, double* dw, const int* plist, const int* orig,
-                        int64_t q0, cudaStream_t st) {
-    return vgemm_rows_t<double>(A, RLP, RL, row_lo, row_hi, Mr, nbins, lmax, V, dw, plist, orig, q0, st);
+int launch_vgemm_rows_df(const float* A, int RLP, int RL, int64_t row_lo, int64_t row_hi, const float2* Mr,
+                         int nbins, int lmax, float2* V, double* dw, const int* plist, const int* orig,
+                         int64_t q0, cudaStream_t st) {
+    return vgemm_rows_t<float2>(A, RLP, RL, row_lo, row_hi, Mr, nbins, lmax, V, dw, plist, orig, q0, st);
 }
 
 }  // namespace g3

@@ -84,9 +84,11 @@ struct g3pcf_plan_s {
     std::vector<int4> colconv;     // Chebyshev-form columns (pair-list path)
     std::vector<float> colcoef;
     std::vector<double> colcoef64;  // the same coefficients in FP64 (double-float path)
+    std::vector<float2> colcoefdf;  // ... as head + tail FP32 pairs (uploaded)
     std::vector<int4> slotconv;    // the transposed connection (pair-list adjoint)
     std::vector<float> slotcoef;
     std::vector<double> slotcoef64;
+    std::vector<float2> slotcoefdf;
     std::vector<int> monoexp, monoidx;  // monomial-basis tables (k_mono)
     std::vector<int4> monoconv;
     std::vector<double> monocoef;
@@ -105,7 +107,7 @@ struct g3pcf_plan_s {
     DevBuf counts, A, partials, d_tiles, d_segs, d_segfirst, d_colmap, d_colscale, d_catoff;
     DevBuf d_colconv, d_colcoef, d_bintab_s, d_slotconv, d_slotcoef, d_monoexp, d_monoconv, d_monoidx, d_monocoef;
     DevBuf d_ranges, d_tiles_tc, d_cats, d_mreal, d_V, d_bintab, wrow, d_vblk, d_strips_tc, d_items;
-    DevBuf d_colcoef64, d_slotcoef64, d_mreal64, d_V64;
+    DevBuf d_slotcoefdf, d_mrealdf, d_Vdf, d_colcoefdf;
     int64_t opt_chunk = 0;   // G3PCF_OPT_CHUNK_ROWS
     // pinned staging for host -> device tables (capturable copies); offset
     // restarts at every forward
@@ -167,6 +169,17 @@ struct g3pcf_plan_s {
 };
 
 namespace {
+
+// FP64 values as head + tail FP32 pairs (head = the nearest float, tail = the
+// nearest float to the remainder): ~48 significant bits.
+std::vector<float2> to_df(const std::vector<double>& v) {
+    std::vector<float2> out(v.size());
+    for (size_t k = 0; k < v.size(); ++k) {
+        const float h = (float)v[k];
+        out[k] = float2{h, (float)(v[k] - (double)h)};
+    }
+    return out;
+}
 
 // Copy a host table to the device through the plan's pinned staging buffer
 // so that the copy can be captured into a CUDA graph (replays read the same
@@ -243,11 +256,14 @@ int upload_consts(g3pcf_plan_t P) {
         return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (constants)");
     CK(cudaMemcpy(P->d_slotconv.p, P->slotconv.data(), P->slotconv.size() * sizeof(int4), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->d_slotcoef.p, P->slotcoef.data(), P->slotcoef.size() * sizeof(float), cudaMemcpyHostToDevice));
-    if (P->d_colcoef64.ensure(P->colcoef64.size() * sizeof(double)) ||
-        P->d_slotcoef64.ensure(P->slotcoef64.size() * sizeof(double)))
+    // the double-float path's coefficients as head + tail FP32 pairs
+    P->colcoefdf = to_df(P->colcoef64);
+    P->slotcoefdf = to_df(P->slotcoef64);
+    if (P->d_colcoefdf.ensure(P->colcoefdf.size() * sizeof(float2)) ||
+        P->d_slotcoefdf.ensure(P->slotcoefdf.size() * sizeof(float2)))
         return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (constants)");
-    CK(cudaMemcpy(P->d_colcoef64.p, P->colcoef64.data(), P->colcoef64.size() * sizeof(double), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(P->d_slotcoef64.p, P->slotcoef64.data(), P->slotcoef64.size() * sizeof(double),
+    CK(cudaMemcpy(P->d_colcoefdf.p, P->colcoefdf.data(), P->colcoefdf.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->d_slotcoefdf.p, P->slotcoefdf.data(), P->slotcoefdf.size() * sizeof(float2),
                   cudaMemcpyHostToDevice));
     if (P->d_monoexp.ensure(P->monoexp.size() * sizeof(int)) || P->d_monoconv.ensure(P->monoconv.size() * sizeof(int4)) ||
         P->d_monoidx.ensure(P->monoidx.size() * sizeof(int)) || P->d_monocoef.ensure(P->monocoef.size() * sizeof(double)))
@@ -631,8 +647,8 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode
     // unless the FP32 form is asked for, the double-float kernels (precise.cu)
     la.exact_img = (mode >= 1 || P->exact_alm) ? 1 : 0;
     la.precise = (la.exact_img && P->opt_grad == 0) ? 1 : 0;
-    la.colcoef64 = P->d_colcoef64.as<double>();
-    la.slotcoef64 = P->d_slotcoef64.as<double>();
+    la.colcoefdf = P->d_colcoefdf.as<float2>();
+    la.slotcoefdf = P->d_slotcoefdf.as<float2>();
     la.monoexp = P->d_monoexp.as<int>();
     la.monoconv = P->d_monoconv.as<int4>();
     la.monoidx = P->d_monoidx.as<int>();
@@ -643,7 +659,7 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode
         la.dpos = pa.dpos;
         la.slotconv = P->d_slotconv.as<int4>();
         la.slotcoef = P->d_slotcoef.as<float>();
-        la.V64 = P->d_V64.as<double>();
+        la.Vdf = P->d_Vdf.as<float2>();
     }
     la.need = P->l_need.as<int>();
     la.base = P->l_base.as<int>();
@@ -779,9 +795,9 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode
             P->launches += 2;
             int vr = launch_accum(P->lmax, la, P->nsm, st);
             if (vr == 0)
-                vr = la.precise ? launch_vgemm_rows64(la.A, la.RLP, la.RL, la.qa - la.q0, la.qb - la.q0,
-                                                      P->d_mreal64.as<double>(), P->nbins, P->lmax,
-                                                      P->d_V64.as<double>(), pa.dw, la.plist, la.orig, la.q0, st)
+                vr = la.precise ? launch_vgemm_rows_df(la.A, la.RLP, la.RL, la.qa - la.q0, la.qb - la.q0,
+                                                      P->d_mrealdf.as<float2>(), P->nbins, P->lmax,
+                                                      P->d_Vdf.as<float2>(), pa.dw, la.plist, la.orig, la.q0, st)
                                 : launch_vgemm_rows(la.A, la.RLP, la.RL, la.qa - la.q0, la.qb - la.q0,
                                                     P->d_mreal.as<float>(), P->nbins, P->lmax, P->d_V.as<float>(),
                                                     pa.dw, la.plist, la.orig, la.q0, st);
@@ -1421,8 +1437,8 @@ int g3pcf_backward(g3pcf_plan_t P, const double* dzeta, double* dpos, double* dw
         // forward) and run each chunk's adjoint on the lists that recomputed them
         const int64_t C = P->fixed_chunk;
         const bool precise = P->opt_grad == 0;
-        if (precise ? (ensure(P, P->d_mreal64, sizeof(double) * adjoint_m_floats(P->nbins, P->lmax), "adjoint M") ||
-                       ensure(P, P->d_V64, sizeof(double) * (size_t)P->RLP * C, "adjoint V"))
+        if (precise ? (ensure(P, P->d_mrealdf, sizeof(float2) * adjoint_m_floats(P->nbins, P->lmax), "adjoint M") ||
+                       ensure(P, P->d_Vdf, sizeof(float2) * (size_t)P->RLP * C, "adjoint V"))
                     : (ensure(P, P->d_mreal, sizeof(float) * adjoint_m_floats(P->nbins, P->lmax), "adjoint M") ||
                        ensure(P, P->d_V, sizeof(float) * (size_t)P->RLP * C, "adjoint V")))
             return G3PCF_ERR_ALLOC;
@@ -1430,8 +1446,8 @@ int g3pcf_backward(g3pcf_plan_t P, const double* dzeta, double* dpos, double* dw
         int* d_queue = d_status + 16;
         CK(cudaMemsetAsync(P->small.p, 0, 256, st));
         CK(cudaMemsetAsync(P->counts.p, 0, sizeof(unsigned long long) * P->nbins, st));
-        if ((precise ? launch_adjoint_m64(dzeta, P->nbins, P->lmax, 1, zsize_of(P->nbins, P->lmax),
-                                          P->d_mreal64.as<double>(), st)
+        if ((precise ? launch_adjoint_m_df(dzeta, P->nbins, P->lmax, 1, zsize_of(P->nbins, P->lmax),
+                                           P->d_mrealdf.as<float2>(), st)
                      : launch_adjoint_m(dzeta, P->nbins, P->lmax, 1, zsize_of(P->nbins, P->lmax),
                                         P->d_mreal.as<float>(), st)) != 0)
             return fail(G3PCF_ERR_CUDA, "adjoint preparation launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -1481,8 +1497,8 @@ int g3pcf_backward(g3pcf_plan_t P, const double* dzeta, double* dpos, double* dw
     }
     // the double-float pair pass (list path, G3PCF_OPT_GRAD_PRECISION 0) takes M and V in FP64
     const bool precise = P->opt_grad == 0 && P->opt_pair != 1;
-    if ((precise ? (ensure(P, P->d_mreal64, sizeof(double) * adjoint_m_floats(P->nbins, P->lmax) * ncat, "adjoint M") ||
-                    ensure(P, P->d_V64, sizeof(double) * (size_t)P->RLP * rows, "adjoint V"))
+    if ((precise ? (ensure(P, P->d_mrealdf, sizeof(float2) * adjoint_m_floats(P->nbins, P->lmax) * ncat, "adjoint M") ||
+                    ensure(P, P->d_Vdf, sizeof(float2) * (size_t)P->RLP * rows, "adjoint V"))
                  : (ensure(P, P->d_mreal, sizeof(float) * adjoint_m_floats(P->nbins, P->lmax) * ncat, "adjoint M") ||
                     ensure(P, P->d_V, sizeof(float) * (size_t)P->RLP * rows, "adjoint V"))) ||
         ensure(P, P->d_vblk, sizeof(int4) * (blks.size() + 1), "adjoint blocks"))
@@ -1492,9 +1508,9 @@ int g3pcf_backward(g3pcf_plan_t P, const double* dzeta, double* dpos, double* dw
     int* d_queue = d_status + 16;
     CK(cudaMemsetAsync(P->small.p, 0, 256, st));
     CK(cudaMemsetAsync(P->counts.p, 0, sizeof(unsigned long long) * P->nbins * ncat, st));
-    if ((precise ? launch_adjoint_prep64(dzeta, P->nbins, P->lmax, ncat, zsize_of(P->nbins, P->lmax),
+    if ((precise ? launch_adjoint_prep_df(dzeta, P->nbins, P->lmax, ncat, zsize_of(P->nbins, P->lmax),
                                          P->A.as<float>(), P->RLP, P->RL, P->d_vblk.as<int4>(), (int)blks.size(),
-                                         P->d_mreal64.as<double>(), P->d_V64.as<double>(), dw, st)
+                                         P->d_mrealdf.as<float2>(), P->d_Vdf.as<float2>(), dw, st)
                  : launch_adjoint_prep(dzeta, P->nbins, P->lmax, ncat, zsize_of(P->nbins, P->lmax),
                                        P->A.as<float>(), P->RLP, P->RL, P->d_vblk.as<int4>(), (int)blks.size(),
                                        P->d_mreal.as<float>(), P->d_V.as<float>(), dw, st)) != 0)
@@ -1855,7 +1871,7 @@ int g3pcf_destroy(g3pcf_plan_t P) {
                       &P->d_segfirst, &P->d_colmap, &P->d_colscale, &P->d_colconv, &P->d_colcoef, &P->d_bintab_s, &P->d_slotconv, &P->d_slotcoef, &P->d_monoexp, &P->d_monoconv, &P->d_monoidx, &P->d_monocoef, &P->d_catoff, &P->d_ranges,
                       &P->d_tiles_tc, &P->d_cats, &P->d_mreal, &P->d_V, &P->d_bintab, &P->d_vblk,
                       &P->d_strips_tc, &P->d_items,
-                      &P->d_colcoef64, &P->d_slotcoef64, &P->d_mreal64, &P->d_V64,
+                      &P->d_slotcoefdf, &P->d_mrealdf, &P->d_Vdf, &P->d_colcoefdf,
                       &P->wrow, &P->l_need, &P->l_base, &P->l_nch, &P->l_pool, &P->l_tag, &P->l_ord,
                       &P->l_gbase, &P->l_scantmp, &P->l_passq};
     for (DevBuf* b : bufs) b->release();

@@ -192,9 +192,9 @@ struct ListArgs {
     // double-float path (multipoles meant for differentiation): FP64 connection
     // tables (same layout as colcoef / slotcoef) and the FP64 V rows
     int precise;
-    const double* colcoef64;
-    const double* slotcoef64;
-    const double* V64;
+    const float2* colcoefdf;     // colcoef as head + tail FP32 pairs (double-float path)
+    const float2* slotcoefdf;    // slotcoef likewise
+    const float2* Vdf;           // V rows as head + tail pairs (double-float adjoint)
     int* chunks;             // pool: 32 ints per chunk
     int* tag;                // pool: (rank among its bin's chunks) << 5 | bin, per chunk
     int* ord;                // pool: the primary's chunks listed by bin (stable), chunk | bin << 26
@@ -318,15 +318,16 @@ int launch_adjoint_m(const double* dzeta, int nbins, int lmax, int ncat, int64_t
 int launch_vgemm_rows(const float* A, int RLP, int RL, int64_t row_lo, int64_t row_hi, const float* Mr,
                       int nbins, int lmax, float* V, double* dw, const int* plist, const int* orig,
                       int64_t q0, cudaStream_t st);
-// FP64 forms of the three (M and V in FP64; for the double-float adjoint pass)
-int launch_adjoint_prep64(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, const float* A,
-                          int RLP, int RL, const int4* blks, int nblks, double* Mr, double* V, double* dw,
-                          cudaStream_t st);
-int launch_adjoint_m64(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, double* Mr,
-                       cudaStream_t st);
-int launch_vgemm_rows64(const float* A, int RLP, int RL, int64_t row_lo, int64_t row_hi, const double* Mr,
-                        int nbins, int lmax, double* V, double* dw, const int* plist, const int* orig,
-                        int64_t q0, cudaStream_t st);
+// Double-float forms of the three (M and V as head + tail FP32 pairs, ~48 bits;
+// for the double-float adjoint pass)
+int launch_adjoint_prep_df(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, const float* A,
+                           int RLP, int RL, const int4* blks, int nblks, float2* Mr, float2* V, double* dw,
+                           cudaStream_t st);
+int launch_adjoint_m_df(const double* dzeta, int nbins, int lmax, int ncat, int64_t zsize, float2* Mr,
+                        cudaStream_t st);
+int launch_vgemm_rows_df(const float* A, int RLP, int RL, int64_t row_lo, int64_t row_hi, const float2* Mr,
+                         int nbins, int lmax, float2* V, double* dw, const int* plist, const int* orig,
+                         int64_t q0, cudaStream_t st);
 
 // ---- api.cu / noalloc.cu -----------------------------------------------------
 void set_last_error(const char* msg);

@@ -21,15 +21,18 @@
 //                 shared-memory record.  Then every lane adds the chunk's 32
 //                 terms T_k w (x + iy)^m to the (lmax+1)^2 / 32 accumulator
 //                 slots it owns (double-float sums, no cross-lane reduction).
-//                 At a change of bin the slots go to FP64 shared memory; at
-//                 the primary's end the Chebyshev -> Legendre-form connection
-//                 (times K_lm) is applied in FP64 and the row of A is stored.
+//                 At a change of bin the slots go to double-float shared
+//                 memory; at the primary's end the Chebyshev -> Legendre-form
+//                 connection (times K_lm, head + tail coefficients) is applied
+//                 in double-float and the row of A is stored.  No FP64
+//                 arithmetic: the FP64 pipe runs at 1/58 of the FP32 rate here.
 //   k_adj_df   -- per primary (one warp), one pair per lane: the adjoint
 //                 coefficients G_{m,k} = w_i sum_l c^(m)_{l-m,k} K_lm V_lm of
 //                 the primary (FP64 from the FP64 V = M A, held as head + tail
 //                 in shared memory), and per pair F = sum Re(conj(G) T_k
-//                 (x + iy)^m) with its gradient in double-float; FP64 atomics
-//                 for the secondary, a double-float sum for the primary.
+//                 (x + iy)^m) with its gradient in double-float, rounded once
+//                 to FP32 per pair; FP64 atomics for the secondary, a
+//                 double-float sum for the primary.
 #include "pair_common.cuh"
 
 namespace g3 {
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(kDThreads) k_accum_df(ListArgs a) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int B = a.bins.nbins;
     unsigned char* base = draw + (size_t)wid * accum_df_smem_per_warp(L, B, NRP);
-    double* res = reinterpret_cast<double*>(base);                          // [B][NRP]
+    float2* res = reinterpret_cast<float2*>(base);                          // [B][NRP] head, tail
     float4* img = reinterpret_cast<float4*>(base + (size_t)B * NRP * 8);    // [54]
     df* Rd = reinterpret_cast<df*>(base + (size_t)B * NRP * 8 + 54 * 16);   // [9]
     float* rec = reinterpret_cast<float*>(base + (size_t)B * NRP * 8 + 54 * 16 + 9 * 8 + 8);  // [32][RS]
@@ -236,7 +239,7 @@ __global__ void __launch_bounds__(kDThreads) k_accum_df(ListArgs a) {
             }
             Rd[lane] = df_from(radial ? los_rotation_entry_d(lane, x0, x1, x2, g.boxd) : ((lane % 4 == 0) ? 1.0 : 0.0));
         }
-        for (int k = lane; k < B * NRP; k += 32) res[k] = 0.0;
+        for (int k = lane; k < B * NRP; k += 32) res[k] = make_float2(0.f, 0.f);
         const int cb = a.base[q] < 0 ? 0 : a.base[q];
         const int nch = a.nchunks[q];
         const int* chunks = a.chunks + (int64_t)cb * 32;
@@ -249,7 +252,11 @@ __global__ void __launch_bounds__(kDThreads) k_accum_df(ListArgs a) {
 #pragma unroll
             for (int s = 0; s < S; ++s) {
                 const int slot = lane + 32 * s;
-                if (slot < NR) res[b * NRP + slot] += df_to(acc[s]);
+                if (slot < NR) {
+                    const float2 o = res[b * NRP + slot];
+                    const df v = df_add({o.x, o.y}, acc[s]);
+                    res[b * NRP + slot] = make_float2(v.h, v.l);
+                }
                 acc[s] = {0.f, 0.f};
             }
         };
@@ -349,10 +356,13 @@ __global__ void __launch_bounds__(kDThreads) k_accum_df(ListArgs a) {
         float* Arow = a.A + (int64_t)row * a.RLP;
         for (int col = lane; col < a.RL; col += 32) {
             const int4 cv = __ldg(a.colconv + col);
-            const double* cf = a.colcoef64 + cv.w;
-            double v = 0.0;
-            for (int k = 0; k < cv.z; ++k) v = fma(__ldg(cf + k), res[cv.x + cv.y * k], v);
-            Arow[col] = (float)v;
+            const float2* cf = a.colcoefdf + cv.w;
+            df v = {0.f, 0.f};
+            for (int k = 0; k < cv.z; ++k) {
+                const float2 c = __ldg(cf + k), r = res[cv.x + cv.y * k];
+                v = df_add(v, df_mul({c.x, c.y}, {r.x, r.y}));
+            }
+            Arow[col] = __fadd_rn(v.h, v.l);
         }
         if (lane == 0) a.wrow[row] = P0.w;
         __syncwarp();
@@ -384,14 +394,16 @@ __global__ void __launch_bounds__(kDThreads) k_adj_df(ListArgs a) {
         const float4 P0 = a.pts[p];
         if (lane < 27) image_df(img, lane, P0, a.pts64, p, g.boxd);
         const int row = a.orig[p];
-        const double* Vrow = a.V64 + (int64_t)(a.chunked ? q - a.q0 : row) * a.RLP;
-        const double wi = (double)P0.w;
+        const float2* Vrow = a.Vdf + (int64_t)(a.chunked ? q - a.q0 : row) * a.RLP;
         for (int idx = lane; idx < B * NR; idx += 32) {
             const int b = idx / NR, sl = idx - b * NR;
             const int4 cv = __ldg(a.slotconv + sl);
-            double v = 0.0;
-            for (int t = 0; t < cv.z; ++t) v = fma(__ldg(a.slotcoef64 + cv.w + t), Vrow[cv.x + b + t * cv.y], v);
-            const df gv = df_from(wi * v);
+            df v = {0.f, 0.f};
+            for (int t = 0; t < cv.z; ++t) {
+                const float2 c = __ldg(a.slotcoefdf + cv.w + t), x = Vrow[cv.x + b + t * cv.y];
+                v = df_add(v, df_mul({c.x, c.y}, {x.x, x.y}));
+            }
+            const df gv = df_mulf(v, P0.w);
             G[b * NRP + sl] = make_float2(gv.h, gv.l);
         }
         const int cb = a.base[q] < 0 ? 0 : a.base[q];
@@ -480,21 +492,23 @@ __global__ void __launch_bounds__(kDThreads) k_adj_df(ListArgs a) {
                 pr = ur;
                 pim = ui;
             });
-            // tangential gradient: (2 w_j / r) (grad F - (grad F . u) u)
+            // tangential gradient: (2 w_j / r) (grad F - (grad F . u) u), formed in
+            // double-float and rounded once: a per-pair relative error of an FP32
+            // ulp is not amplified by the sums over pairs
             const df gdr = df_add(df_add(df_mul(Fx, ux), df_mul(Fy, uy)), df_mul(Fz, z));
             const float tx = df_add(Fx, df_neg(df_mul(gdr, ux))).h;
             const float ty = df_add(Fy, df_neg(df_mul(gdr, uy))).h;
             const float tz = df_add(Fz, df_neg(df_mul(gdr, z))).h;
-            const double sc = 2.0 * (double)qv.w * df_to(rinv);
-            const double gx = sc * (double)tx, gy = sc * (double)ty, gz3 = sc * (double)tz;
+            const float sc = __fmul_rn(2.f * qv.w, __fadd_rn(rinv.h, rinv.l));
+            const float gx = __fmul_rn(sc, tx), gy = __fmul_rn(sc, ty), gz3 = __fmul_rn(sc, tz);
             const int jj = __ldg(a.orig + (e & kIdxMask));
-            atomicAdd(a.dw + jj, 2.0 * df_to(F));
-            atomicAdd(a.dpos + 3 * (int64_t)jj, gx);
-            atomicAdd(a.dpos + 3 * (int64_t)jj + 1, gy);
-            atomicAdd(a.dpos + 3 * (int64_t)jj + 2, gz3);
-            df_acc(pix, df_from(gx));
-            df_acc(piy, df_from(gy));
-            df_acc(piz, df_from(gz3));
+            atomicAdd(a.dw + jj, (double)__fmul_rn(2.f, __fadd_rn(F.h, F.l)));
+            atomicAdd(a.dpos + 3 * (int64_t)jj, (double)gx);
+            atomicAdd(a.dpos + 3 * (int64_t)jj + 1, (double)gy);
+            atomicAdd(a.dpos + 3 * (int64_t)jj + 2, (double)gz3);
+            df_acc(pix, {gx, 0.f});
+            df_acc(piy, {gy, 0.f});
+            df_acc(piz, {gz3, 0.f});
         }
         double di0 = -df_to(pix), di1 = -df_to(piy), di2 = -df_to(piz);
 #pragma unroll
