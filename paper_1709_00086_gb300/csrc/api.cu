@@ -967,11 +967,9 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
         const int part_stride = ntiles * T * T;
         // segments of every chunk (partial slots are global across chunks)
         std::vector<std::vector<Segment>> csegs(nchunks);
-        // tensor-core work units per virtual segment: a two-tile strip takes one
-        // segment per CTA, a one-tile strip two
-        double tc_units = 0.0;
-        for (const TcStrip& sp : P->strips_tc) tc_units += sp.ntile == 2 ? 1.0 : 0.5;
-        if (tc_units <= 0.0) tc_units = 1.0;
+        // tensor-core work split per (chunk, catalog): segments per item of every strip
+        const int nstrips = (int)P->strips_tc.size();
+        std::vector<std::vector<int>> csteps(nchunks);
         const int64_t rows_tot = chunked ? std::min<int64_t>(C, rows_all) : rows_all;
         std::vector<int> segfirst(c.ncat + 1, 0);
         std::vector<std::vector<int>> ccats(nchunks);
@@ -987,16 +985,17 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
                 const int64_t len = r1 - r0;
                 if (use_tc) {
                     // padded primary coordinates: every catalog starts on a k-block; an
-                    // even number V of virtual segments per catalog, about
-                    // nsm * (catalog share of the primaries) / (work units per segment)
+                    // V equal virtual segments per catalog; every strip's items cover
+                    // step[s] of them, balanced over the catalog's share of the SMs
                     const int64_t plen = (len + KB - 1) / KB * KB;
                     ccats[ch].insert(ccats[ch].end(), {(int)cpad[ch], (int)r0, (int)len, 0});
                     const double share = rows_tot > 0 ? (double)plen / (double)rows_tot : 1.0;
-                    int64_t V = 2 * (int64_t)std::llround(share * P->nsm / (2.0 * tc_units));
                     // at least one full FP32 accumulation run (2048 primaries) per segment
                     const int64_t vmax = 2 * (plen / (2 * 2048));
-                    if (V > vmax) V = vmax;
-                    if (V < 2) V = 2;
+                    const size_t st0 = csteps[ch].size();
+                    csteps[ch].resize(st0 + (size_t)nstrips);
+                    const int64_t V = plan_tc_items(P->strips_tc.data(), nstrips, (int)std::min<int64_t>(vmax, 1 << 20),
+                                                    share * P->nsm, csteps[ch].data() + st0);
                     const int64_t seg = ((plen + V - 1) / V + KB - 1) / KB * KB;
                     for (int64_t v = 0; v < V; ++v) {
                         Segment sg;
@@ -1095,13 +1094,15 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
                     UP(P->d_cats.p, ccats[ch].data(), 4 * ccats[ch].size());
                     P->launches += 1;
                     // work items: every strip over every virtual segment of every
-                    // catalog (one-tile strips two segments at a time)
+                    // catalog, step[s] consecutive segments at a time (planned above)
                     std::vector<TcItem> items;
-                    for (int s0 = 0; s0 < nsegs;) {
+                    int kc = 0;  // catalog index within this chunk
+                    for (int s0 = 0; s0 < nsegs; ++kc) {
                         int s1 = s0;
                         while (s1 < nsegs && segs[s1].cat == segs[s0].cat) ++s1;
-                        for (int k = 0; k < (int)P->strips_tc.size(); ++k) {
-                            const int step = P->strips_tc[k].ntile == 2 ? 1 : 2;
+                        const int* stp = csteps[ch].data() + (size_t)kc * nstrips;
+                        for (int k = 0; k < nstrips; ++k) {
+                            const int step = stp[k];
                             for (int v = s0; v < s1; v += step)
                                 items.push_back(TcItem{k, v, std::min(step, s1 - v), 0});
                         }

@@ -22,19 +22,27 @@
 // into an even number of equal "virtual segments"; a two-tile strip takes one
 // per CTA and a one-tile strip two, so that every CTA does the same MMA work
 // (its partial goes to the first slot and the second is zeroed).
-//   warps 5-12 (converters): per k-block of 64 primaries, read the rows of A
-//     (coalesced 128-byte pieces of each row), scale them by sqrt(w) (or by 1
-//     and w), split into bf16 hi and lo and store them K-major in the 128-byte
-//     swizzled shared-memory layout of the MMA descriptors; only the columns of
-//     the strip's m block are read (the rest of a panel is zero); a ring of 2
-//     to 7 stages, handed to the MMA thread through mbarriers;
-//   warp 4 (one thread): tcgen05.mma into an N-column TMEM accumulator,
-//     double-buffered per run of kSubKB k-blocks;
-//   warps 0-3 (drain): tcgen05.ld of each finished run, added to the FP64
-//     partials (one per (virtual segment, tile)) that the FP64 reduction adds
-//     in a fixed order.
+//   warp 9 (TMA): per k-block of 64 primaries and panel, one 2-D bulk copy of
+//     the FP32 rows of A (the columns the panel's MMAs use, from the panel's
+//     first column rounded down to a 16-byte boundary) into a staging slot,
+//     with the primaries' scales of that side (sqrt(w), or 1 and w) beside it;
+//   warps 10-25 (converters): scale the staged rows, split them into bf16 hi
+//     and lo and store them K-major in the 128-byte swizzled shared-memory
+//     layout of the MMA descriptors, in one operand stage handed to the MMA
+//     thread through mbarriers; every converter warp runs on its own, and a
+//     warp whose rows no MMA uses forms nothing;
+//   warp 8 (one thread): tcgen05.mma of width N (the strip's valid columns
+//     rounded up to 16) into a TMEM accumulator, double-buffered per run of
+//     kSubKB k-blocks;
+//   warps 0-7 (drain): tcgen05.ld of each finished run (two warps per TMEM
+//     lane quarter, alternate 32-column groups), added to the FP64 partials
+//     (one per (virtual segment, tile), kept in L2 with evict-last priority)
+//     that the FP64 reduction adds in a fixed order.
 // Every wait is bounded: on expiry the kernel records a timeout in the status
-// word, all warps stop at an agreed point, the TMEM is freed and it returns.
+// word, every warp stops at its next wait, the TMA thread lets its own copies
+// land, the TMEM is freed and the kernel returns.
+#include <algorithm>
+#include <vector>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -49,18 +57,30 @@ namespace {
 
 constexpr int kTT = 128;          // output tile edge (M = N = 128)
 constexpr int kKB = 64;           // primaries per k-block (one 128-byte swizzle row of bf16)
+constexpr int kKSteps = kKB / 16;  // MMA k-steps per k-block (K = 16 for kind::f16)
 constexpr int kOpBytes = kTT * kKB * 2;          // one operand box (128 rows x 64 primaries): 16 KB
 // stage buffers: 2 to 6 operand boxes per stage (R hi / lo of one or two panels,
-// L hi / lo unless shared with R), as many stages as fit
-constexpr int kBufBytes = 13 * kOpBytes;         // 208 KB: operand stages + FP32 staging slots
-constexpr int kMaxStages = 7;
+// L hi / lo unless shared with R).  One operand stage: while the MMAs read it
+// the converters only load and split the next k-block, and store it once the
+// MMAs are done (measured faster than a ring of stages, where the converters'
+// stores and the MMAs' operand reads contend for shared-memory bandwidth:
+// 4.37 vs 4.65 ms on the 2M-point workload); the rest holds FP32 staging slots.
+constexpr int kBufBytes = 13 * kOpBytes;         // 208 KB: operand stage + FP32 staging slots
+constexpr int kMaxStages = 1;
 // FP32 staging of one unit (one panel of one k-block): rows of A for the 64
 // primaries, 132 columns from the panel's first column rounded down to a
 // multiple of 4 (a TMA box must start on a 16-byte boundary)
 constexpr int kStgCols = kTT + 4;
 constexpr int kStgBytes = kKB * kStgCols * 4;    // 33,792 bytes
+// A unit copies only the columns its panel's MMAs use: boxes of 32 w + 4
+// columns (w = 1..4, tensor map w - 1), staged with that row pitch.
+constexpr int kBoxes = kTT / 32;
+__host__ __device__ constexpr int box_cols(int wi) { return 32 * (wi + 1) + 4; }
+struct TcMaps {
+    CUtensorMap m[kBoxes];
+};
 
-constexpr int kMaxStg = 4;
+constexpr int kMaxStg = 6;
 static_assert(kBufBytes + 1024 + 1024 <= 227 * 1024, "stage buffers and barriers fit in shared memory");
 constexpr unsigned kSpinLimit = 1u << 26;        // bounded waits
 
@@ -154,12 +174,13 @@ struct TcArgs {
 };
 
 constexpr int kSubKB = 32;          // k-blocks per FP32 accumulation run (2048 primaries)
-constexpr int kDrainWarps = 4;      // warps 0-3: TMEM drain (lanes 0-127)
-constexpr int kMmaWarp = 4;         // warp 4: MMA issue
-constexpr int kTmaWarp = 5;         // warp 5: TMA loads of the FP32 rows
-constexpr int kCvtWarps = 16;       // warps 6-21: operand formation
-constexpr int kCvtThreads = kCvtWarps * 32;
+constexpr int kDrainWarps = 8;      // warps 0-7: TMEM drain (lanes 32 (w % 4) .., column groups of parity w / 4)
+constexpr int kDrainBatch = 16;     // partial columns read before they are written back
+constexpr int kMmaWarp = 8;         // warp 8: MMA issue
+constexpr int kTmaWarp = 9;         // warp 9: TMA loads of the FP32 rows
+constexpr int kCvtWarps = 16;       // warps 10-25: operand formation
 constexpr int kTcWarps = kDrainWarps + 2 + kCvtWarps;
+static_assert(kCvtWarps * 32 == kTT * kKSteps, "one converter thread per (panel row, k-step)");
 
 __device__ __forceinline__ void tmem_ld32(unsigned taddr, unsigned (&r)[32]) {
     asm volatile(
@@ -173,6 +194,22 @@ __device__ __forceinline__ void tmem_ld32(unsigned taddr, unsigned (&r)[32]) {
           "=r"(r[31])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// The FP64 partials are re-read by every accumulation run of their CTA: kept in
+// L2 ahead of the streamed rows of A (evict-last priority).
+__device__ __forceinline__ unsigned long long l2_keep_policy() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ double ld_keep(const double* ptr, unsigned long long pol) {
+    double v;
+    asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_keep(double* ptr, double v, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(ptr), "d"(v), "l"(pol) : "memory");
 }
 
 // Bounded wait that also gives up when another warp has flagged an abort.
@@ -191,21 +228,9 @@ __device__ __forceinline__ bool mbar_wait_or_abort(unsigned bar, unsigned parity
     return false;
 }
 
-// Barrier 1 over the converter warps with an OR of a predicate: every converter
-// thread gets the same answer, so they stop (or go on) together.
-__device__ __forceinline__ bool cvt_barrier_any(bool pred) {
-    unsigned r;
-    asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
-        : "=r"(r)
-        : "r"((unsigned)pred), "r"(kCvtThreads)
-        : "memory");
-    return r != 0;
-}
-
 // One CTA = one work item (strip, virtual segments).  The k-blocks are
-// accumulated in runs of kSubKB into one of two TMEM buffers (columns [0, N)
-// and [N, 2N)); while the MMA warp fills one buffer the drain warps add the
+// accumulated in runs of kSubKB into one of two TMEM buffers (columns [0, Np)
+// and [Np, 2 Np)); while the MMA warp fills one buffer the drain warps add the
 // other into the FP64 partials, which bounds every FP32 accumulation run to
 // 3 * kSubKB * 4 MMA steps whatever the segment length.
 //   units: the panels of every k-block in order (u = nb kb + b; panel b < nt
@@ -213,13 +238,12 @@ __device__ __forceinline__ bool cvt_barrier_any(bool pred) {
 //   the TMA thread stages unit u in slot u % S, the converters turn it into
 //   the operand boxes of stage kb % O, the MMA thread consumes the stage.
 __global__ void __launch_bounds__(kTcWarps * 32, 1)
-    k_contract_tc(const __grid_constant__ CUtensorMap mA, TcArgs a) {
+    k_contract_tc(const __grid_constant__ TcMaps maps, TcArgs a) {
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     __shared__ __align__(8) unsigned long long bars[2 * kMaxStages + 2 * kMaxStg + 4];
     __shared__ unsigned tmem_slot;
     __shared__ int abort_flag;
-    __shared__ __align__(16) float meta_sl[2][kKB];  // per k-block: scale of each primary on the row (L) side
-    __shared__ __align__(16) float meta_sr[2][kKB];  // ... on the column (R) side
+    __shared__ __align__(16) float meta[kMaxStg][kKB];  // per staged unit: its side's scale of each primary
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const TcItem it = a.items[blockIdx.x];
     const TcStrip sp = a.strips[it.strip];
@@ -228,8 +252,9 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
     const int kb0 = row0 / kKB;
     const int nkb = (row1 - row0 + kKB - 1) / kKB;
     const int nsub = (nkb + kSubKB - 1) / kSubKB;
-    const int nt = sp.ntile;   // tiles side by side: N = 128 nt
-    const int N = kTT * nt;
+    const int nt = sp.ntile;   // tiles side by side (column panels of 128)
+    const int N = sp.n;        // MMA width: the strip's valid columns rounded up to 16
+    const int Np = kTT * nt;   // TMEM columns of one accumulator buffer
     const unsigned raw = smem_u32(tc_smem_raw);
     const unsigned sbase = (raw + 1023u) & ~1023u;  // 1024-byte aligned stage buffers
     unsigned char* sgen = tc_smem_raw + (sbase - raw);
@@ -239,10 +264,10 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
     const bool lshare = sym && sp.xrow == sp.xcol;
     const int nb = lshare ? nt : nt + 1;               // units (panels) per k-block
     const unsigned stage_bytes = (unsigned)(2 * nb) * kOpBytes;
-    // staging slots first (up to two k-blocks of copies in flight), then as many
-    // operand stages as fit (>= 1 for every strip shape)
+    // as many staging slots (copies in flight) as fit beside one operand stage
     int S = (int)((kBufBytes - stage_bytes) / kStgBytes);
     S = S < kMaxStg ? S : kMaxStg;
+    S = S > 1 ? S : 1;
     int O = (int)((kBufBytes - S * kStgBytes) / stage_bytes);
     O = O < kMaxStages ? O : kMaxStages;
     const unsigned stg0 = (unsigned)O * stage_bytes;   // staging after the operand stages
@@ -271,7 +296,7 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_slot)),
-                     "r"(2 * N)
+                     "r"(2 * Np)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -280,24 +305,71 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = tmem_slot;
     auto unit_col = [&](int b) { return b == nt ? sp.xrow : sp.xcol + kTT * b; };
+    // operand rows of unit b that the MMAs use: the B operand's N rows of a
+    // column panel, and the row panel's valid rows for A (the other rows of D
+    // are discarded); its box is the narrowest that holds them from xp & ~3
+    const int rowsL = a.tiles[sp.tile0].rows;
+    auto unit_need = [&](int b) {
+        const bool isL = b == nt;
+        const int needB = isL ? 0 : min(kTT, N - kTT * b);
+        return (isL || (lshare && b == 0)) ? max(needB, rowsL) : needB;
+    };
+    auto unit_box = [&](int b) { return (unit_need(b) + 31) / 32 - 1; };
 
     if (warp == kTmaWarp) {
-        if (lane == 0 && nunits > 0) {
-            int issued = 0;
-            bool ok = true;
-            for (int u = 0; u < nunits; ++u) {
-                const int slot = u % S;
-                if (u >= S && !mbar_wait_or_abort(sempty0 + 8 * slot, ((u / S) - 1) & 1, &abort_flag)) {
+        // unit u: the scales of its side into meta[u % S] (0 past the catalog),
+        // then the FP32 rows into staging slot u % S; the slot's mbarrier phase
+        // (the elected lane's arrive, release, and the copy's bytes) publishes both.
+        // The weights of k-block kb + 2 are loaded while kb is issued, so that no
+        // global load latency sits between two copies.
+        int issued = 0;
+        bool ok = true;
+        auto wload = [&](int kb, int i) -> float {
+            const int k = (kb0 + kb) * kKB + i - cat.x;
+            return (kb < nkb && k >= 0 && k < cat.z) ? __ldg(a.wrow + cat.y + k) : 0.f;
+        };
+        auto inrange = [&](int kb, int i) {
+            const int k = (kb0 + kb) * kKB + i - cat.x;
+            return k >= 0 && k < cat.z;
+        };
+        float w0a = wload(0, lane), w0b = wload(0, lane + 32);
+        float w1a = wload(1, lane), w1b = wload(1, lane + 32);
+        float w2a = 0.f, w2b = 0.f;
+        for (int u = 0; u < nunits; ++u) {
+            const int slot = u % S;
+            if (u >= S) {
+                const bool freed = mbar_wait_or_abort(sempty0 + 8 * slot, ((u / S) - 1) & 1, &abort_flag);
+                if (!__all_sync(0xffffffffu, freed)) {
                     ok = false;
                     break;
                 }
-                const int kb = u / nb, b = u - kb * nb;
+            }
+            const int kb = u / nb, b = u - kb * nb;
+            const bool isL = b == nt;
+            if (b == 0 && kb > 0) {
+                w0a = w1a;
+                w0b = w1b;
+                w1a = w2a;
+                w1b = w2b;
+            }
+            if (b == 0) {
+                w2a = wload(kb + 2, lane);
+                w2b = wload(kb + 2, lane + 32);
+            }
+            static_assert(kKB == 64, "two weights per lane");
+            meta[slot][lane] = sym ? sqrtf(w0a) : (isL ? (inrange(kb, lane) ? 1.f : 0.f) : w0a);
+            meta[slot][lane + 32] = sym ? sqrtf(w0b) : (isL ? (inrange(kb, lane + 32) ? 1.f : 0.f) : w0b);
+            __syncwarp();
+            if (lane == 0) {
                 const int xp = unit_col(b);
                 const int y = cat.y + (kb0 + kb) * kKB - cat.x;  // A row of the k-block's first primary
-                mbar_expect_tx(sfull0 + 8 * slot, kStgBytes);
-                tma_load_2d(sbase + stg0 + slot * kStgBytes, &mA, xp & ~3, y, sfull0 + 8 * slot);
-                ++issued;
+                const int wi = unit_box(b);
+                mbar_expect_tx(sfull0 + 8 * slot, (unsigned)(box_cols(wi) * kKB * 4));
+                tma_load_2d(sbase + stg0 + slot * kStgBytes, &maps.m[wi], xp & ~3, y, sfull0 + 8 * slot);
             }
+            ++issued;
+        }
+        if (lane == 0) {
             if (!ok && !abort_flag) {
                 abort_flag = 1;
                 atomicOr(a.status, kStatusTimeout);
@@ -334,7 +406,7 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
                 const unsigned st = sbase + o * stage_bytes;
                 const unsigned Rh = st, Rl = st + nt * kOpBytes;
                 const unsigned Lh = lshare ? Rh : st + 2 * nt * kOpBytes, Ll = lshare ? Rl : Lh + kOpBytes;
-                const unsigned d = tmem + (unsigned)(buf * N);
+                const unsigned d = tmem + (unsigned)(buf * Np);
 #pragma unroll
                 for (int k = 0; k < kKB / 16; ++k) {
                     const unsigned off = k * 32;  // 16 bf16 along K inside the swizzled row
@@ -366,62 +438,65 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
         // 16-byte stores (one chunk of 8 primaries per lane) cover every bank
         // group four times.  No per-element test: a primary past its catalog
         // has scale 0, columns past the m block only feed discarded rows of the
-        // tile, and the box reads zeros past the ends of A.
+        // tile, and the box reads zeros past the ends of A.  Every converter
+        // warp runs on its own: the mbarriers order it against the TMA and MMA
+        // threads, and a warp that stops on an expired wait raises the abort
+        // flag, which ends the other warps' next wait.
         const int ct = threadIdx.x - (kTmaWarp + 1) * 32;
         const int r = ct & (kTT - 1);
         const int q = ct >> 7;
         const unsigned swz = (unsigned)((r >> 3) * 1024 + (r & 7) * 128);
+        // a warp whose 32 rows are all past unit_need forms nothing (the MMAs
+        // never read those rows, or read them only into discarded rows of D)
+        const int r0w = r & ~31;
         for (int u = 0; u < nunits; ++u) {
             const int kb = u / nb, b = u - kb * nb;
-            const int o = kb % O, mb = kb & 1, slot = u % S;
-            if (b == 0 && ct < kKB) {  // the k-block's scales (both sides); 0 past the catalog
-                const int k = (kb0 + kb) * kKB + ct - cat.x;
-                const float w = (k >= 0 && k < cat.z) ? __ldg(a.wrow + cat.y + k) : 0.f;
-                meta_sl[mb][ct] = sym ? sqrtf(w) : ((k >= 0 && k < cat.z) ? 1.f : 0.f);
-                meta_sr[mb][ct] = sym ? sqrtf(w) : w;
-            }
-            bool ok = mbar_wait_or_abort(sfull0 + 8 * slot, (u / S) & 1, &abort_flag);
-            if (cvt_barrier_any(!ok || abort_flag != 0)) {
-                if (!ok && !abort_flag) {
+            const int o = kb % O, slot = u % S;
+            const bool landed = mbar_wait_or_abort(sfull0 + 8 * slot, (u / S) & 1, &abort_flag);
+            if (!__all_sync(0xffffffffu, landed)) {
+                if (lane == 0 && !abort_flag) {
                     abort_flag = 1;
                     atomicOr(a.status, kStatusTimeout);
                 }
                 break;
             }
             const int xp = unit_col(b);
+            const bool isL = b == nt;
+            const bool active = r0w < unit_need(b);  // warp-uniform
+            const int pitch = box_cols(unit_box(b));
             const float* stg = reinterpret_cast<const float*>(sgen + stg0 + slot * kStgBytes) +
-                               (16 * q) * kStgCols + (xp & 3) + r;
+                               (16 * q) * pitch + (xp & 3) + r;
+            const float4* sc4 = reinterpret_cast<const float4*>(&meta[slot][16 * q]);
             float cur[16];
+            if (active) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) cur[i] = stg[i * kStgCols];
+                for (int c = 0; c < 4; ++c) {
+                    const float4 sc = sc4[c];
+                    cur[4 * c] = __fmul_rn(stg[(4 * c) * pitch], sc.x);
+                    cur[4 * c + 1] = __fmul_rn(stg[(4 * c + 1) * pitch], sc.y);
+                    cur[4 * c + 2] = __fmul_rn(stg[(4 * c + 2) * pitch], sc.z);
+                    cur[4 * c + 3] = __fmul_rn(stg[(4 * c + 3) * pitch], sc.w);
+                }
+            }
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sempty0 + 8 * slot) : "memory");
-            const bool isL = b == nt;
-            const float4* sc4 = reinterpret_cast<const float4*>((isL ? meta_sl[mb] : meta_sr[mb]) + 16 * q);
             unsigned h[8], l[8];
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {  // 16-byte chunk c: 8 primaries
-                const float4 s0 = sc4[2 * c], s1 = sc4[2 * c + 1];
-                const float2 sc2[4] = {make_float2(s0.x, s0.y), make_float2(s0.z, s0.w), make_float2(s1.x, s1.y),
-                                       make_float2(s1.z, s1.w)};
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int i0 = 8 * c + 2 * e;
-                    const float2 y = __fmul2_rn(make_float2(cur[i0], cur[i0 + 1]), sc2[e]);
-                    const __nv_bfloat162 hp = __floats2bfloat162_rn(y.x, y.y);
-                    const unsigned hu = *reinterpret_cast<const unsigned*>(&hp);
-                    const float2 hf = make_float2(__uint_as_float(hu << 16), __uint_as_float(hu & 0xffff0000u));
-                    const float2 dd = __fadd2_rn(y, make_float2(-hf.x, -hf.y));
-                    const __nv_bfloat162 lp = __floats2bfloat162_rn(dd.x, dd.y);
-                    h[4 * c + e] = hu;
-                    l[4 * c + e] = *reinterpret_cast<const unsigned*>(&lp);
-                }
+            for (int e = 0; e < 8; ++e) {
+                const float2 y = make_float2(cur[2 * e], cur[2 * e + 1]);
+                const __nv_bfloat162 hp = __floats2bfloat162_rn(y.x, y.y);
+                const unsigned hu = *reinterpret_cast<const unsigned*>(&hp);
+                const float2 hf = make_float2(__uint_as_float(hu << 16), __uint_as_float(hu & 0xffff0000u));
+                const float2 dd = __fadd2_rn(y, make_float2(-hf.x, -hf.y));
+                const __nv_bfloat162 lp = __floats2bfloat162_rn(dd.x, dd.y);
+                h[e] = hu;
+                l[e] = *reinterpret_cast<const unsigned*>(&lp);
             }
             // the operand stage must have been read by the MMAs of k-block kb - O
             if (b == 0 && kb >= O) {
-                ok = mbar_wait_or_abort(oempty0 + 8 * o, ((kb / O) - 1) & 1, &abort_flag);
-                if (cvt_barrier_any(!ok || abort_flag != 0)) {
-                    if (!ok && !abort_flag) {
+                const bool freed = mbar_wait_or_abort(oempty0 + 8 * o, ((kb / O) - 1) & 1, &abort_flag);
+                if (!__all_sync(0xffffffffu, freed)) {
+                    if (lane == 0 && !abort_flag) {
                         abort_flag = 1;
                         atomicOr(a.status, kStatusTimeout);
                     }
@@ -431,11 +506,15 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
             const unsigned st = o * stage_bytes;
             unsigned char* hib = sgen + st + (isL ? 2 * nt : b) * kOpBytes + swz;
             unsigned char* lob = sgen + st + (isL ? 2 * nt + 1 : nt + b) * kOpBytes + swz;
+            if (active) {
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const unsigned chunk = (unsigned)(((2 * q + c) ^ (r & 7)) << 4);
-                *reinterpret_cast<uint4*>(hib + chunk) = make_uint4(h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]);
-                *reinterpret_cast<uint4*>(lob + chunk) = make_uint4(l[4 * c], l[4 * c + 1], l[4 * c + 2], l[4 * c + 3]);
+                for (int c = 0; c < 2; ++c) {
+                    const unsigned chunk = (unsigned)(((2 * q + c) ^ (r & 7)) << 4);
+                    *reinterpret_cast<uint4*>(hib + chunk) =
+                        make_uint4(h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]);
+                    *reinterpret_cast<uint4*>(lob + chunk) =
+                        make_uint4(l[4 * c], l[4 * c + 1], l[4 * c + 2], l[4 * c + 3]);
+                }
             }
             if (b == nb - 1) {
                 // the MMA reads shared memory through the async proxy
@@ -445,9 +524,12 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
             }
         }
     } else {
-        // drain warps: TMEM lane (= output row) warp*32 + lane; column c of the
-        // accumulator is column c % 128 of the strip's tile c / 128
-        const int row = warp * 32 + lane;
+        // drain warps: TMEM lane (= output row) 32 (warp % 4) + lane; column c of
+        // the accumulator is column c % 128 of the strip's tile c / 128; warp w
+        // takes the 32-column groups g with g % 2 == w / 4
+        const int quarter = warp & 3, half = warp >> 2;
+        const int row = quarter * 32 + lane;
+        const unsigned long long keep = l2_keep_policy();
         double* outs = a.partials + (int64_t)it.vseg0 * a.part_stride;
         for (int sub = 0; sub < nsub; ++sub) {
             const int buf = sub & 1;
@@ -457,20 +539,35 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
                 if (lane == 0) atomicOr(a.status, kStatusTimeout);
                 break;
             }
+            // the partial is column-major (a warp's rows of one column are one
+            // 256-byte line); a run after the first adds to it, reading a batch
+            // of kDrainBatch columns before writing them, so that the batch's
+            // loads are in flight together
 #pragma unroll 1
-            for (int c0 = 0; c0 < N; c0 += 32) {
+            for (int c0 = 32 * half; c0 < N; c0 += 64) {
                 unsigned rr[32];
-                tmem_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(buf * N + c0), rr);
+                tmem_ld32(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)(buf * Np + c0), rr);
                 const Tile t = a.tiles[sp.tile0 + c0 / kTT];
                 const int cc = c0 % kTT;
-                double* out = outs + t.out_off;
+                const int ncol = t.cols - cc;  // valid columns from cc (the tile's width)
+                double* out = outs + t.out_off + (int64_t)cc * kTT + row;
                 if (row < t.rows) {
+                    if (sub == 0) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        if (cc + j < t.cols) {
-                            double* o = out + (int64_t)(cc + j) * kTT + row;  // column-major
-                            const double v = (double)__uint_as_float(rr[j]);
-                            *o = (sub == 0) ? v : *o + v;
+                        for (int j = 0; j < 32; ++j)
+                            if (j < ncol) st_keep(out + (int64_t)j * kTT, (double)__uint_as_float(rr[j]), keep);
+                    } else {
+#pragma unroll
+                        for (int h = 0; h < 32; h += kDrainBatch) {
+                            double old[kDrainBatch];
+#pragma unroll
+                            for (int j = 0; j < kDrainBatch; ++j)
+                                old[j] = (h + j < ncol) ? ld_keep(out + (int64_t)(h + j) * kTT, keep) : 0.0;
+#pragma unroll
+                            for (int j = 0; j < kDrainBatch; ++j)
+                                if (h + j < ncol)
+                                    st_keep(out + (int64_t)(h + j) * kTT, old[j] + (double)__uint_as_float(rr[h + j]),
+                                            keep);
                         }
                     }
                 }
@@ -485,14 +582,14 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
             const Tile t = a.tiles[sp.tile0 + p];
             for (int v = (nsub == 0 ? 0 : 1); v < it.nvseg; ++v) {
                 double* out = a.partials + (int64_t)(it.vseg0 + v) * a.part_stride + t.out_off;
-                for (int c = 0; c < kTT; ++c) out[(int64_t)c * kTT + row] = 0.0;
+                for (int c = half; c < kTT; c += 2) out[(int64_t)c * kTT + row] = 0.0;
             }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * N)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * Np)
                      : "memory");
 }
 
@@ -510,13 +607,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // FP32 rows of A as a 2-D tensor: RL columns (inner) x rows, row pitch RLP
-// floats; boxes of kStgCols x kKB, no swizzle, zeros outside.
-int make_map_a(CUtensorMap* m, const float* A, int RLP, int RL, int64_t rows) {
+// floats; boxes of `cols` x kKB, no swizzle, zeros outside.
+int make_map_a(CUtensorMap* m, const float* A, int RLP, int RL, int64_t rows, int cols) {
     auto fn = encode_fn();
     if (!fn) return -1;
     cuuint64_t dims[2] = {(cuuint64_t)RL, (cuuint64_t)(rows > 0 ? rows : 1)};
     cuuint64_t strides[1] = {(cuuint64_t)RLP * 4};
-    cuuint32_t box[2] = {kStgCols, kKB};
+    cuuint32_t box[2] = {(cuuint32_t)cols, kKB};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -538,6 +635,8 @@ int make_strips(const Tile* tiles, int ntiles, TcStrip* out, int max_strips) {
         if (n >= max_strips) return -1;
         out[n].tile0 = k;
         out[n].ntile = pair ? 2 : 1;
+        const int cols = tiles[k].cols + (pair ? tiles[k + 1].cols : 0);
+        out[n].n = (cols + 15) / 16 * 16;  // kind::f16 with M = 128: N a multiple of 16, <= 256
         out[n].xrow = tiles[k].col0 + tiles[k].r0;
         out[n].xcol = tiles[k].col0 + tiles[k].c0;
         ++n;
@@ -548,13 +647,31 @@ int make_strips(const Tile* tiles, int ntiles, TcStrip* out, int max_strips) {
 
 int contract_tc_kblock() { return kKB; }
 
+// Every CTA takes the same number of k-blocks: a strip's k-block costs about
+// the same whatever its width (the per-k-block copies and hand-offs bound it),
+// so a two-tile strip, with twice the operand panels, takes one segment per
+// item and a one-tile strip two.
+int plan_tc_items(const TcStrip* strips, int nstrips, int vmax, double slots, int* step) {
+    double units = 0.0;  // items per virtual segment
+    for (int s = 0; s < nstrips; ++s) {
+        step[s] = strips[s].ntile == 2 ? 1 : 2;
+        units += 1.0 / step[s];
+    }
+    if (units <= 0.0) units = 1.0;
+    int V = 2 * (int)std::llround(slots / (2.0 * units));
+    if (V > vmax) V = vmax;
+    if (V < 2) V = 2;
+    return V;
+}
+
 int launch_contract_tc(const float* A, int RLP, int RL, int64_t arows, const float* wrow, const int4* cats,
                        const Tile* tiles, const TcStrip* strips, const TcItem* items, int nitems,
                        const Segment* segs, double* partials, int part_stride, const int* negw, int* status,
                        cudaStream_t st, int test_timeout) {
     if (nitems <= 0) return 0;
-    CUtensorMap m;
-    if (make_map_a(&m, A, RLP, RL, arows) != 0) return -2;
+    TcMaps m;
+    for (int wi = 0; wi < kBoxes; ++wi)
+        if (make_map_a(&m.m[wi], A, RLP, RL, arows, box_cols(wi)) != 0) return -2;
     const int smem = kBufBytes + 1024;
     if (cudaFuncSetAttribute(k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
         cudaSuccess)

@@ -291,11 +291,17 @@ int contract_tc_kblock();
 // cats: per catalog {padded start, first A row, length, 0}.
 // A strip: ntile (1 or 2) output tiles side by side in one row panel, tiles
 // tile0.. of the tile list; xrow / xcol = A column of its first row / column.
-struct TcStrip { int tile0; int ntile; int xrow; int xcol; };
+// A strip: ntile (1 or 2) tiles of one row panel from tile0, computed as one
+// M = 128 MMA of width n (the strip's valid columns rounded up to 16).
+struct TcStrip { int tile0; int ntile; int xrow; int xcol; int n; };
 // A work item of the tensor-core contraction: a strip and nvseg (1 or 2)
 // consecutive virtual segments from vseg0 (partials go to slot vseg0).
 struct TcItem { int strip; int vseg0; int nvseg; int pad; };
 int make_strips(const Tile* tiles, int ntiles, TcStrip* out, int max_strips);
+// Work split of one catalog for the tensor-core contraction: returns V, the
+// number of equal virtual segments (even, >= 2, <= vmax unless vmax < 2), about
+// slots / (items per segment), and step[s], the segments per work item of strip s.
+int plan_tc_items(const TcStrip* strips, int nstrips, int vmax, double slots, int* step);
 // arows: rows of A in the buffer (the tensor map's extent; rows beyond read as 0)
 int launch_contract_tc(const float* A, int RLP, int RL, int64_t arows, const float* wrow, const int4* cats,
                        const Tile* tiles, const TcStrip* strips, const TcItem* items, int nitems,
