@@ -330,6 +330,20 @@ __device__ __forceinline__ float los_rotation_entry(int lane, double x0, double 
     return (float)los_rotation_entry_d(lane, x0, x1, x2, boxd);
 }
 
+// A float widened to double by its IEEE-754 fields on the integer ALU (sign,
+// exponent rebiased from 127 to 1023, 23 mantissa bits moved to the top of
+// 52): exact, and no FP64-pipe conversion, which runs at 1/64 of the FP32
+// rate here.  Zero keeps its sign; subnormal, infinite and NaN inputs take the
+// plain conversion.
+__device__ __forceinline__ double f2d_exact(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    if (e == 0u || e == 0xffu) return (double)x;
+    const unsigned hi = (u & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((u >> 3) & 0x000fffffu);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+
 // Cell coordinates of a position (the index build's formula).
 __device__ __forceinline__ int cell_of(float x, const Grid& g) {
     const int c = (int)(x * g.inv_cell);

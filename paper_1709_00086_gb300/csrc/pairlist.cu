@@ -767,10 +767,10 @@ __global__ void __launch_bounds__(kLThreads) k_adj(ListArgs a) {
                     const float sc = 2.f * qv.w * rinv;
                     const float gx = sc * fmaf(-gdr, ux, Fx), gy = sc * fmaf(-gdr, uy, Fy),
                                 gz3 = sc * fmaf(-gdr, z, Fz);
-                    atomicAdd(a.dw + jj, (double)(2.f * F));
-                    atomicAdd(a.dpos + 3 * (int64_t)jj, (double)gx);
-                    atomicAdd(a.dpos + 3 * (int64_t)jj + 1, (double)gy);
-                    atomicAdd(a.dpos + 3 * (int64_t)jj + 2, (double)gz3);
+                    atomicAdd(a.dw + jj, f2d_exact(2.f * F));
+                    atomicAdd(a.dpos + 3 * (int64_t)jj, f2d_exact(gx));
+                    atomicAdd(a.dpos + 3 * (int64_t)jj + 1, f2d_exact(gy));
+                    atomicAdd(a.dpos + 3 * (int64_t)jj + 2, f2d_exact(gz3));
                     pix += gx;
                     piy += gy;
                     piz += gz3;

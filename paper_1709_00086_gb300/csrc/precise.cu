@@ -137,15 +137,21 @@ __device__ __forceinline__ void unit_df(df dx, df dy, df dz, const df* R, bool r
 
 // Primary image `code` (position minus the code's box shift, FP64 input used
 // when given) as head + tail in shared memory: img[code] head, img[27 + code] tail.
+// FP32 input: the position is exact and the shift s (box_h + box_l) is added in
+// double-float; FP64 input: formed in FP64.
 __device__ __forceinline__ void image_df(float4* img, int code, const float4& P0, const double* pts64, int p,
-                                         double boxd) {
+                                         double boxd, df box) {
     const int sx = code % 3 - 1, sy = (code / 3) % 3 - 1, sz = code / 9 - 1;
-    double x = P0.x, y = P0.y, z = P0.z;
-    if (pts64) {
-        x = pts64[3 * (int64_t)p];
-        y = pts64[3 * (int64_t)p + 1];
-        z = pts64[3 * (int64_t)p + 2];
+    if (!pts64) {
+        auto shifted = [&](float v, int sh) {
+            return sh == 0 ? df{v, 0.f} : df_add({v, 0.f}, {-(float)sh * box.h, -(float)sh * box.l});
+        };
+        const df x = shifted(P0.x, sx), y = shifted(P0.y, sy), z = shifted(P0.z, sz);
+        img[code] = make_float4(x.h, y.h, z.h, 0.f);
+        img[27 + code] = make_float4(x.l, y.l, z.l, 0.f);
+        return;
     }
+    double x = pts64[3 * (int64_t)p], y = pts64[3 * (int64_t)p + 1], z = pts64[3 * (int64_t)p + 2];
     x -= sx * boxd;
     y -= sy * boxd;
     z -= sz * boxd;
@@ -220,6 +226,7 @@ __global__ void __launch_bounds__(kDThreads) k_accum_df(ListArgs a) {
         }
     }
     const Grid& g = a.g;
+    const df boxdf = df_from(g.boxd);  // the box side as head + tail
     const bool radial = g.radial != 0;
     const int qa = a.qrange ? a.qrange[0] : a.qa, qb = a.qrange ? a.qrange[1] : a.qb;
     for (;;) {
@@ -229,15 +236,19 @@ __global__ void __launch_bounds__(kDThreads) k_accum_df(ListArgs a) {
         if (q >= qb) break;
         const int p = a.plist ? a.plist[q] : q;
         const float4 P0 = a.pts[p];
-        if (lane < 27) image_df(img, lane, P0, a.pts64, p, g.boxd);
+        if (lane < 27) image_df(img, lane, P0, a.pts64, p, g.boxd, boxdf);
         if (lane < 9) {
-            double x0 = P0.x, x1 = P0.y, x2 = P0.z;
-            if (a.pts64) {
-                x0 = a.pts64[3 * (int64_t)p];
-                x1 = a.pts64[3 * (int64_t)p + 1];
-                x2 = a.pts64[3 * (int64_t)p + 2];
+            if (radial) {
+                double x0 = P0.x, x1 = P0.y, x2 = P0.z;
+                if (a.pts64) {
+                    x0 = a.pts64[3 * (int64_t)p];
+                    x1 = a.pts64[3 * (int64_t)p + 1];
+                    x2 = a.pts64[3 * (int64_t)p + 2];
+                }
+                Rd[lane] = df_from(los_rotation_entry_d(lane, x0, x1, x2, g.boxd));
+            } else {
+                Rd[lane] = {(lane % 4 == 0) ? 1.f : 0.f, 0.f};
             }
-            Rd[lane] = df_from(radial ? los_rotation_entry_d(lane, x0, x1, x2, g.boxd) : ((lane % 4 == 0) ? 1.0 : 0.0));
         }
         for (int k = lane; k < B * NRP; k += 32) res[k] = make_float2(0.f, 0.f);
         const int cb = a.base[q] < 0 ? 0 : a.base[q];
@@ -384,6 +395,7 @@ __global__ void __launch_bounds__(kDThreads) k_adj_df(ListArgs a) {
     float2* G = reinterpret_cast<float2*>(base);                           // [B][NRP] head, tail
     float4* img = reinterpret_cast<float4*>(base + (size_t)B * NRP * 8);   // [54]
     const Grid& g = a.g;
+    const df boxdf = df_from(g.boxd);  // the box side as head + tail
     const int qa = a.qrange ? a.qrange[0] : a.qa, qb = a.qrange ? a.qrange[1] : a.qb;
     for (;;) {
         int q = 0;
@@ -392,7 +404,7 @@ __global__ void __launch_bounds__(kDThreads) k_adj_df(ListArgs a) {
         if (q >= qb) break;
         const int p = a.plist ? a.plist[q] : q;
         const float4 P0 = a.pts[p];
-        if (lane < 27) image_df(img, lane, P0, a.pts64, p, g.boxd);
+        if (lane < 27) image_df(img, lane, P0, a.pts64, p, g.boxd, boxdf);
         const int row = a.orig[p];
         const float2* Vrow = a.Vdf + (int64_t)(a.chunked ? q - a.q0 : row) * a.RLP;
         for (int idx = lane; idx < B * NR; idx += 32) {
@@ -502,10 +514,10 @@ __global__ void __launch_bounds__(kDThreads) k_adj_df(ListArgs a) {
             const float sc = __fmul_rn(2.f * qv.w, __fadd_rn(rinv.h, rinv.l));
             const float gx = __fmul_rn(sc, tx), gy = __fmul_rn(sc, ty), gz3 = __fmul_rn(sc, tz);
             const int jj = __ldg(a.orig + (e & kIdxMask));
-            atomicAdd(a.dw + jj, (double)__fmul_rn(2.f, __fadd_rn(F.h, F.l)));
-            atomicAdd(a.dpos + 3 * (int64_t)jj, (double)gx);
-            atomicAdd(a.dpos + 3 * (int64_t)jj + 1, (double)gy);
-            atomicAdd(a.dpos + 3 * (int64_t)jj + 2, (double)gz3);
+            atomicAdd(a.dw + jj, f2d_exact(__fmul_rn(2.f, __fadd_rn(F.h, F.l))));
+            atomicAdd(a.dpos + 3 * (int64_t)jj, f2d_exact(gx));
+            atomicAdd(a.dpos + 3 * (int64_t)jj + 1, f2d_exact(gy));
+            atomicAdd(a.dpos + 3 * (int64_t)jj + 2, f2d_exact(gz3));
             df_acc(pix, {gx, 0.f});
             df_acc(piy, {gy, 0.f});
             df_acc(piz, {gz3, 0.f});
