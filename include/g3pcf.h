@@ -201,8 +201,9 @@ int g3pcf_status(g3pcf_plan_t plan);
  * [8] kernels launched by the call, [9] candidate secondaries visited
  * (pair-list path; 0 for the fused kernel), [10] passes of the pair lists,
  * [11] and [12] summed device times (ms) of the list scan and accumulate
- * kernels, [13] accumulate launches.  Synchronises the stream.
- * At most min(nvals, 14) values are written. */
+ * kernels, [13] accumulate launches, [14] 1 when the pair stage wrote the
+ * tensor-core operands (G3PCF_OPT_TC_OPERANDS), else 0.  Synchronises the stream.
+ * At most min(nvals, 15) values are written. */
 int g3pcf_stats(g3pcf_plan_t plan, double* vals, int nvals);
 
 /* zeta from multipoles the caller already holds, without allocating any
@@ -299,7 +300,7 @@ int g3pcf_fp32_peak(double* tflops, void* stream);
  *   G3PCF_OPT_GRAD_PRECISION  arithmetic of the pair stage for multipoles that are
  *                             differentiated (forwards with G3PCF_F_KEEP_ALM, the
  *                             backward and its recomputation): 0 = double-float
- *                             (FP32 head + tail; V = M A in FP64), gradients within
+ *                             (FP32 head + tail, V = M A too), gradients within
  *                             1e-7 of the FP64 reference; 1 = FP32, about 1e-6
  *                             (faster).  Plain forwards always use FP32; the fused
  *                             kernel (G3PCF_OPT_PAIR_KERNELS = 1) is FP32 only
@@ -317,6 +318,16 @@ int g3pcf_fp32_peak(double* tflops, void* stream);
  *                             the kernel then flags G3PCF_ERR_TIMEOUT, waits (bounded)
  *                             for its own copies, frees its tensor memory and
  *                             returns; 0 = off
+ *   G3PCF_OPT_TC_OPERANDS     operands of the tensor-core contraction: 0 = formed
+ *                             inside the contraction kernel from the FP32 rows of A;
+ *                             1 = written by the pair stage as bf16 hi / lo rows of
+ *                             sqrt(w) A, so that the contraction only copies and
+ *                             multiplies (used when no weight is negative, the
+ *                             forward is one pass of the pair lists in the Chebyshev
+ *                             basis outside a captured graph and they fit in memory;
+ *                             otherwise as 0).  Both give bit-identical results; 1
+ *                             shortens the contraction and lengthens the accumulate
+ *                             kernel (on the 2M-point workload by 1.6 and 3.7 ms).
  * Returns G3PCF_ERR_ARG for unknown options or values out of range. */
 enum {
     G3PCF_OPT_CHUNK_ROWS = 1,
@@ -328,7 +339,8 @@ enum {
     G3PCF_OPT_X_REFINE = 8,
     G3PCF_OPT_GRAD_PRECISION = 9,
     G3PCF_OPT_TEST_FAIL_ALLOC = 10,
-    G3PCF_OPT_TEST_TC_TIMEOUT = 11
+    G3PCF_OPT_TEST_TC_TIMEOUT = 11,
+    G3PCF_OPT_TC_OPERANDS = 12
 };
 int g3pcf_set_option(g3pcf_plan_t plan, int option, int64_t value);
 

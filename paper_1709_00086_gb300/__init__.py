@@ -26,6 +26,7 @@ OPT_BASIS = 7
 OPT_X_REFINE = 8
 OPT_GRAD_PRECISION = 9
 OPT_TEST_FAIL_ALLOC, OPT_TEST_TC_TIMEOUT = 10, 11
+OPT_TC_OPERANDS = 12
 F_POS_F64, F_CONTRACT_FP32, F_NO_SYNC, F_KEEP_ALM, F_GRAPH = 1, 2, 4, 8, 16
 ERRORS = {0: "OK", -1: "ERR_ARG", -2: "ERR_RANGE", -3: "ERR_RMAX", -4: "ERR_ALLOC",
           -5: "ERR_CUDA", -6: "ERR_TIMEOUT", -7: "ERR_STATE", -8: "ERR_UNSUPPORTED"}
@@ -291,18 +292,18 @@ class Plan:
 
     def set_option(self, option: int, value: int):
         """Tuning knob (OPT_CHUNK_ROWS, OPT_CELLS_PER_RMAX, OPT_KFLUSH, OPT_PAIR_KERNELS,
-        OPT_LIST_BYTES, OPT_BASIS, OPT_X_REFINE, OPT_GRAD_PRECISION; 0 = automatic)."""
+        OPT_LIST_BYTES, OPT_BASIS, OPT_X_REFINE, OPT_GRAD_PRECISION, OPT_TC_OPERANDS; 0 = automatic)."""
         _check(lib().g3pcf_set_option(self._h, int(option), int(value)))
 
     def status(self):
         _check(lib().g3pcf_status(self._h))
 
     def stats(self) -> dict:
-        v = np.zeros(14)
-        _check(lib().g3pcf_stats(self._h, v.ctypes.data_as(ctypes.c_void_p), 14))
+        v = np.zeros(15)
+        _check(lib().g3pcf_stats(self._h, v.ctypes.data_as(ctypes.c_void_p), 15))
         keys = ["index_ms", "pair_ms", "contract_ms", "reduce_ms", "total_ms", "pairs", "primaries",
                 "cells_per_rmax", "launches", "candidates", "list_passes", "scan_ms", "accum_ms",
-                "accum_launches"]
+                "accum_launches", "tc_operands_from_pairs"]
         return dict(zip(keys, v.tolist()))
 
 

@@ -99,6 +99,10 @@ struct g3pcf_plan_s {
     std::vector<Tile> tiles;      // FP32 contraction tiles (edge T)
     std::vector<Tile> tiles_tc;   // tensor-core contraction tiles (edge T_tc)
     std::vector<TcStrip> strips_tc;  // their strips (one or two tiles of a row panel)
+    std::vector<int4> bblk;          // per m block: {first A column, width, first bf16 operand column, 0}
+    int RLPb = 0;                    // bf16 operand row pitch
+    int opt_tc_operands = 0;         // 0: operands formed in the contraction; 1: written by the pair stage when possible
+    bool direct_used = false;        // this forward's pair stage wrote the bf16 operands
     int T = 0, T_tc = 0;
     int kflush = 16;
     // device buffers
@@ -107,6 +111,7 @@ struct g3pcf_plan_s {
     DevBuf counts, A, partials, d_tiles, d_segs, d_segfirst, d_colmap, d_colscale, d_catoff;
     DevBuf d_colconv, d_colcoef, d_bintab_s, d_slotconv, d_slotcoef, d_monoexp, d_monoconv, d_monoidx, d_monocoef;
     DevBuf d_ranges, d_tiles_tc, d_cats, d_mreal, d_V, d_bintab, wrow, d_vblk, d_strips_tc, d_items;
+    DevBuf d_bop, d_bblk, d_bcat;
     DevBuf d_slotcoefdf, d_mrealdf, d_Vdf, d_colcoefdf;
     int64_t opt_chunk = 0;   // G3PCF_OPT_CHUNK_ROWS
     // pinned staging for host -> device tables (capturable copies); offset
@@ -164,7 +169,7 @@ struct g3pcf_plan_s {
     int last_pos_f64 = 0;
     Grid last_grid{};
     unsigned* key_sorted = nullptr;
-    double stats[14] = {};
+    double stats[15] = {};
     int launches = 0;
 };
 
@@ -236,6 +241,11 @@ int upload_consts(g3pcf_plan_t P) {
         return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (constants)");
     CK(cudaMemcpy(P->d_tiles_tc.p, P->tiles_tc.data(), P->tiles_tc.size() * sizeof(Tile),
                   cudaMemcpyHostToDevice));
+    if (!P->bblk.empty()) {
+        if (P->d_bblk.ensure(P->bblk.size() * sizeof(int4)))
+            return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (constants)");
+        CK(cudaMemcpy(P->d_bblk.p, P->bblk.data(), P->bblk.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    }
     if (P->d_strips_tc.ensure(P->strips_tc.size() * sizeof(TcStrip)))
         return fail(G3PCF_ERR_ALLOC, "workspace allocation failed (constants)");
     CK(cudaMemcpy(P->d_strips_tc.p, P->strips_tc.data(), P->strips_tc.size() * sizeof(TcStrip),
@@ -667,6 +677,15 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode
     la.qa = qa;
     la.qb = qb;
     la.ncand = reinterpret_cast<unsigned long long*>(pa.status + 24);  // zeroed with the status word
+    la.bop = nullptr;
+    if (mode == 0 && pa.bop && !la.precise && P->opt_basis == 0 && !P->capturing) {
+        la.bop = pa.bop;
+        la.nbcat = pa.nbcat;
+        la.bop_pitch = pa.bop_pitch;
+        la.bblk = pa.bblk;
+        la.nblk = pa.nblk;
+        la.bcat = pa.bcat;
+    }
     if (P->capturing) {
         // no host round trip inside a graph: plan the passes on the device from
         // the pool the warm-up run sized (sizes of that run, same A-chunk order)
@@ -719,8 +738,14 @@ int run_pair_lists(g3pcf_plan_t P, const PairArgs& pa, cudaStream_t st, int mode
         return fail(G3PCF_ERR_CUDA, "pair count launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     CK(cudaMemcpyAsync(P->h_need, la.need + qa, 4 * nq, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(P->h_status + 8, la.ncand, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(P->h_status + 12, pa.status + kNegWeightSlot, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     P->stats[9] = (double)*reinterpret_cast<unsigned long long*>(P->h_status + 8);
+    // the bf16 operands are sqrt(w) A: with a negative weight the contraction
+    // forms its operands from the FP32 rows instead
+    if (la.bop && P->h_status[12] != 0) la.bop = nullptr;
+    la.skip_a = (la.bop && !P->exact_alm) ? 1 : 0;
+    if (mode == 0) P->direct_used = la.bop != nullptr;
     // pool capacity (per chunk: 128 bytes of entries, a tag and a list int)
     int64_t total = 0, most = 0;
     for (int64_t k = 0; k < nq; ++k) {
@@ -937,21 +962,28 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
         const int KB = contract_tc_kblock();
         const int64_t rows_all = (c.ncat > 1) ? n : c.n_primary;
         int64_t C = rows_all;
-        if (c.ncat == 1) {
-            if (P->opt_chunk > 0) {
-                C = P->opt_chunk;
-            } else if (P->capturing && P->fixed_chunk > 0) {
-                C = P->fixed_chunk;
-            } else {
-                size_t fr = 0, tot = 0;
-                CK(cudaMemGetInfo(&fr, &tot));
-                double budget = 0.4 * (double)fr;
-                if (budget > 48e9) budget = 48e9;
-                const double per_row = 4.0 * P->RLP + 4.0;
-                C = (int64_t)(budget / per_row) / KB * KB;
-                if (C < KB) C = KB;
+        // the bf16 tensor-core operands (4 bytes per operand column and row) are
+        // written by the pair stage only when they fit beside A in the budget
+        bool ops_fit = false;
+        const bool ops = use_tc && P->opt_tc_operands == 1 && P->opt_pair != 1 && P->opt_basis == 0 && !P->capturing;
+        {
+            size_t fr = 0, tot = 0;
+            CK(cudaMemGetInfo(&fr, &tot));
+            double budget = 0.4 * (double)fr;
+            if (budget > 48e9) budget = 48e9;
+            const double per_row = 4.0 * P->RLP + 4.0;
+            ops_fit = ops && budget / (per_row + 4.0 * P->RLPb) >= (double)(rows_all + 64 * c.ncat);
+            if (c.ncat == 1) {
+                if (P->opt_chunk > 0) {
+                    C = P->opt_chunk;
+                } else if (P->capturing && P->fixed_chunk > 0) {
+                    C = P->fixed_chunk;
+                } else {
+                    C = (int64_t)(budget / per_row) / KB * KB;
+                    if (C < KB) C = KB;
+                }
+                if (C > rows_all) C = rows_all;
             }
-            if (C > rows_all) C = rows_all;
         }
         const bool chunked = (c.ncat == 1) && C < rows_all;
         P->fixed_chunk = C;
@@ -1044,6 +1076,23 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
                 P->cev.push_back(e);
             }
         const bool chunk_events = (int64_t)P->cev.size() >= 2 * nchunks;
+        // bf16 tensor-core operands written by the pair stage (one pass of the
+        // multipoles, list path, Chebyshev basis, outside a capture): rows in the
+        // padded catalog coordinates of the contraction, padding rows zeroed
+        P->direct_used = false;
+        __nv_bfloat16* bop = nullptr;
+        int64_t bop_elems = 0;
+        if (ops_fit && !chunked && nprim > 0 && !ccats.empty() && cpad[0] > 0) {
+            bop_elems = cpad[0] * 2 * (int64_t)P->RLPb;  // hi and lo of every padded row
+            if (ensure(P, P->d_bop, sizeof(__nv_bfloat16) * (size_t)bop_elems, "tensor-core operands") ||
+                ensure(P, P->d_bcat, sizeof(int4) * (ccats[0].size() / 4), "tensor-core operands"))
+                return G3PCF_ERR_ALLOC;
+            bop = P->d_bop.as<__nv_bfloat16>();
+            UP(P->d_bcat.p, ccats[0].data(), 4 * ccats[0].size());
+            P->launches += 1;
+            if (launch_zero_pad(bop, P->RLPb, P->d_bcat.as<int4>(), (int)(ccats[0].size() / 4), st) != 0)
+                return fail(G3PCF_ERR_CUDA, "operand padding launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        }
         int seg_base = 0;
         for (int64_t ch = 0; ch < nchunks; ++ch) {
             const int64_t q0 = ch * C, q1 = chunked ? std::min(rows_all, q0 + C) : nprim;
@@ -1074,6 +1123,12 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
                 pa.bins = P->bins;
                 pa.bintab = P->d_bintab.as<unsigned char>();
                 pa.bin_tscale = P->bin_tscale;
+                pa.bop = bop;
+                pa.nbcat = (int)(ccats.empty() ? 0 : ccats[0].size() / 4);
+                pa.bop_pitch = P->RLPb;
+                pa.bblk = P->d_bblk.as<int4>();
+                pa.nblk = (int)P->bblk.size();
+                pa.bcat = P->d_bcat.as<int4>();
                 const bool use_list = P->opt_pair != 1;
                 if (use_list) {
                     if (int r = run_pair_lists(P, pa, st)) return r;
@@ -1114,12 +1169,17 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
                     // the rows of A written by this pass: the map reads zeros past them, so
                     // the padding primaries of the last k-block never meet stale memory
                     const int64_t rows_written = chunked ? q1 - q0 : rows_all;
-                    const int rc = launch_contract_tc(P->A.as<float>(), P->RLP, P->RL, rows_written, P->wrow.as<float>(),
-                                                      P->d_cats.as<int4>(), d_tl, P->d_strips_tc.as<TcStrip>(),
-                                                      P->d_items.as<TcItem>(), (int)items.size(),
-                                                      P->d_segs.as<Segment>(), part, part_stride,
-                                                      d_status + kNegWeightSlot, d_status, st,
-                                                      P->test_tc_timeout);
+                    const int rc =
+                        P->direct_used
+                            ? launch_contract_tc_op(bop, P->RLPb, cpad[ch], d_tl,
+                                                    P->d_strips_tc.as<TcStrip>(), P->d_items.as<TcItem>(),
+                                                    (int)items.size(), P->d_segs.as<Segment>(), part, part_stride,
+                                                    d_status, st, P->test_tc_timeout)
+                            : launch_contract_tc(P->A.as<float>(), P->RLP, P->RL, rows_written, P->wrow.as<float>(),
+                                                 P->d_cats.as<int4>(), d_tl, P->d_strips_tc.as<TcStrip>(),
+                                                 P->d_items.as<TcItem>(), (int)items.size(), P->d_segs.as<Segment>(),
+                                                 part, part_stride, d_status + kNegWeightSlot, d_status, st,
+                                                 P->test_tc_timeout);
                     if (rc == -2) return fail(G3PCF_ERR_CUDA, "cuTensorMapEncodeTiled unavailable or failed");
                     if (rc != 0)
                         return fail(G3PCF_ERR_CUDA, "tensor-core contraction launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -1315,6 +1375,12 @@ int g3pcf_plan(g3pcf_plan_t* out, int nbins, double rmin, double rmax, int lmax,
     P->strips_tc.resize(nt);
     const int nstrip = make_strips(P->tiles_tc.data(), nt, P->strips_tc.data(), nt);
     P->strips_tc.resize(nstrip > 0 ? nstrip : 0);
+    P->bblk.assign(lmax + 1, int4{0, 0, 0, 0});
+    P->RLPb = tc_operand_blocks(P->tiles_tc.data(), nt, P->bblk.data(), lmax + 1);
+    if (P->RLPb < 0) {
+        delete P;
+        return fail(G3PCF_ERR_ARG, "operand blocks out of range");
+    }
     *out = P;
     return G3PCF_OK;
 }
@@ -1593,6 +1659,10 @@ int g3pcf_set_option(g3pcf_plan_t P, int option, int64_t value) {
             if (value < 0 || value > 1) return fail(G3PCF_ERR_ARG, "tensor-core timeout test must be 0 or 1");
             P->test_tc_timeout = (int)value;
             return G3PCF_OK;
+        case G3PCF_OPT_TC_OPERANDS:
+            if (value < 0 || value > 1) return fail(G3PCF_ERR_ARG, "tensor-core operands must be 0 or 1");
+            P->opt_tc_operands = (int)value;
+            return G3PCF_OK;
         case G3PCF_OPT_GRAD_PRECISION:
             if (value < 0 || value > 1) return fail(G3PCF_ERR_ARG, "gradient precision must be 0 or 1");
             P->opt_grad = (int)value;
@@ -1831,7 +1901,8 @@ int g3pcf_stats(g3pcf_plan_t P, double* vals, int nvals) {
     P->stats[11] = scan_ms;
     P->stats[12] = accum_ms;
     P->stats[13] = (double)(P->lev_used / 4);
-    for (int k = 0; k < nvals && k < 14; ++k) vals[k] = P->stats[k];
+    P->stats[14] = P->direct_used ? 1.0 : 0.0;
+    for (int k = 0; k < nvals && k < 15; ++k) vals[k] = P->stats[k];
     return G3PCF_OK;
 }
 

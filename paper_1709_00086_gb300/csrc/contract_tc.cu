@@ -228,6 +228,74 @@ __device__ __forceinline__ bool mbar_wait_or_abort(unsigned bar, unsigned parity
     return false;
 }
 
+// Drain warps of a work item: TMEM lane (= output row) 32 (warp % 4) + lane;
+// column c of the accumulator is column c % 128 of the strip's tile c / 128;
+// warp w takes the 32-column groups g with g % 2 == w / 4.  Each finished run
+// (ready barrier) is added to the item's FP64 partials, then the TMEM buffer is
+// released (drained barrier); the item's other segment slots are zeroed.
+__device__ __forceinline__ void drain_item(int warp, int lane, unsigned tmem, int N, int Np, int nt, int nsub,
+                                           unsigned ready0, unsigned drained0, volatile int* abort_flag,
+                                           const Tile* tiles, const TcStrip& sp, const TcItem& it, double* partials,
+                                           int part_stride, int* status) {
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = quarter * 32 + lane;
+    const unsigned long long keep = l2_keep_policy();
+    double* outs = partials + (int64_t)it.vseg0 * part_stride;
+    for (int sub = 0; sub < nsub; ++sub) {
+        const int buf = sub & 1;
+        const bool ok = mbar_wait(ready0 + 8 * buf, (sub >> 1) & 1);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!ok || *abort_flag) {
+            if (lane == 0) atomicOr(status, kStatusTimeout);
+            break;
+        }
+        // the partial is column-major (a warp's rows of one column are one
+        // 256-byte line); a run after the first adds to it, reading a batch
+        // of kDrainBatch columns before writing them, so that the batch's
+        // loads are in flight together
+#pragma unroll 1
+        for (int c0 = 32 * half; c0 < N; c0 += 64) {
+            unsigned rr[32];
+            tmem_ld32(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)(buf * Np + c0), rr);
+            const Tile t = tiles[sp.tile0 + c0 / kTT];
+            const int cc = c0 % kTT;
+            const int ncol = t.cols - cc;  // valid columns from cc (the tile's width)
+            double* out = outs + t.out_off + (int64_t)cc * kTT + row;
+            if (row < t.rows) {
+                if (sub == 0) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (j < ncol) st_keep(out + (int64_t)j * kTT, (double)__uint_as_float(rr[j]), keep);
+                } else {
+#pragma unroll
+                    for (int h = 0; h < 32; h += kDrainBatch) {
+                        double old[kDrainBatch];
+#pragma unroll
+                        for (int j = 0; j < kDrainBatch; ++j)
+                            old[j] = (h + j < ncol) ? ld_keep(out + (int64_t)(h + j) * kTT, keep) : 0.0;
+#pragma unroll
+                        for (int j = 0; j < kDrainBatch; ++j)
+                            if (h + j < ncol)
+                                st_keep(out + (int64_t)(h + j) * kTT, old[j] + (double)__uint_as_float(rr[h + j]), keep);
+                    }
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(drained0 + 8 * buf) : "memory");
+    }
+    // an empty range writes zeros; the item's later virtual segments are zeroed
+    // (their primaries are in the first slot's sum)
+    for (int p = 0; p < nt; ++p) {
+        const Tile t = tiles[sp.tile0 + p];
+        for (int v = (nsub == 0 ? 0 : 1); v < it.nvseg; ++v) {
+            double* out = partials + (int64_t)(it.vseg0 + v) * part_stride + t.out_off;
+            for (int c = half; c < kTT; c += 2) out[(int64_t)c * kTT + row] = 0.0;
+        }
+    }
+}
+
 // One CTA = one work item (strip, virtual segments).  The k-blocks are
 // accumulated in runs of kSubKB into one of two TMEM buffers (columns [0, Np)
 // and [Np, 2 Np)); while the MMA warp fills one buffer the drain warps add the
@@ -524,73 +592,212 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
             }
         }
     } else {
-        // drain warps: TMEM lane (= output row) 32 (warp % 4) + lane; column c of
-        // the accumulator is column c % 128 of the strip's tile c / 128; warp w
-        // takes the 32-column groups g with g % 2 == w / 4
-        const int quarter = warp & 3, half = warp >> 2;
-        const int row = quarter * 32 + lane;
-        const unsigned long long keep = l2_keep_policy();
-        double* outs = a.partials + (int64_t)it.vseg0 * a.part_stride;
-        for (int sub = 0; sub < nsub; ++sub) {
-            const int buf = sub & 1;
-            const bool ok = mbar_wait(ready0 + 8 * buf, (sub >> 1) & 1);
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (!ok || abort_flag) {
-                if (lane == 0) atomicOr(a.status, kStatusTimeout);
-                break;
-            }
-            // the partial is column-major (a warp's rows of one column are one
-            // 256-byte line); a run after the first adds to it, reading a batch
-            // of kDrainBatch columns before writing them, so that the batch's
-            // loads are in flight together
-#pragma unroll 1
-            for (int c0 = 32 * half; c0 < N; c0 += 64) {
-                unsigned rr[32];
-                tmem_ld32(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)(buf * Np + c0), rr);
-                const Tile t = a.tiles[sp.tile0 + c0 / kTT];
-                const int cc = c0 % kTT;
-                const int ncol = t.cols - cc;  // valid columns from cc (the tile's width)
-                double* out = outs + t.out_off + (int64_t)cc * kTT + row;
-                if (row < t.rows) {
-                    if (sub == 0) {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (j < ncol) st_keep(out + (int64_t)j * kTT, (double)__uint_as_float(rr[j]), keep);
-                    } else {
-#pragma unroll
-                        for (int h = 0; h < 32; h += kDrainBatch) {
-                            double old[kDrainBatch];
-#pragma unroll
-                            for (int j = 0; j < kDrainBatch; ++j)
-                                old[j] = (h + j < ncol) ? ld_keep(out + (int64_t)(h + j) * kTT, keep) : 0.0;
-#pragma unroll
-                            for (int j = 0; j < kDrainBatch; ++j)
-                                if (h + j < ncol)
-                                    st_keep(out + (int64_t)(h + j) * kTT, old[j] + (double)__uint_as_float(rr[h + j]),
-                                            keep);
-                        }
-                    }
-                }
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(drained0 + 8 * buf) : "memory");
-        }
-        // an empty range writes zeros; the second virtual segment of a one-tile
-        // strip's item is zeroed (its primaries are in the first slot's sum)
-        for (int p = 0; p < nt; ++p) {
-            const Tile t = a.tiles[sp.tile0 + p];
-            for (int v = (nsub == 0 ? 0 : 1); v < it.nvseg; ++v) {
-                double* out = a.partials + (int64_t)(it.vseg0 + v) * a.part_stride + t.out_off;
-                for (int c = half; c < kTT; c += 2) out[(int64_t)c * kTT + row] = 0.0;
-            }
-        }
+        drain_item(warp, lane, tmem, N, Np, nt, nsub, ready0, drained0, &abort_flag, a.tiles, sp, it, a.partials,
+                   a.part_stride, a.status);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * Np)
                      : "memory");
+}
+
+// ---- the same contraction from bf16 operand rows written by k_accum ----------
+// On request (G3PCF_OPT_TC_OPERANDS = 1) and when no weight is negative, k_accum
+// writes sqrt(w) A split into bf16 hi and lo rows (the same operations as the
+// converter warps, so the operands and the result are bit-identical), each m
+// block from a multiple of 64 columns, a row's hi and lo side by side.  The
+// operands are then MN-major in the 128-byte swizzle: one 2-D copy of 64 operand
+// columns x 64 primaries lands as eight groups of 8 primaries x 128 bytes, the
+// descriptors step 8 KB between 64-column boxes (leading byte offset) and 1 KB
+// between 8-primary groups (stride byte offset), and an MMA k-step of 16
+// primaries advances 2 KB.  No staging, no conversion: warp 9 copies the boxes
+// the MMAs use into a ring of operand stages, warp 8 issues the MMAs, warps 0-7
+// drain as in k_contract_tc.
+constexpr int kOpMmaWarp = kDrainWarps;      // warp 8
+constexpr int kOpTmaWarp = kDrainWarps + 1;  // warp 9
+constexpr int kOpWarps = kDrainWarps + 2;
+constexpr int kOpBox = 64 * kKB * 2;         // one box: 64 columns x 64 primaries of bf16 = 8 KB
+constexpr int kOpMaxStages = 8;
+
+__device__ __forceinline__ unsigned long long make_desc_mn(unsigned saddr) {
+    unsigned long long d = 0;
+    d |= (unsigned long long)((saddr & 0x3FFFF) >> 4);
+    d |= (unsigned long long)(kOpBox >> 4) << 16;  // leading byte offset: the next 64 columns
+    d |= (unsigned long long)(1024 >> 4) << 32;    // stride byte offset: the next 8 primaries
+    d |= (unsigned long long)1 << 46;
+    d |= (unsigned long long)2 << 61;
+    return d;
+}
+// as make_idesc, with both operands MN-major (bits 15 and 16)
+__host__ __device__ constexpr unsigned make_idesc_mn(int M, int N) {
+    return make_idesc(M, N) | (1u << 15) | (1u << 16);
+}
+
+struct TcOpMaps {
+    CUtensorMap hi, lo;
+};
+struct TcOpArgs {
+    const Tile* tiles;
+    const TcStrip* strips;
+    const TcItem* items;
+    const Segment* segs;  // padded primary coordinates = operand rows
+    double* partials;
+    int part_stride;
+    int* status;
+    int test_timeout;
+};
+
+__global__ void __launch_bounds__(kOpWarps * 32, 1)
+    k_contract_tc_op(const __grid_constant__ TcOpMaps maps, TcOpArgs a) {
+    extern __shared__ __align__(1024) unsigned char op_smem_raw[];
+    __shared__ __align__(8) unsigned long long bars[2 * kOpMaxStages + 4];
+    __shared__ unsigned tmem_slot;
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const TcItem it = a.items[blockIdx.x];
+    const TcStrip sp = a.strips[it.strip];
+    const int row0 = a.segs[it.vseg0].row0, row1 = a.segs[it.vseg0 + it.nvseg - 1].row1;
+    const int kb0 = row0 / kKB;
+    const int nkb = (row1 - row0 + kKB - 1) / kKB;
+    const int nsub = (nkb + kSubKB - 1) / kSubKB;
+    const int nt = sp.ntile, N = sp.n, Np = kTT * nt;
+    const int rowsL = a.tiles[sp.tile0].rows;
+    const unsigned raw = smem_u32(op_smem_raw);
+    const unsigned sbase = (raw + 1023u) & ~1023u;
+    // stage: panel b's hi boxes from b * 16 KB, its lo boxes from (nt + b) * 16 KB
+    const unsigned stage_bytes = (unsigned)(2 * nt) * kOpBytes;
+    int O = (int)(kBufBytes / stage_bytes);
+    O = O < kOpMaxStages ? O : kOpMaxStages;
+    // boxes of panel b that the MMAs read: B's N columns; panel 0 is also A,
+    // whose rows past the row panel's valid rows only feed discarded rows of D
+    auto nbox = [&](int b) {
+        const int needB = min(kTT, N - kTT * b);
+        const int need = b == 0 ? max(needB, rowsL) : needB;
+        return (need + 63) / 64;
+    };
+    unsigned kb_bytes = 0;
+    for (int b = 0; b < nt; ++b) kb_bytes += (unsigned)(2 * nbox(b) * kOpBox);
+    const unsigned full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[kOpMaxStages]);
+    const unsigned ready0 = smem_u32(&bars[2 * kOpMaxStages]);
+    const unsigned drained0 = ready0 + 16;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kOpMaxStages; ++s) {
+            mbar_init(full0 + 8 * s, 1);   // the copying thread's arrival and the bytes
+            mbar_init(empty0 + 8 * s, 1);  // the MMA thread's commit
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(ready0 + 8 * b, 1);
+            mbar_init(drained0 + 8 * b, kDrainWarps);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_slot)),
+                     "r"(2 * Np)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tmem_slot;
+
+    if (warp == kOpTmaWarp) {
+        if (lane == 0 && nkb > 0) {
+            int issued = 0;
+            bool ok = true;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int o = kb % O;
+                if (kb >= O && !mbar_wait_or_abort(empty0 + 8 * o, ((kb / O) - 1) & 1, &abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                const unsigned st = sbase + o * stage_bytes;
+                const int y = (kb0 + kb) * kKB;  // operand row of the k-block's first primary
+                mbar_expect_tx(full0 + 8 * o, kb_bytes);
+                for (int b = 0; b < nt; ++b)
+                    for (int c = 0; c < nbox(b); ++c) {
+                        const int x = sp.xb + kTT * b + 64 * c;  // a multiple of 64 columns
+                        tma_load_2d(st + b * kOpBytes + c * kOpBox, &maps.hi, x, y, full0 + 8 * o);
+                        tma_load_2d(st + (nt + b) * kOpBytes + c * kOpBox, &maps.lo, x, y, full0 + 8 * o);
+                    }
+                ++issued;
+            }
+            if (!ok && !abort_flag) {
+                abort_flag = 1;
+                atomicOr(a.status, kStatusTimeout);
+            }
+            if (abort_flag) {
+                // this CTA's copies still in flight (the latest of every stage) land
+                // before it exits (bounded)
+                for (int kb = issued > O ? issued - O : 0; kb < issued; ++kb)
+                    mbar_wait(full0 + 8 * (kb % O), (kb / O) & 1);
+            }
+        }
+    } else if (warp == kOpMmaWarp) {
+        if (lane == 0 && nkb > 0) {
+            const unsigned idesc = make_idesc_mn(kTT, N);
+            bool ok = true;
+            for (int kb = 0; kb < nkb && ok; ++kb) {
+                const int sub = kb / kSubKB, buf = sub & 1;
+                const bool first = (kb % kSubKB) == 0;
+                const bool last = (kb % kSubKB) == kSubKB - 1 || kb == nkb - 1;
+                if (first && sub >= 2 && !mbar_wait(drained0 + 8 * buf, ((sub >> 1) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                const int o = kb % O;
+                // error-path test: the first wait gives up at once, as if its bound had expired
+                const bool landed = (kb == 0 && a.test_timeout)
+                                        ? false
+                                        : mbar_wait_or_abort(full0 + 8 * o, (kb / O) & 1, &abort_flag);
+                if (!landed) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned st = sbase + o * stage_bytes;
+                const unsigned H = st, Lo = st + nt * kOpBytes;  // hi and lo (A = their panel 0)
+                const unsigned d = tmem + (unsigned)(buf * Np);
+#pragma unroll
+                for (int k = 0; k < kKB / 16; ++k) {
+                    const unsigned off = k * 2048;  // 16 primaries = two groups of 8
+                    mma_bf16(d, make_desc_mn(H + off), make_desc_mn(H + off), idesc, (first && k == 0) ? 0u : 1u);
+                    mma_bf16(d, make_desc_mn(H + off), make_desc_mn(Lo + off), idesc, 1u);
+                    mma_bf16(d, make_desc_mn(Lo + off), make_desc_mn(H + off), idesc, 1u);
+                }
+                mma_commit(empty0 + 8 * o);  // frees the stage when these MMAs have read it
+                if (last) mma_commit(ready0 + 8 * buf);
+            }
+            if (!ok) {
+                if (!abort_flag) {
+                    abort_flag = 1;
+                    atomicOr(a.status, kStatusTimeout);
+                }
+                mma_commit(ready0);
+                mma_commit(ready0 + 8);
+            }
+        }
+    } else if (warp < kDrainWarps) {
+        drain_item(warp, lane, tmem, N, Np, nt, nsub, ready0, drained0, &abort_flag, a.tiles, sp, it, a.partials,
+                   a.part_stride, a.status);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * Np)
+                     : "memory");
+}
+
+__global__ void k_zero_pad(__nv_bfloat16* bop, int pitch, const int4* bcat) {
+    const int4 c = bcat[blockIdx.x];
+    const int64_t r0 = (int64_t)c.x + c.z, r1 = (int64_t)c.x + (int64_t)(c.z + kKB - 1) / kKB * kKB;
+    const int64_t n = (r1 - r0) * 2 * pitch;  // hi and lo of every padding row
+    unsigned short* h = reinterpret_cast<unsigned short*>(bop) + r0 * 2 * pitch;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) h[i] = 0;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -621,6 +828,22 @@ int make_map_a(CUtensorMap* m, const float* A, int RLP, int RL, int64_t rows, in
     return r == CUDA_SUCCESS ? 0 : -1;
 }
 
+// bf16 operand rows as a 2-D tensor: pitch columns (inner) x rows, rows 2 pitch
+// apart (hi and lo of a row side by side); boxes of 64 columns x kKB rows in the
+// 128-byte swizzle, zeros outside.
+int make_map_op(CUtensorMap* m, const __nv_bfloat16* B, int pitch, int64_t rows) {
+    auto fn = encode_fn();
+    if (!fn) return -1;
+    cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)(rows > 0 ? rows : 1)};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch * 4};
+    cuuint32_t box[2] = {64, kKB};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(B), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : -1;
+}
+
 }  // namespace
 
 int contract_tile_dim_tc() { return kTT; }
@@ -629,7 +852,13 @@ int contract_tile_dim_tc() { return kTT; }
 // tiles from the diagonal): consecutive tiles of one row panel, two at a time.
 int make_strips(const Tile* tiles, int ntiles, TcStrip* out, int max_strips) {
     int n = 0;
+    int bm = -1, b0 = 0, bnext = 0;  // operand column of the current m block, and of the next
     for (int k = 0; k < ntiles;) {
+        if (tiles[k].m != bm) {
+            bm = tiles[k].m;
+            b0 = bnext;
+            bnext = b0 + (tiles[k].width + 63) / 64 * 64;
+        }
         const bool pair = k + 1 < ntiles && tiles[k + 1].m == tiles[k].m && tiles[k + 1].r0 == tiles[k].r0 &&
                           tiles[k + 1].c0 == tiles[k].c0 + kTT;
         if (n >= max_strips) return -1;
@@ -639,6 +868,7 @@ int make_strips(const Tile* tiles, int ntiles, TcStrip* out, int max_strips) {
         out[n].n = (cols + 15) / 16 * 16;  // kind::f16 with M = 128: N a multiple of 16, <= 256
         out[n].xrow = tiles[k].col0 + tiles[k].r0;
         out[n].xcol = tiles[k].col0 + tiles[k].c0;
+        out[n].xb = b0 + tiles[k].c0;
         ++n;
         k += pair ? 2 : 1;
     }
@@ -646,6 +876,20 @@ int make_strips(const Tile* tiles, int ntiles, TcStrip* out, int max_strips) {
 }
 
 int contract_tc_kblock() { return kKB; }
+
+int tc_operand_blocks(const Tile* tiles, int ntiles, int4* blk, int max_blk) {
+    int bm = -1, nb = 0, bnext = 0;
+    for (int k = 0; k < ntiles; ++k) {
+        if (tiles[k].m == bm) continue;
+        bm = tiles[k].m;
+        if (bm >= max_blk) return -1;
+        blk[bm] = make_int4(tiles[k].col0, tiles[k].width, bnext, 0);
+        bnext += (tiles[k].width + 63) / 64 * 64;
+        nb = bm + 1;
+    }
+    (void)nb;
+    return bnext;
+}
 
 // Every CTA takes the same number of k-blocks: a strip's k-block costs about
 // the same whatever its width (the per-k-block copies and hand-offs bound it),
@@ -678,6 +922,27 @@ int launch_contract_tc(const float* A, int RLP, int RL, int64_t arows, const flo
         return -1;
     TcArgs a{A, RLP, wrow, cats, tiles, strips, items, segs, partials, part_stride, negw, status, test_timeout};
     k_contract_tc<<<(unsigned)nitems, kTcWarps * 32, smem, st>>>(m, a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_contract_tc_op(const __nv_bfloat16* bop, int pitch, int64_t rows, const Tile* tiles,
+                          const TcStrip* strips, const TcItem* items, int nitems, const Segment* segs,
+                          double* partials, int part_stride, int* status, cudaStream_t st, int test_timeout) {
+    if (nitems <= 0) return 0;
+    if (pitch % 64 != 0) return -1;
+    TcOpMaps m;
+    if (make_map_op(&m.hi, bop, pitch, rows) != 0 || make_map_op(&m.lo, bop + pitch, pitch, rows) != 0) return -2;
+    const int smem = kBufBytes + 1024;
+    if (cudaFuncSetAttribute(k_contract_tc_op, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return -1;
+    TcOpArgs a{tiles, strips, items, segs, partials, part_stride, status, test_timeout};
+    k_contract_tc_op<<<(unsigned)nitems, kOpWarps * 32, smem, st>>>(m, a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_zero_pad(__nv_bfloat16* bop, int pitch, const int4* bcat, int ncat, cudaStream_t st) {
+    if (ncat <= 0) return 0;
+    k_zero_pad<<<(unsigned)ncat, 256, 0, st>>>(bop, pitch, bcat);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -14,6 +14,7 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 
 #include "../../include/g3pcf.h"
 
@@ -136,6 +137,14 @@ struct PairArgs {
     double* dpos;
     Grid g;
     Bins bins;
+    // forward, list path: the tensor-core operands written with the multipoles
+    // (ListArgs::bop ...; null: not written), used only when no weight is negative
+    __nv_bfloat16* bop;
+    int nbcat;
+    int bop_pitch;
+    const int4* bblk;
+    int nblk;
+    const int4* bcat;
 };
 // mode 0: forward multipoles; mode 1: adjoint pair pass
 int launch_pair(int lmax, const PairArgs& a, int nsm, cudaStream_t st, int mode = 0);
@@ -195,6 +204,19 @@ struct ListArgs {
     const float2* colcoefdf;     // colcoef as head + tail FP32 pairs (double-float path)
     const float2* slotcoefdf;    // slotcoef likewise
     const float2* Vdf;           // V rows as head + tail pairs (double-float adjoint)
+    // tensor-core operands written by k_accum (forward, no negative weight):
+    // sqrt(w) A split into bf16 hi and lo: row r holds hi at bop + 2 r bop_pitch and
+    // lo bop_pitch later (one contiguous stretch per row), m blocks from multiples
+    // of 64 (bblk[m] = {first A column, width, first operand column, 0}), rows in
+    // padded coordinates (bcat per catalog: {first padded row, first A row, rows,
+    // 0}; nbcat catalogs); skip_a: the FP32 rows of A are not written
+    __nv_bfloat16* bop;
+    int nbcat;
+    int bop_pitch;
+    const int4* bblk;
+    int nblk;
+    const int4* bcat;
+    int skip_a;
     int* chunks;             // pool: 32 ints per chunk
     int* tag;                // pool: (rank among its bin's chunks) << 5 | bin, per chunk
     int* ord;                // pool: the primary's chunks listed by bin (stable), chunk | bin << 26
@@ -292,8 +314,10 @@ int contract_tc_kblock();
 // A strip: ntile (1 or 2) output tiles side by side in one row panel, tiles
 // tile0.. of the tile list; xrow / xcol = A column of its first row / column.
 // A strip: ntile (1 or 2) tiles of one row panel from tile0, computed as one
-// M = 128 MMA of width n (the strip's valid columns rounded up to 16).
-struct TcStrip { int tile0; int ntile; int xrow; int xcol; int n; };
+// M = 128 MMA of width n (the strip's valid columns rounded up to 16); xb: the
+// column of its first column panel in the bf16 operand rows (m blocks from
+// multiples of 64).
+struct TcStrip { int tile0; int ntile; int xrow; int xcol; int n; int xb; };
 // A work item of the tensor-core contraction: a strip and nvseg (1 or 2)
 // consecutive virtual segments from vseg0 (partials go to slot vseg0).
 struct TcItem { int strip; int vseg0; int nvseg; int pad; };
@@ -307,6 +331,19 @@ int launch_contract_tc(const float* A, int RLP, int RL, int64_t arows, const flo
                        const Tile* tiles, const TcStrip* strips, const TcItem* items, int nitems,
                        const Segment* segs, double* partials, int part_stride, const int* negw, int* status,
                        cudaStream_t st, int test_timeout = 0);
+// Operand columns of the bf16 rows written by k_accum: every m block starts on a
+// multiple of 64; blk[m] = {first A column, width, first operand column, 0}
+// (m <= lmax < max_blk); returns the row pitch, or -1
+int tc_operand_blocks(const Tile* tiles, int ntiles, int4* blk, int max_blk);
+// The same contraction from the bf16 hi / lo operand rows (row r: hi at bop +
+// 2 r pitch, lo pitch later; rows = padded rows): no conversion in the kernel;
+// every weight must be non-negative (the operands are sqrt(w) A).
+int launch_contract_tc_op(const __nv_bfloat16* bop, int pitch, int64_t rows, const Tile* tiles,
+                          const TcStrip* strips, const TcItem* items, int nitems, const Segment* segs,
+                          double* partials, int part_stride, int* status, cudaStream_t st, int test_timeout = 0);
+// Zero the padding rows [first + rows, first + padded) of every catalog's operand
+// rows (bcat as in ListArgs; padded = rows rounded up to the k-block)
+int launch_zero_pad(__nv_bfloat16* bop, int pitch, const int4* bcat, int ncat, cudaStream_t st);
 
 // ---- adjoint.cu ----------------------------------------------------------------
 size_t adjoint_m_floats(int nbins, int lmax);

@@ -503,6 +503,46 @@ __host__ __device__ constexpr size_t accum_smem_per_warp(int B, int NRP) {
     return (size_t)B * NRP * 4 + kImgBytes + 64 + kEntRing * 32 * 4 + kPtRing * 32 * 16;
 }
 
+// The row of A of one primary from its per-bin Chebyshev sums res (the
+// Legendre-form connection times K_lm per column), and, when asked for, the
+// tensor-core operands: sqrt(w) times the row split into bf16 hi and lo (the
+// operations of the contraction's converter warps) at the row's padded position
+// inside its catalog, m block by m block.  Out of line, so that the register
+// allocation of the pair loop does not see it.
+__device__ __forceinline__ float connect(const ListArgs& a, const float* res, int col) {
+    const int4 cv = __ldg(a.colconv + col);
+    const float* cf = a.colcoef + cv.w;
+    float v = 0.f;
+    for (int k = 0; k < cv.z; ++k) v = fmaf(__ldg(cf + k), res[cv.x + cv.y * k], v);
+    return v;
+}
+
+__device__ __noinline__ void emit_row(const ListArgs& a, const float* res, int row, int p, float w, int lane) {
+    float* Arow = a.A + (int64_t)row * a.RLP;
+    if (!a.bop) {
+        for (int col = lane; col < a.RL; col += 32) Arow[col] = connect(a, res, col);
+        return;
+    }
+    const int4 bc = __ldg(a.bcat + (a.nbcat == 1 ? 0 : (int)(a.key[p] / (unsigned long long)a.g.cells_per_cat)));
+    __nv_bfloat16* Bh = a.bop + ((int64_t)bc.x + (row - bc.y)) * 2 * a.bop_pitch;
+    __nv_bfloat16* Bl = Bh + a.bop_pitch;
+    const float sw = sqrtf(w);
+    // one column per lane, as the FP32 rows (consecutive lanes read the bins of
+    // one (l, m) in turn from res), the operand columns of an m block contiguous
+    for (int m = 0; m < a.nblk; ++m) {
+        const int4 bb = __ldg(a.bblk + m);  // {first A column, width, first operand column, 0}
+        for (int j = lane; j < bb.y; j += 32) {
+            const int col = bb.x + j;
+            const float v = connect(a, res, col);
+            if (!a.skip_a) Arow[col] = v;
+            const float y = __fmul_rn(v, sw);
+            const __nv_bfloat16 h = __float2bfloat16_rn(y);
+            Bh[bb.z + j] = h;
+            Bl[bb.z + j] = __float2bfloat16_rn(__fsub_rn(y, __bfloat162float(h)));
+        }
+    }
+}
+
 template <int L, bool EXACT>
 __global__ void __launch_bounds__(kLThreads, 3) k_accum(ListArgs a) {
     constexpr int NRP = Shape<L>::NRP;
@@ -609,16 +649,7 @@ __global__ void __launch_bounds__(kLThreads, 3) k_accum(ListArgs a) {
         }
         __syncwarp();
         const int row = a.chunked ? q - a.q0 : a.orig[p];
-        float* Arow = a.A + (int64_t)row * a.RLP;
-        // Legendre form: column (l, m, part, b) = sum_k coef_k res[slot0 + stride k]
-        // (the Chebyshev-to-D_lm connection coefficients times K_lm)
-        for (int col = lane; col < a.RL; col += 32) {
-            const int4 cv = __ldg(a.colconv + col);
-            const float* cf = a.colcoef + cv.w;
-            float v = 0.f;
-            for (int k = 0; k < cv.z; ++k) v = fmaf(__ldg(cf + k), res[cv.x + cv.y * k], v);
-            Arow[col] = v;
-        }
+        emit_row(a, res, row, p, P0.w, lane);
         if (lane == 0) a.wrow[row] = P0.w;
         __syncwarp();
     }

@@ -97,7 +97,9 @@ def test_set_option_validation():
     p.set_option(g3.OPT_TEST_FAIL_ALLOC, 0)
     p.set_option(g3.OPT_TEST_TC_TIMEOUT, 1)
     p.set_option(g3.OPT_TEST_TC_TIMEOUT, 0)
-    for opt, val in [(g3.OPT_TEST_FAIL_ALLOC, -1), (g3.OPT_TEST_TC_TIMEOUT, 2), (g3.OPT_GRAD_PRECISION, 2), (g3.OPT_GRAD_PRECISION, -1), (g3.OPT_CHUNK_ROWS, -1), (g3.OPT_CELLS_PER_RMAX, 9), (g3.OPT_KFLUSH, 1),
+    p.set_option(g3.OPT_TC_OPERANDS, 1)
+    p.set_option(g3.OPT_TC_OPERANDS, 0)
+    for opt, val in [(g3.OPT_TEST_FAIL_ALLOC, -1), (g3.OPT_TEST_TC_TIMEOUT, 2), (g3.OPT_TC_OPERANDS, 2), (g3.OPT_TC_OPERANDS, -1), (g3.OPT_GRAD_PRECISION, 2), (g3.OPT_GRAD_PRECISION, -1), (g3.OPT_CHUNK_ROWS, -1), (g3.OPT_CELLS_PER_RMAX, 9), (g3.OPT_KFLUSH, 1),
                      (g3.OPT_X_REFINE, 17), (g3.OPT_X_REFINE, -1),
                      (g3.OPT_KFLUSH, 17), (g3.OPT_PAIR_KERNELS, 3), (g3.OPT_PAIR_KERNELS, -1),
                      (g3.OPT_LIST_BYTES, -1), (g3.OPT_LIST_BYTES, 1000), (g3.OPT_BASIS, 2), (99, 1)]:

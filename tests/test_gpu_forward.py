@@ -195,6 +195,57 @@ def test_batch_tensor_core_path():
         assert maxrel(zb[k].cpu().numpy(), zo) < TOL_TC
 
 
+def test_tc_operand_paths_bit_identical():
+    # The bf16 operands written by the pair stage and those formed inside the
+    # contraction kernel are the same numbers (the same FP32 row times the same
+    # sqrt(w), split the same way), summed in the same order: zeta must agree
+    # bit for bit, on one catalog over many segments and on a ragged batch.
+    cat = catalogs.clustered_2m(n=60000, seed=21, box=700.0)
+    plan = g3.Plan(**cat.params())
+    pos, w = to_dev(cat, torch)
+    zc, cc = plan.compute(pos, w)
+    assert plan.stats()["tc_operands_from_pairs"] == 0.0
+    plan.set_option(g3.OPT_TC_OPERANDS, 1)
+    zd, cd = plan.compute(pos, w)
+    assert plan.stats()["tc_operands_from_pairs"] == 1.0
+    assert torch.equal(cd, cc)
+    assert torch.equal(zd, zc)
+    plan.close()
+
+    cats = catalogs.batched(ncat=5, seed=6, sizes=[700, 1300, 0, 90, 1000], box=400.0)
+    plan = g3.Plan(**cats[0].params())
+    pos = torch.from_numpy(np.concatenate([c.pos for c in cats])).cuda()
+    w = torch.from_numpy(np.concatenate([c.w for c in cats])).cuda()
+    offs = np.cumsum([0] + [c.n for c in cats])
+    zc, _ = plan.compute_batch(pos, w, offs)
+    plan.set_option(g3.OPT_TC_OPERANDS, 1)
+    zd, _ = plan.compute_batch(pos, w, offs)
+    assert plan.stats()["tc_operands_from_pairs"] == 1.0
+    assert torch.equal(zd, zc)
+    for k, c in enumerate(cats):
+        zo, _ = oracle_zeta(c)
+        if np.abs(zo).max() > 0:
+            assert maxrel(zd[k].cpu().numpy(), zo) < TOL_TC
+    plan.close()
+
+
+def test_tc_operands_fall_back_with_negative_weights():
+    # data plus randoms at negative weight: the sqrt(w) operands cannot be formed,
+    # so the contraction forms its own from the FP32 rows; zeta matches the oracle
+    cat = catalogs.data_minus_randoms(catalogs.small_case("clustered", 1500, seed=9, box=400.0, nbins=6, rmin=5.0,
+                                                          rmax=80.0, lmax=6),
+                                      nrand_factor=2, seed=10)
+    plan = g3.Plan(**cat.params())
+    plan.set_option(g3.OPT_TC_OPERANDS, 1)
+    pos, w = to_dev(cat, torch)
+    z, c = plan.compute(pos, w)
+    assert plan.stats()["tc_operands_from_pairs"] == 0.0
+    zo, co = oracle_zeta(cat)
+    np.testing.assert_array_equal(c.cpu().numpy(), co)
+    assert maxrel(z.cpu().numpy(), zo) < TOL_TC
+    plan.close()
+
+
 @pytest.mark.parametrize("tc", [False, True])
 def test_chunked_passes_match_single_pass(tc):
     # primaries processed in 5 chunks (multipoles of earlier chunks are
