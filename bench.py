@@ -60,9 +60,9 @@ def accum_exec_flops(L: int) -> int:
 
 
 # DRAM bytes of one k_accum launch per primary, from the ncu capture summarised
-# in profiles/k_accum_clustered_200k_L696.md (17.59 GB for 200,000 primaries,
+# in profiles/k_accum_clustered_200k_L696.md (17.60 GB for 200,000 primaries,
 # Lambda = 10); a full-size launch is scaled by its primaries.
-ACCUM_DRAM_BYTES_PER_PRIMARY = 17.59e9 / 200000
+ACCUM_DRAM_BYTES_PER_PRIMARY = 17.60e9 / 200000
 
 
 def peaks():
