@@ -66,11 +66,16 @@ def test_injected_allocation_failure_in_backward():
     assert torch.count_nonzero(dpos).item() == 0 and torch.count_nonzero(dw).item() == 0
 
 
-def test_tensor_core_wait_gives_up_then_recovery():
+@pytest.mark.parametrize("operands", [0, 1])
+def test_tensor_core_wait_gives_up_then_recovery(operands):
+    # operands 1: the contraction kernel that copies the operands written by the
+    # pair stage, whose MMA thread waits on the copies instead of the converters
     cat = _cat()
     ref = oracle_zeta(cat)
     plan = g3.Plan(**cat.params())
+    plan.set_option(g3.OPT_TC_OPERANDS, operands)
     _check(plan, cat, ref, tc=True)
+    assert plan.stats()["tc_operands_from_pairs"] == float(operands)
     plan.set_option(g3.OPT_TEST_TC_TIMEOUT, 1)
     with pytest.raises(g3.G3PCFError) as ei:
         plan.compute(*to_dev(cat, torch))
