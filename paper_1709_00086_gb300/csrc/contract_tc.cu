@@ -47,8 +47,6 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
-#include <cstdio>
-
 #include "internal.h"
 
 namespace g3 {
