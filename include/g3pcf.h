@@ -179,8 +179,12 @@ int g3pcf_alm(g3pcf_plan_t plan, const int64_t* primaries, int64_t np, double* o
  * neighbours per point n (4/3) pi rmax^3 / box^3 in quarter-octave buckets); a
  * hit applies the stored settings without timing anything, a miss tunes and
  * appends a line (an unreadable or unwritable file only disables the cache).
- * chosen (HOST, may be NULL): {cells per rmax, x refinement, kflush,
- * pair-stage microseconds of the sample, 1 if taken from the cache}.
+ * With the pair lists in the Chebyshev basis it then times the pair stage and
+ * the tensor-core contraction together on the same sample for both settings of
+ * G3PCF_OPT_TC_OPERANDS and keeps the faster.
+ * chosen (HOST, may be NULL, 6 entries): {cells per rmax, x refinement, kflush,
+ * pair-stage microseconds of the sample, 1 if taken from the cache,
+ * G3PCF_OPT_TC_OPERANDS}.
  * Allocates a temporary zeta buffer; synchronises the plan's stream. */
 int g3pcf_autotune_cached(g3pcf_plan_t plan, const void* pos, const float* w, int64_t n, int flags,
                           const char* cache_path, int64_t* chosen);

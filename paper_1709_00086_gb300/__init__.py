@@ -276,19 +276,19 @@ class Plan:
 
     def autotune_cached(self, pos, w, cache_path=None) -> dict:
         """Tune cell resolution and x refinement (pair lists) or flush size (fused
-        kernel) on a sample of this data, through the on-disk cache cache_path
-        (see g3pcf_autotune_cached)."""
+        kernel), then the contraction's operand source, on a sample of this data,
+        through the on-disk cache cache_path (see g3pcf_autotune_cached)."""
         import torch
         pos = pos.contiguous()
         w = w.contiguous()
         flags = F_POS_F64 if pos.dtype == torch.float64 else 0
-        out = np.zeros(5, dtype=np.int64)
+        out = np.zeros(6, dtype=np.int64)
         self._stream()
         _check(lib().g3pcf_autotune_cached(self._h, _ptr(pos), _ptr(w), pos.shape[0], flags,
                                            None if cache_path is None else str(cache_path).encode(),
                                            out.ctypes.data_as(ctypes.c_void_p)))
         return {"cells_per_rmax": int(out[0]), "x_refine": int(out[1]), "kflush": int(out[2]),
-                "pair_us": int(out[3]), "from_cache": bool(out[4])}
+                "pair_us": int(out[3]), "from_cache": bool(out[4]), "tc_operands": int(out[5])}
 
     def set_option(self, option: int, value: int):
         """Tuning knob (OPT_CHUNK_ROWS, OPT_CELLS_PER_RMAX, OPT_KFLUSH, OPT_PAIR_KERNELS,

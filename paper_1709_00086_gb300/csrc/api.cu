@@ -1686,13 +1686,13 @@ std::string tune_key(g3pcf_plan_t P, int64_t n) {
     const double nb = (double)n * V / (P->box * P->box * P->box);
     const int bucket = (int)std::lround(4.0 * std::log2(nb > 1e-30 ? nb : 1e-30));
     char k[160];
-    snprintf(k, sizeof(k), "g3pcf-tune-v1 nbins=%d lmax=%d los=%d pairk=%d sm=%d nbr4=%d", P->nbins, P->lmax,
+    snprintf(k, sizeof(k), "g3pcf-tune-v2 nbins=%d lmax=%d los=%d pairk=%d sm=%d nbr4=%d", P->nbins, P->lmax,
              P->los_mode, P->opt_pair == 1 ? 1 : 0, P->nsm, bucket);
     return k;
 }
 
-// A cache line is "<key> | <cells> <xref> <kflush> <microseconds>".
-bool tune_lookup(const char* path, const std::string& key, int v[4]) {
+// A cache line is "<key> | <cells> <xref> <kflush> <microseconds> <operands>".
+bool tune_lookup(const char* path, const std::string& key, int v[5]) {
     FILE* f = std::fopen(path, "r");
     if (!f) return false;
     char line[512];
@@ -1700,10 +1700,10 @@ bool tune_lookup(const char* path, const std::string& key, int v[4]) {
     while (std::fgets(line, sizeof(line), f)) {
         const char* bar = std::strstr(line, " | ");
         if (!bar || (size_t)(bar - line) != key.size() || std::strncmp(line, key.c_str(), key.size()) != 0) continue;
-        int a[4];
-        if (std::sscanf(bar + 3, "%d %d %d %d", &a[0], &a[1], &a[2], &a[3]) == 4 && a[0] >= 1 && a[0] <= 8 &&
-            a[1] >= 1 && a[1] <= 16 && a[2] >= 2 && a[2] <= 16) {
-            for (int t = 0; t < 4; ++t) v[t] = a[t];
+        int a[5];
+        if (std::sscanf(bar + 3, "%d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4]) == 5 && a[0] >= 1 &&
+            a[0] <= 8 && a[1] >= 1 && a[1] <= 16 && a[2] >= 2 && a[2] <= 16 && (a[4] == 0 || a[4] == 1)) {
+            for (int t = 0; t < 5; ++t) v[t] = a[t];
             found = true;  // the last matching line wins
         }
     }
@@ -1711,10 +1711,10 @@ bool tune_lookup(const char* path, const std::string& key, int v[4]) {
     return found;
 }
 
-void tune_store(const char* path, const std::string& key, const int v[4]) {
+void tune_store(const char* path, const std::string& key, const int v[5]) {
     FILE* f = std::fopen(path, "a");
     if (!f) return;  // an unwritable cache only costs a re-tune
-    std::fprintf(f, "%s | %d %d %d %d\n", key.c_str(), v[0], v[1], v[2], v[3]);
+    std::fprintf(f, "%s | %d %d %d %d %d\n", key.c_str(), v[0], v[1], v[2], v[3], v[4]);
     std::fclose(f);
 }
 
@@ -1729,17 +1729,16 @@ int g3pcf_autotune_cached(g3pcf_plan_t P, const void* pos, const float* w, int64
     if (flags & ~G3PCF_F_POS_F64) return fail(G3PCF_ERR_ARG, "autotune accepts G3PCF_F_POS_F64 only");
     if (int r = setup_device(P)) return r;
     const std::string key = tune_key(P, n);
-    int hit[4];
+    int hit[5];
     if (cache_path && *cache_path && tune_lookup(cache_path, key, hit)) {
         P->opt_cells = hit[0];
         P->opt_xref = hit[1];
         P->kflush = hit[2];
+        P->opt_tc_operands = hit[4];
         if (chosen) {
-            chosen[0] = hit[0];
-            chosen[1] = hit[1];
-            chosen[2] = hit[2];
-            chosen[3] = hit[3];
+            for (int t = 0; t < 4; ++t) chosen[t] = hit[t];
             chosen[4] = 1;
+            chosen[5] = hit[4];
         }
         return G3PCF_OK;
     }
@@ -1760,6 +1759,7 @@ int g3pcf_autotune_cached(g3pcf_plan_t P, const void* pos, const float* w, int64
             break;
         }
     const int saved_cells = P->opt_cells, saved_xref = P->opt_xref, saved_kf = P->kflush;
+    const int saved_ops = P->opt_tc_operands;
     const int64_t saved_chunk = P->opt_chunk;
     double best = 1e300;
     int best_s = s0, best_x = 8, best_kf = saved_kf;
@@ -1807,6 +1807,43 @@ int g3pcf_autotune_cached(g3pcf_plan_t P, const void* pos, const float* w, int64
             }
         }
     }
+    // with those, the contraction's operands (pair-list path, Chebyshev basis):
+    // formed in the contraction kernel or written by the pair stage, timed over
+    // the pair stage and the tensor-core contraction together
+    int best_ops = saved_ops;
+    if (rc == G3PCF_OK && !fused && P->opt_basis == 0) {
+        P->opt_cells = best_s;
+        P->opt_xref = best_x;
+        P->kflush = best_kf;
+        double best_total = 1e300;
+        for (int ops = 0; ops <= 1 && rc == G3PCF_OK; ++ops) {
+            P->opt_tc_operands = ops;
+            CallSpec c;
+            c.pos = pos;
+            c.w = w;
+            c.n = n;
+            c.n_primary = n < 32768 ? n : 32768;
+            c.pos_f64 = (flags & G3PCF_F_POS_F64) ? 1 : 0;
+            c.ncat = 1;
+            c.offs = {0, n};
+            c.zeta = ztmp;
+            c.counts = nullptr;
+            c.flags = 0;
+            double t = 1e300;
+            for (int rep = 0; rep < 3 && rc == G3PCF_OK; ++rep) {
+                rc = run_forward(P, c);
+                if (rc == G3PCF_OK && rep >= 1) {
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, P->ev[1], P->ev[3]);
+                    t = std::min(t, (double)ms);
+                }
+            }
+            if (rc == G3PCF_OK && t < best_total) {
+                best_total = t;
+                best_ops = ops;
+            }
+        }
+    }
     cudaFree(ztmp);
     P->have_forward = false;
     P->have_alm = false;
@@ -1815,23 +1852,26 @@ int g3pcf_autotune_cached(g3pcf_plan_t P, const void* pos, const float* w, int64
         P->opt_cells = saved_cells;
         P->opt_xref = saved_xref;
         P->kflush = saved_kf;
+        P->opt_tc_operands = saved_ops;
         return rc;
     }
     P->opt_cells = best_s;
     P->opt_xref = best_x;
     P->kflush = best_kf;
-    const int v[4] = {best_s, best_x, best_kf, (int)std::min(best * 1000.0, 2e9)};
+    P->opt_tc_operands = best_ops;
+    const int v[5] = {best_s, best_x, best_kf, (int)std::min(best * 1000.0, 2e9), best_ops};
     if (cache_path && *cache_path) tune_store(cache_path, key, v);
     if (chosen) {
         for (int t = 0; t < 4; ++t) chosen[t] = v[t];
         chosen[4] = 0;
+        chosen[5] = best_ops;
     }
     return G3PCF_OK;
 }
 
 int g3pcf_autotune(g3pcf_plan_t P, const void* pos, const float* w, int64_t n, int flags,
                    int64_t* chosen) {
-    int64_t c5[5] = {0, 0, 0, 0, 0};
+    int64_t c5[6] = {0, 0, 0, 0, 0, 0};
     const int rc = g3pcf_autotune_cached(P, pos, w, n, flags, nullptr, c5);
     if (rc == G3PCF_OK && chosen) {
         chosen[0] = c5[0];

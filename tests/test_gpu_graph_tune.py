@@ -101,17 +101,23 @@ def test_autotune_cache_round_trip_and_tuned_parity(tmp_path):
     p1 = g3.Plan(**cat.params())
     t1 = p1.autotune_cached(pos, w, cache)
     assert not t1["from_cache"] and t1["pair_us"] > 0
-    assert 1 <= t1["cells_per_rmax"] <= 8 and t1["x_refine"] in (4, 8, 16)
+    assert 1 <= t1["cells_per_rmax"] <= 8 and t1["x_refine"] in (4, 8, 16) and t1["tc_operands"] in (0, 1)
     lines = cache.read_text().strip().splitlines()
     assert len(lines) == 1 and "nbins=10 lmax=10" in lines[0]
     p2 = g3.Plan(**cat.params())
     t2 = p2.autotune_cached(pos, w, cache)
-    assert t2["from_cache"] and (t2["cells_per_rmax"], t2["x_refine"]) == (t1["cells_per_rmax"], t1["x_refine"])
+    assert t2["from_cache"] and (t2["cells_per_rmax"], t2["x_refine"], t2["tc_operands"]) == (
+        t1["cells_per_rmax"], t1["x_refine"], t1["tc_operands"])
     assert len(cache.read_text().strip().splitlines()) == 1
     z, c = p2.compute(pos, w, n_primary=300, fp32_contraction=True)
     zo, co = oracle_zeta(cat, n_primary=300)
     np.testing.assert_array_equal(c.cpu().numpy(), co)
     assert maxrel(z.cpu().numpy(), zo) < 1e-5
+    # the tuned tensor-core forward, with the operand source the tuner kept
+    ztc, ctc = p2.compute(pos, w, n_primary=300)
+    assert p2.stats()["tc_operands_from_pairs"] == float(t1["tc_operands"])
+    np.testing.assert_array_equal(ctc.cpu().numpy(), co)
+    assert maxrel(ztc.cpu().numpy(), zo) < 1e-4
     # every x refinement and resolution the tuner may pick gives the same counts
     for s, x in ((max(1, t1["cells_per_rmax"] - 1), 4), (t1["cells_per_rmax"] + 1, 16)):
         p3 = g3.Plan(**cat.params())
