@@ -503,12 +503,8 @@ __host__ __device__ constexpr size_t accum_smem_per_warp(int B, int NRP) {
     return (size_t)B * NRP * 4 + kImgBytes + 64 + kEntRing * 32 * 4 + kPtRing * 32 * 16;
 }
 
-// The row of A of one primary from its per-bin Chebyshev sums res (the
-// Legendre-form connection times K_lm per column), and, when asked for, the
-// tensor-core operands: sqrt(w) times the row split into bf16 hi and lo (the
-// operations of the contraction's converter warps) at the row's padded position
-// inside its catalog, m block by m block.  Out of line, so that the register
-// allocation of the pair loop does not see it.
+// Column col of a row of A from the per-bin Chebyshev sums res: the
+// Legendre-form connection times K_lm.
 __device__ __forceinline__ float connect(const ListArgs& a, const float* res, int col) {
     const int4 cv = __ldg(a.colconv + col);
     const float* cf = a.colcoef + cv.w;
@@ -517,6 +513,11 @@ __device__ __forceinline__ float connect(const ListArgs& a, const float* res, in
     return v;
 }
 
+// The row of A of one primary, and, when asked for, the tensor-core operands:
+// sqrt(w) times the row split into bf16 hi and lo (the operations of the
+// contraction's converter warps) at the row's padded position inside its
+// catalog, m block by m block.  Out of line, so that the register allocation of
+// the pair loop does not see it.
 __device__ __noinline__ void emit_row(const ListArgs& a, const float* res, int row, int p, float w, int lane) {
     float* Arow = a.A + (int64_t)row * a.RLP;
     if (!a.bop) {
