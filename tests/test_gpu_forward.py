@@ -228,6 +228,21 @@ def test_tc_operand_paths_bit_identical():
             assert maxrel(zd[k].cpu().numpy(), zo) < TOL_TC
     plan.close()
 
+    # FP64 positions and a subset of primaries (a ragged 1,111 of 4,000 points)
+    cat = catalogs.small_case("uniform", 4000, seed=31, box=300.0, nbins=7, rmin=2.0, rmax=70.0, lmax=7,
+                              dtype=np.float64)
+    plan = g3.Plan(**cat.params())
+    pos, w = to_dev(cat, torch)
+    zc, cc = plan.compute(pos, w, n_primary=1111)
+    plan.set_option(g3.OPT_TC_OPERANDS, 1)
+    zd, cd = plan.compute(pos, w, n_primary=1111)
+    assert plan.stats()["tc_operands_from_pairs"] == 1.0
+    assert torch.equal(cd, cc) and torch.equal(zd, zc)
+    zo, co = oracle_zeta(cat, n_primary=1111)
+    np.testing.assert_array_equal(cd.cpu().numpy(), co)
+    assert maxrel(zd.cpu().numpy(), zo) < TOL_TC
+    plan.close()
+
 
 def test_tc_operands_fall_back_with_negative_weights():
     # data plus randoms at negative weight: the sqrt(w) operands cannot be formed,
