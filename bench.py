@@ -310,6 +310,25 @@ def measure_forward(cat, steps: int, warmup: int) -> dict:
             "contract_share": con / t, "pair_ms": float(np.mean([x["pair_ms"] for x in st])),
             "zeta_tflops": zeta_flops_per_primary(cat.nbins, cat.lmax) * st[-1]["primaries"] / (con / 1e3) / 1e12}
     res["pairs_per_step"] = pairs
+    # the tensor-core form replayed from a CUDA graph (passes planned on the device:
+    # no host round trip and no per-kernel launch cost inside the step); the same
+    # output buffer every call, so that every call after the first replays
+    zb = torch.empty((plan.zsize, 2), dtype=torch.float64, device=dev)
+    for _ in range(max(warmup, 2)):
+        plan.compute(pos, w, with_counts=False, graph=True, out=zb)
+    ms = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.compute(pos, w, with_counts=False, sync=False, graph=True, out=zb)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    plan.status()
+    tg = float(np.mean(ms))
+    res["tc"]["graph_ms_per_step"] = tg
+    res["tc"]["graph_pairs_per_s"] = pairs / (tg / 1e3)
     del plan, pos, w
     torch.cuda.empty_cache()
     return res
