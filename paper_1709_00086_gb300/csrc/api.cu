@@ -966,24 +966,27 @@ int run_forward(g3pcf_plan_t P, CallSpec& c) {
         // written by the pair stage only when they fit beside A in the budget
         bool ops_fit = false;
         const bool ops = use_tc && P->opt_tc_operands == 1 && P->opt_pair != 1 && P->opt_basis == 0 && !P->capturing;
-        {
+        // no memory query inside a capture: a captured forward keeps the warm-up's chunking
+        const bool fixed = P->capturing && P->fixed_chunk > 0;
+        double budget = 0.0;
+        const double per_row = 4.0 * P->RLP + 4.0;
+        if (ops || (c.ncat == 1 && P->opt_chunk <= 0 && !fixed)) {
             size_t fr = 0, tot = 0;
             CK(cudaMemGetInfo(&fr, &tot));
-            double budget = 0.4 * (double)fr;
+            budget = 0.4 * (double)fr;
             if (budget > 48e9) budget = 48e9;
-            const double per_row = 4.0 * P->RLP + 4.0;
-            ops_fit = ops && budget / (per_row + 4.0 * P->RLPb) >= (double)(rows_all + 64 * c.ncat);
-            if (c.ncat == 1) {
-                if (P->opt_chunk > 0) {
-                    C = P->opt_chunk;
-                } else if (P->capturing && P->fixed_chunk > 0) {
-                    C = P->fixed_chunk;
-                } else {
-                    C = (int64_t)(budget / per_row) / KB * KB;
-                    if (C < KB) C = KB;
-                }
-                if (C > rows_all) C = rows_all;
+        }
+        ops_fit = ops && budget / (per_row + 4.0 * P->RLPb) >= (double)(rows_all + 64 * c.ncat);
+        if (c.ncat == 1) {
+            if (P->opt_chunk > 0) {
+                C = P->opt_chunk;
+            } else if (fixed) {
+                C = P->fixed_chunk;
+            } else {
+                C = (int64_t)(budget / per_row) / KB * KB;
+                if (C < KB) C = KB;
             }
+            if (C > rows_all) C = rows_all;
         }
         const bool chunked = (c.ncat == 1) && C < rows_all;
         P->fixed_chunk = C;
