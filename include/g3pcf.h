@@ -227,9 +227,8 @@ int g3pcf_stats(g3pcf_plan_t plan, double* vals, int nvals);
  * Scratch: 16 MiB of FP64 partial sums and small tile tables in fixed device
  * arrays inside the library, present on every GPU that loads it until the
  * process exits.  The first call on a device looks up their addresses (with
- * that device current; safe from several host threads); make that first call
- * before any stream capture, and do not call this entry point on a device
- * after cudaDeviceReset().  Every call rewrites the tables on the device and
+ * that device current; safe from several host threads); do not call this
+ * entry point on a device after cudaDeviceReset().  Every call rewrites the tables on the device and
  * overwrites what it reads, so nothing needs clearing; calls that overlap on
  * the GPU share the arrays and race, so the caller must serialise them.
  * Limits: nbins <= 32, lmax <= 10, np < 2^27; shapes whose tile table or one
