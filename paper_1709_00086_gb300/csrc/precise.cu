@@ -175,27 +175,54 @@ __device__ __forceinline__ void load_sec(const ListArgs& a, unsigned e, float4& 
 }
 
 // ---- forward ----------------------------------------------------------------
-// Per-pair record in shared memory (floats): T_k head/tail at 2k (k = 0..L),
-// w at 2(L+1) (tail 0), w (x + iy)^m for m >= 1 at 2(L+1) + 2 + 4(m-1):
-// Re head, Re tail, Im head, Im tail.  Row stride RS with RS/2 odd (float2
-// accesses of 32 rows at one offset hit distinct banks).
+// The (lmax+1)^2 accumulator slots are handled in pairs, two slots per packed
+// (f32x2) operation: the m = 0 slots k, k + 1 (k even), and for m >= 1 the Re
+// and Im slots of one (m, k).  Per-pair record in shared memory (floats, every
+// group of four 16-byte aligned so that one 128-bit load gives a slot pair's
+// head pair and tail pair):
+//   TA (m = 0), k even:  T_k.h, T_k+1.h, T_k.l, T_k+1.l      (LE = lmax+1 rounded up to even)
+//   TB (m >= 1), k < L:  T_k.h, T_k.h,   T_k.l, T_k.l
+//   W:                   w,     w,       0,     0
+//   CB, m = 1..L:        Re.h,  Im.h,    Re.l,  Im.l         of w (x + iy)^m
+// Row stride RS (floats) a multiple of 4.
 template <int L>
 struct DfRec {
-    static constexpr int N = 6 * L + 4;
-    static constexpr int RS = ((N / 2) % 2 == 1) ? N : N + 2;
-    static constexpr int NR = (L + 1) * (L + 1);
-    static constexpr int S = (NR + 31) / 32;  // slots per lane
+    static constexpr int LE = (L + 2) & ~1;       // m = 0 slots, padded to even
+    static constexpr int TA = 0;
+    static constexpr int TB = 2 * LE;
+    static constexpr int W = TB + 4 * L;
+    static constexpr int CB = W + 4;
+    static constexpr int N = CB + 4 * L;
+    static constexpr int RS = N;                   // a multiple of 4
+    static constexpr int NP = LE / 2 + L * (L + 1) / 2;  // slot pairs
+    static constexpr int S2 = (NP + 31) / 32;            // slot pairs per lane
 };
 
 __host__ __device__ constexpr size_t accum_df_smem_per_warp(int L, int B, int NRP) {
-    return (size_t)B * NRP * 8 + 54 * 16 + 9 * 8 + 8 +
-           (size_t)32 * (((6 * L + 4) / 2) % 2 == 1 ? 6 * L + 4 : 6 * L + 6) * 4;
+    return (size_t)B * NRP * 8 + 54 * 16 + 9 * 8 + 8 + (size_t)32 * (2 * ((L + 2) & ~1) + 8 * L + 4) * 4;
+}
+
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+// Two double-float accumulators at once (.x and .y): (H, Lo) += T * C, the
+// operations of df_acc(acc, df_mul_u(T, C)) lane for lane.
+__device__ __forceinline__ void df_acc_mul2(float2& H, float2& Lo, float4 T, float4 C) {
+    const float2 Th = make_float2(T.x, T.y), Tl = make_float2(T.z, T.w);
+    const float2 Ch = make_float2(C.x, C.y), Cl = make_float2(C.z, C.w);
+    const float2 p = __fmul2_rn(Th, Ch);
+    float2 e = __ffma2_rn(Th, Ch, neg2(p));
+    e = __ffma2_rn(Th, Cl, __ffma2_rn(Tl, Ch, e));
+    const float2 s = __fadd2_rn(H, p);
+    const float2 bb = __fadd2_rn(s, neg2(H));
+    const float2 err = __fadd2_rn(__fadd2_rn(H, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(p, neg2(bb)));
+    Lo = __fadd2_rn(Lo, __fadd2_rn(err, e));
+    H = s;
 }
 
 template <int L>
 __global__ void __launch_bounds__(kDThreads) k_accum_df(ListArgs a) {
     using R_ = DfRec<L>;
-    constexpr int NR = R_::NR, S = R_::S, RS = R_::RS;
+    constexpr int S2 = R_::S2, RS = R_::RS, NP = R_::NP;
+    constexpr int U = S2 == 1 ? 8 : 4;  // pairs per round of the accumulation
     constexpr int NRP = Shape<L>::NRP;
     extern __shared__ __align__(16) unsigned char draw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -205,24 +232,29 @@ __global__ void __launch_bounds__(kDThreads) k_accum_df(ListArgs a) {
     float4* img = reinterpret_cast<float4*>(base + (size_t)B * NRP * 8);    // [54]
     df* Rd = reinterpret_cast<df*>(base + (size_t)B * NRP * 8 + 54 * 16);   // [9]
     float* rec = reinterpret_cast<float*>(base + (size_t)B * NRP * 8 + 54 * 16 + 9 * 8 + 8);  // [32][RS]
-    // this lane's slots: offsets of T_k and of the (m, part) factor in a record
-    int offT[S], offC[S];
+    // this lane's slot pairs: record offsets of their T and C operands and their
+    // two slots (slot1 < 0: none, e.g. the padding slot of m = 0)
+    int offT[S2], offC[S2], slot0[S2], slot1[S2];
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-        const int slot = lane + 32 * s;
-        offT[s] = -1;
-        offC[s] = 0;
-        if (slot < NR) {
-            if (slot <= L) {
-                offT[s] = 2 * slot;
-                offC[s] = 2 * (L + 1);
-            } else {
-                int m = 1;
-                while (m < L && slot >= acc_base(L, m + 1)) ++m;
-                const int idx = slot - acc_base(L, m);
-                offT[s] = 2 * (idx >> 1);
-                offC[s] = 2 * (L + 1) + 2 + 4 * (m - 1) + 2 * (idx & 1);
+    for (int s = 0; s < S2; ++s) {
+        const int sp = lane + 32 * s;
+        offT[s] = 0;
+        offC[s] = R_::W;
+        slot0[s] = slot1[s] = -1;
+        if (sp < R_::LE / 2) {
+            offT[s] = R_::TA + 4 * sp;
+            slot0[s] = 2 * sp;
+            slot1[s] = 2 * sp + 1 <= L ? 2 * sp + 1 : -1;
+        } else if (sp < NP) {
+            int idx = sp - R_::LE / 2, m = 1;
+            while (idx >= L + 1 - m) {
+                idx -= L + 1 - m;
+                ++m;
             }
+            offT[s] = R_::TB + 4 * idx;
+            offC[s] = R_::CB + 4 * (m - 1);
+            slot0[s] = acc_base(L, m) + 2 * idx;
+            slot1[s] = slot0[s] + 1;
         }
     }
     const Grid& g = a.g;
@@ -256,19 +288,23 @@ __global__ void __launch_bounds__(kDThreads) k_accum_df(ListArgs a) {
         const int* chunks = a.chunks + (int64_t)cb * 32;
         const int* ordp = a.ord + cb;
         __syncwarp();
-        df acc[S];
+        float2 accH[S2], accL[S2];
 #pragma unroll
-        for (int s = 0; s < S; ++s) acc[s] = {0.f, 0.f};
+        for (int s = 0; s < S2; ++s) accH[s] = accL[s] = make_float2(0.f, 0.f);
         auto flush = [&](int b) {
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-                const int slot = lane + 32 * s;
-                if (slot < NR) {
-                    const float2 o = res[b * NRP + slot];
-                    const df v = df_add({o.x, o.y}, acc[s]);
-                    res[b * NRP + slot] = make_float2(v.h, v.l);
+            for (int s = 0; s < S2; ++s) {
+                if (slot0[s] >= 0) {
+                    const float2 o = res[b * NRP + slot0[s]];
+                    const df v = df_add({o.x, o.y}, {accH[s].x, accL[s].x});
+                    res[b * NRP + slot0[s]] = make_float2(v.h, v.l);
                 }
-                acc[s] = {0.f, 0.f};
+                if (slot1[s] >= 0) {
+                    const float2 o = res[b * NRP + slot1[s]];
+                    const df v = df_add({o.x, o.y}, {accH[s].y, accL[s].y});
+                    res[b * NRP + slot1[s]] = make_float2(v.h, v.l);
+                }
+                accH[s] = accL[s] = make_float2(0.f, 0.f);
             }
         };
         if (nch > 0) {
@@ -293,8 +329,8 @@ __global__ void __launch_bounds__(kDThreads) k_accum_df(ListArgs a) {
                     flush(curb);
                     curb = b;
                 }
-                // this lane's pair -> its record
-                float* my = rec + lane * RS;
+                // this lane's pair -> its record (only valid pairs are read back)
+                float4* my = reinterpret_cast<float4*>(rec + lane * RS);
                 if (e != kNoPairD) {
                     const int code = (int)(e >> kIdxBits);
                     const float4 hh = img[code], tt = img[27 + code];
@@ -303,33 +339,25 @@ __global__ void __launch_bounds__(kDThreads) k_accum_df(ListArgs a) {
                     df ux, uy, uz, rinv;
                     unit_df(dx, dy, dz, Rd, radial, ux, uy, uz, rinv);
                     const float w = qv.w;
-                    df Tm = {1.f, 0.f}, Tc = uz;
-                    my[0] = 1.f;
-                    my[1] = 0.f;
-                    if constexpr (L >= 1) {
-                        my[2] = uz.h;
-                        my[3] = uz.l;
-                    }
+                    df T[R_::LE];
+                    T[0] = {1.f, 0.f};
+                    if constexpr (L >= 1) T[1] = uz;
                     const df z2 = {2.f * uz.h, 2.f * uz.l};
 #pragma unroll
-                    for (int k = 2; k <= L; ++k) {
-                        const df Tn = df_add(df_mul(z2, Tc), df_neg(Tm));
-                        my[2 * k] = Tn.h;
-                        my[2 * k + 1] = Tn.l;
-                        Tm = Tc;
-                        Tc = Tn;
-                    }
-                    my[2 * (L + 1)] = w;
-                    my[2 * (L + 1) + 1] = 0.f;
+                    for (int k = 2; k <= L; ++k) T[k] = df_add(df_mul(z2, T[k - 1]), df_neg(T[k - 2]));
+#pragma unroll
+                    for (int k = L + 1; k < R_::LE; ++k) T[k] = {0.f, 0.f};
+#pragma unroll
+                    for (int k = 0; k < R_::LE; k += 2)
+                        my[(R_::TA >> 2) + (k >> 1)] = make_float4(T[k].h, T[k + 1].h, T[k].l, T[k + 1].l);
+#pragma unroll
+                    for (int k = 0; k < L; ++k) my[(R_::TB >> 2) + k] = make_float4(T[k].h, T[k].h, T[k].l, T[k].l);
+                    my[R_::W >> 2] = make_float4(w, w, 0.f, 0.f);
                     if constexpr (L >= 1) {
                         df cr = df_mulf(ux, w), ci = df_mulf(uy, w);
 #pragma unroll
                         for (int m = 1; m <= L; ++m) {
-                            float* c = my + 2 * (L + 1) + 2 + 4 * (m - 1);
-                            c[0] = cr.h;
-                            c[1] = cr.l;
-                            c[2] = ci.h;
-                            c[3] = ci.l;
+                            my[(R_::CB >> 2) + (m - 1)] = make_float4(cr.h, ci.h, cr.l, ci.l);
                             if (m < L) {
                                 df nr, ni;
                                 df_cmul(cr, ci, ux, uy, nr, ni);
@@ -338,23 +366,37 @@ __global__ void __launch_bounds__(kDThreads) k_accum_df(ListArgs a) {
                             }
                         }
                     }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < R_::N; ++k) my[k] = 0.f;
                 }
                 __syncwarp();
-                // every valid pair of the chunk into this lane's slots
+                // every valid pair of the chunk into this lane's slot pairs, U
+                // pairs per round (loads and products of later pairs overlap the
+                // sums of earlier ones; the sums keep the pairs' order)
                 unsigned valid = __ballot_sync(kFull, e != kNoPairD);
                 while (valid) {
-                    const int t = __ffs(valid) - 1;
-                    valid &= valid - 1;
-                    const float* rt = rec + t * RS;
+                    int t[U];
 #pragma unroll
-                    for (int s = 0; s < S; ++s) {
-                        if (offT[s] >= 0) {
-                            const float2 T = *reinterpret_cast<const float2*>(rt + offT[s]);
-                            const float2 C = *reinterpret_cast<const float2*>(rt + offC[s]);
-                            df_acc(acc[s], df_mul_u({T.x, T.y}, {C.x, C.y}));
+                    for (int u = 0; u < U; ++u) {
+                        t[u] = -1;
+                        if (valid) {
+                            t[u] = __ffs(valid) - 1;
+                            valid &= valid - 1;
+                        }
+                    }
+#pragma unroll
+                    for (int s = 0; s < S2; ++s) {
+                        if (lane + 32 * s < NP) {
+                            float4 T4[U], C4[U];
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                if (t[u] >= 0) {
+                                    const float* rt = rec + t[u] * RS;
+                                    T4[u] = *reinterpret_cast<const float4*>(rt + offT[s]);
+                                    C4[u] = *reinterpret_cast<const float4*>(rt + offC[s]);
+                                }
+                            }
+#pragma unroll
+                            for (int u = 0; u < U; ++u)
+                                if (t[u] >= 0) df_acc_mul2(accH[s], accL[s], T4[u], C4[u]);
                         }
                     }
                 }
