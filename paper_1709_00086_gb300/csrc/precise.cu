@@ -426,6 +426,9 @@ __global__ void __launch_bounds__(kDThreads) k_accum_df(ListArgs a) {
 __host__ __device__ constexpr size_t adj_df_smem_per_warp(int B, int NRP) {
     return (size_t)B * NRP * 8 + 54 * 16;
 }
+// a double-float value (head, tail) as the duplicated operand (h, h, t, t) of a
+// packed product
+__device__ __forceinline__ float4 dup2(float2 v) { return make_float4(v.x, v.x, v.y, v.y); }
 
 template <int L>
 __global__ void __launch_bounds__(kDThreads) k_adj_df(ListArgs a) {
@@ -506,25 +509,31 @@ __global__ void __launch_bounds__(kDThreads) k_adj_df(ListArgs a) {
                     u1 = u2;
                 });
             }
-            df F = {0.f, 0.f}, Fz = {0.f, 0.f}, Fx = {0.f, 0.f}, Fy = {0.f, 0.f};
+            // (T_k, T_k') side by side: the second operand of the packed products
+            float4 TD[L + 1];
             static_for<0, L + 1>([&](auto kc) {
                 constexpr int k = decltype(kc)::value;
-                const float2 gk = Gb[k];
-                df_acc(F, df_mul_u({gk.x, gk.y}, T[k]));
-                df_acc(Fz, df_mul_u({gk.x, gk.y}, D[k]));
+                TD[k] = make_float4(T[k].h, D[k].h, T[k].l, D[k].l);
+            });
+            // (F, Fz) in one packed double-float accumulator (.x = F, .y = Fz), and per
+            // m the pairs (gmr, gzr) and (gmi, gzi): every component takes the
+            // operations and order of its own scalar sum
+            float2 FH = make_float2(0.f, 0.f), FL = make_float2(0.f, 0.f);
+            df Fx = {0.f, 0.f}, Fy = {0.f, 0.f};
+            static_for<0, L + 1>([&](auto kc) {
+                constexpr int k = decltype(kc)::value;
+                df_acc_mul2(FH, FL, dup2(Gb[k]), TD[k]);
             });
             df pr = {1.f, 0.f}, pim = {0.f, 0.f};  // (x + iy)^(m-1)
             static_for<1, L + 1>([&](auto mc) {
                 constexpr int m = decltype(mc)::value;
                 constexpr int b0 = acc_base(L, m);
-                df gmr = {0.f, 0.f}, gmi = {0.f, 0.f}, gzr = {0.f, 0.f}, gzi = {0.f, 0.f};
+                float2 RH = make_float2(0.f, 0.f), RL = make_float2(0.f, 0.f);  // (gmr, gzr)
+                float2 IH = make_float2(0.f, 0.f), IL = make_float2(0.f, 0.f);  // (gmi, gzi)
                 static_for<0, L - m + 1>([&](auto kc) {
                     constexpr int k = decltype(kc)::value;
-                    const float2 gr = Gb[b0 + 2 * k], gi = Gb[b0 + 2 * k + 1];
-                    df_acc(gmr, df_mul_u({gr.x, gr.y}, T[k]));
-                    df_acc(gmi, df_mul_u({gi.x, gi.y}, T[k]));
-                    df_acc(gzr, df_mul_u({gr.x, gr.y}, D[k]));
-                    df_acc(gzi, df_mul_u({gi.x, gi.y}, D[k]));
+                    df_acc_mul2(RH, RL, dup2(Gb[b0 + 2 * k]), TD[k]);
+                    df_acc_mul2(IH, IL, dup2(Gb[b0 + 2 * k + 1]), TD[k]);
                 });
                 df ur, ui;  // (x + iy)^m
                 if constexpr (m == 1) {
@@ -535,10 +544,9 @@ __global__ void __launch_bounds__(kDThreads) k_adj_df(ListArgs a) {
                 }
                 // F += Re(conj(gm) u^m), Fz likewise with gz, and the derivatives of
                 // u^m: d/dx = m u^(m-1), d/dy = i m u^(m-1)
-                df_acc(F, df_mul_u(gmr, ur));
-                df_acc(F, df_mul_u(gmi, ui));
-                df_acc(Fz, df_mul_u(gzr, ur));
-                df_acc(Fz, df_mul_u(gzi, ui));
+                df_acc_mul2(FH, FL, make_float4(RH.x, RH.y, RL.x, RL.y), make_float4(ur.h, ur.h, ur.l, ur.l));
+                df_acc_mul2(FH, FL, make_float4(IH.x, IH.y, IL.x, IL.y), make_float4(ui.h, ui.h, ui.l, ui.l));
+                const df gmr = {RH.x, RL.x}, gmi = {IH.x, IL.x};
                 const df ax = df_add(df_mul_u(gmr, pr), df_mul_u(gmi, pim));
                 const df ay = df_add(df_mul_u(gmi, pr), df_neg(df_mul_u(gmr, pim)));
                 df_acc(Fx, df_mulf(ax, (float)m));
@@ -546,6 +554,7 @@ __global__ void __launch_bounds__(kDThreads) k_adj_df(ListArgs a) {
                 pr = ur;
                 pim = ui;
             });
+            const df F = {FH.x, FL.x}, Fz = {FH.y, FL.y};
             // tangential gradient: (2 w_j / r) (grad F - (grad F . u) u), formed in
             // double-float and rounded once: a per-pair relative error of an FP32
             // ulp is not amplified by the sums over pairs
