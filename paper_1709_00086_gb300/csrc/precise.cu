@@ -19,10 +19,11 @@
 //                 is exact), r^2, 1/r by one Newton step from rsqrt, the unit
 //                 vector, T_k(z) and w (x + iy)^m, all in double-float, into a
 //                 shared-memory record.  Then every lane adds the chunk's 32
-//                 terms T_k w (x + iy)^m to the (lmax+1)^2 / 32 accumulator
-//                 slots it owns (double-float sums, no cross-lane reduction).
-//                 At a change of bin the slots go to double-float shared
-//                 memory; at the primary's end the Chebyshev -> Legendre-form
+//                 terms T_k w (x + iy)^m to the accumulator slots it owns, two
+//                 slots per packed f32x2 operation (double-float sums, no
+//                 cross-lane reduction).  At a change of bin the slots go to
+//                 double-float shared memory; at the primary's end the
+//                 Chebyshev -> Legendre-form
 //                 connection (times K_lm, head + tail coefficients) is applied
 //                 in double-float and the row of A is stored.  No FP64
 //                 arithmetic: the FP64 pipe runs at 1/58 of the FP32 rate here.
@@ -30,9 +31,10 @@
 //                 coefficients G_{m,k} = w_i sum_l c^(m)_{l-m,k} K_lm V_lm of
 //                 the primary (FP64 from the FP64 V = M A, held as head + tail
 //                 in shared memory), and per pair F = sum Re(conj(G) T_k
-//                 (x + iy)^m) with its gradient in double-float, rounded once
-//                 to FP32 per pair; FP64 atomics for the secondary, a
-//                 double-float sum for the primary.
+//                 (x + iy)^m) with its gradient in double-float (F with dF/dz,
+//                 and the per-m sums against T_k and T_k', as packed f32x2
+//                 pairs), rounded once to FP32 per pair; FP64 atomics for the
+//                 secondary, a double-float sum for the primary.
 #include "pair_common.cuh"
 
 namespace g3 {
