@@ -25,8 +25,8 @@
 //                 double-float shared memory; at the primary's end the
 //                 Chebyshev -> Legendre-form connection (times K_lm, head +
 //                 tail coefficients) is applied in double-float and the row
-//                 of A is stored.  No FP64
-//                 arithmetic: the FP64 pipe runs at 1/58 of the FP32 rate here.
+//                 of A is stored.  No FP64 arithmetic: the FP64 pipe runs at
+//                 1/58 of the FP32 rate here.
 //   k_adj_df   -- per primary (one warp), one pair per lane: the adjoint
 //                 coefficients G_{m,k} = w_i sum_l c^(m)_{l-m,k} K_lm V_lm of
 //                 the primary (FP64 from the FP64 V = M A, held as head + tail
