@@ -22,9 +22,11 @@
 //               partials, and one warp butterfly per (primary, bin) reduces
 //               them; the normalised row of multipoles goes to A.
 //
-// Compared with the fused kernel (pair.cu, kept for graph-captured calls and
-// for the adjoint), the accumulation runs without the scan's state in
-// registers and reduces across lanes once per bin instead of once per bucket.
+// Compared with the fused kernel (pair.cu, G3PCF_OPT_PAIR_KERNELS = 1, kept as
+// a cross-check), the accumulation runs without the scan's state in registers
+// and reduces across lanes once per bin instead of once per bucket.  Plain,
+// batched and graph-captured forwards, and the adjoint pair pass (k_adj), all
+// walk these lists.
 #include "pair_common.cuh"
 
 namespace g3 {
